@@ -1,0 +1,263 @@
+/*
+ * mpcg.h -- C ABI of the GB300 (sm_103a) mixed-precision conjugate gradient library.
+ *
+ * The library solves sparse symmetric positive definite systems A x = b (A in CSR) with
+ * the conjugate gradient method of arXiv 2504.14268, Section 3, Eq. (1)-(4), in which the
+ * four operations of Section 4.2 run at a precision chosen at every iteration by a
+ * policy:
+ *     op 1  q_k      = fl_p1(A p_k)          (sparse matrix-vector product)
+ *     op 2  z_{k+1}  = fl_p2(M^-1 r_{k+1})   (preconditioner solve; M = I here, so a rounding of r)
+ *     op 3  nu_k     = fl_p3(p_k^T q_k)      (inner product for alpha)
+ *     op 4  sigma_k+1= fl_p4(r^T z)          (inner product for beta)
+ * while the residual update r_{k+1} = r_k - alpha_k q_k and the scalars alpha_k = sigma_k /
+ * nu_k, beta_k = sigma_{k+1} / sigma_k stay in fp64 (Section 4.2). Policies are the
+ * Q-learning tables of Section 4.1 (greedy inference as in Algorithm 2, epsilon-greedy
+ * training as in Algorithm 1), fixed assignments, replayed schedules, or a small MLP
+ * Q-function.
+ *
+ * Conventions (every entry point):
+ *   - Every call returns an mpcg_status. A solver outcome (converged, iteration cap,
+ *     breakdown) is not an error; it is reported in mpcg_result.outcome.
+ *   - Arguments are validated on the host before any kernel launch; device-side problems
+ *     (a barrier wait that exceeded its time limit) are reported through a device status
+ *     word and returned as MPCG_ERR_TIMEOUT. No kernel traps.
+ *   - Memory the caller passes in (CSR arrays, b, x, history) stays owned by the caller;
+ *     the library neither frees nor keeps pointers to it past the call. Objects the
+ *     library creates (context, matrix, policy) are freed by the matching *_destroy.
+ *   - Pointers to vectors and CSR arrays may be host memory (pageable or pinned) or device
+ *     memory of the context's device; the library tells them apart with
+ *     cudaPointerGetAttributes and stages host data through its own device buffers.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is enqueued on
+ *     it; calls that return host-side results synchronise that stream before returning.
+ *   - A context is used by one host thread at a time.
+ *   - On error, mpcg_last_error(ctx) returns a message describing the failure.
+ */
+#ifndef MPCG_H
+#define MPCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpcg_ctx_s* mpcg_ctx_t;       /* library-owned, opaque */
+typedef struct mpcg_matrix_s* mpcg_matrix_t; /* library-owned device copies of A in every format */
+typedef struct mpcg_policy_s* mpcg_policy_t; /* FIXED | SCHEDULE | QTABLE | MLP */
+
+/* Number formats. 0..4 are the precision set of Section 5, in the order used for argmax
+ * ties (first index wins). fp16/bf16/fp32/fp64 follow Table 1; tf32 (not in Table 1) is
+ * read as 11 significand digits with the fp32 exponent range. BF16R / FP16R store the
+ * matrix values of row i as fl(a_ij / s_i) with s_i = 2^floor(log2 max_j |a_ij|) (an
+ * extension: power-of-two row scaling); for ops 2-4 they round like BF16 / FP16. */
+typedef enum {
+  MPCG_FP16 = 0,
+  MPCG_BF16 = 1,
+  MPCG_TF32 = 2,
+  MPCG_FP32 = 3,
+  MPCG_FP64 = 4,
+  MPCG_BF16R = 5,
+  MPCG_FP16R = 6
+} mpcg_prec;
+#define MPCG_NUM_FORMATS 7
+#define MPCG_NUM_OPS 4
+#define MPCG_MAX_PREC 8
+
+typedef enum {
+  MPCG_OK = 0,
+  MPCG_ERR_INVALID_ARG = 1, /* bad pointer, size, CSR structure or option     */
+  MPCG_ERR_CUDA = 2,        /* a CUDA runtime call failed                      */
+  MPCG_ERR_OOM = 3,         /* device allocation failed                        */
+  MPCG_ERR_BAD_POLICY = 4,  /* policy incompatible with the context's options  */
+  MPCG_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up              */
+  MPCG_ERR_INTERNAL = 6
+} mpcg_status;
+
+typedef enum { MPCG_CONVERGED = 0, MPCG_MAX_ITER = 1, MPCG_BREAKDOWN = 2 } mpcg_outcome;
+
+/* CSR matrix: n rows, nnz stored entries, row_ptr[n+1] (row_ptr[0] = 0, non-decreasing,
+ * row_ptr[n] = nnz), col[nnz] in [0, n), val[nnz] fp64. Every row must hold its diagonal
+ * entry with a positive value (a necessary condition for SPD). Symmetry is not checked.
+ * nnz < 2^31. Host or device pointers (all three in the same space). */
+typedef struct {
+  int32_t n;
+  int64_t nnz;
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const double* val;
+} mpcg_csr;
+
+/* Method options. mpcg_options_default() fills the values of Sections 4.1 and 5. */
+typedef struct {
+  int32_t b_bins;          /* b iteration bins (10)                                     */
+  int32_t r_bins;          /* r residual bins (10)                                      */
+  int32_t t_bin;           /* T_max used by the iteration bins (1000)                   */
+  int32_t min_k;           /* a solve may stop at iteration k only if k >= min_k (10)   */
+  double eps_min;          /* residual floor of the bins and reward (1e-16)             */
+  int32_t nprec;           /* size of the precision set P (5), <= MPCG_MAX_PREC         */
+  int32_t precs[MPCG_MAX_PREC]; /* P as mpcg_prec codes, in argmax tie order            */
+  double cost[MPCG_MAX_PREC];   /* c(p) for each entry of precs (cost setting C1)       */
+  double w1, w2, w3;       /* reward weights (1.0, 0.1, 10.0)                           */
+  double lr, gamma;        /* Q-learning rate alpha and discount gamma (0.1, 0.9)       */
+  double eps0, eps_floor;  /* exploration: eps_e = max(eps_floor, eps0 (1 - e/E)) (1, 0.1) */
+  uint64_t seed;           /* key of the Philox4x64-10 exploration draws                */
+  int32_t unvisited_fallback; /* greedy action for a (state, op) never updated in
+                                 training: an mpcg_prec code (default MPCG_FP64), or -1
+                                 for the plain first-index argmax                      */
+  int32_t true_res_every;  /* >0: replace r by b - A x (fp64) every this many iterations */
+  int32_t true_res_at_conv;/* 1: confirm a claimed convergence with b - A x (fp64)      */
+  int32_t warm_start;      /* 1: x holds x_0 on entry; 0: x_0 = 0 (Algorithms 1 and 2)  */
+  int32_t mlp_hidden;      /* hidden width of the MLP policy (64)                       */
+} mpcg_options;
+
+/* Result of one solve. */
+typedef struct {
+  int32_t outcome;         /* mpcg_outcome                                              */
+  int32_t iters;           /* completed iterations (Algorithm 2 logs k+1 at the stop)   */
+  double rel_res_rec;      /* ||r|| / ||b|| of the recursive residual at the end        */
+  double rel_res_true;     /* ||b - A x|| / ||b|| computed in fp64 at the end           */
+  int32_t n_true_checks;   /* residual recomputations during the solve                  */
+  int32_t pad;
+  int64_t action_hist[MPCG_NUM_OPS][MPCG_MAX_PREC]; /* iterations per (op, format)       */
+} mpcg_result;
+
+/* One record per iteration k (64 bytes). rho is rho_{k+1} after the iteration (the true
+ * relative residual when r was replaced). flags: bit0 converged here, bit1 breakdown here,
+ * bit2 r replaced by b - A x, bit3 an operation explored (training). */
+typedef struct {
+  int32_t k, state;
+  int8_t fmt[4];
+  int8_t act[4];
+  double rho, nu, alpha, sigma, beta, reward;
+  int32_t flags, pad;
+} mpcg_iter_record;
+
+/* Matrix statistics filled by mpcg_matrix_info. */
+typedef struct {
+  int32_t n;
+  int64_t nnz;
+  double mean_row_nnz, max_row_nnz, cv_row_nnz;
+  int32_t spmv_sched[MPCG_NUM_FORMATS]; /* SpMV schedule chosen per value format          */
+  int32_t spmv_lanes[MPCG_NUM_FORMATS]; /* lanes per row of that schedule                 */
+  int64_t device_bytes;                 /* library-owned device memory of the matrix      */
+  double static_features[5];            /* MLP policy's static matrix features            */
+} mpcg_matrix_stats;
+
+/* ---- context ---------------------------------------------------------------------- */
+
+/* Fills *opt with the paper's defaults (Sections 4.1 and 5, cost setting C1, P = {fp16,
+ * bf16, tf32, fp32, fp64}). */
+void mpcg_options_default(mpcg_options* opt);
+
+/* Creates a context on CUDA device `device` with a copy of *opt (NULL = defaults).
+ * Errors: INVALID_ARG (bad options), CUDA, OOM. */
+mpcg_status mpcg_create(mpcg_ctx_t* out, int device, const mpcg_options* opt);
+mpcg_status mpcg_destroy(mpcg_ctx_t ctx);
+/* Message of the last failed call on ctx ("" if none). Valid until the next call. */
+const char* mpcg_last_error(mpcg_ctx_t ctx);
+/* Returns the number of SMs and the co-resident CTAs per SM of the solver kernel. */
+mpcg_status mpcg_device_info(mpcg_ctx_t ctx, int32_t* num_sms, int32_t* ctas_per_sm);
+
+/* ---- matrices --------------------------------------------------------------------- */
+
+/* Copies A into library-owned device memory, validates it on the device (row_ptr
+ * monotone, col in range, finite values, positive diagonal present in every row), builds
+ * the value copies in every format (a single rounding from fp64 each; Table 1 formats and
+ * the row-scaled extensions) and picks an SpMV schedule per format. Enqueued on `stream`
+ * and synchronised. Errors: INVALID_ARG (structure; message names the first bad row),
+ * CUDA, OOM. */
+mpcg_status mpcg_matrix_create(mpcg_ctx_t ctx, const mpcg_csr* A, mpcg_matrix_t* out, void* stream);
+mpcg_status mpcg_matrix_destroy(mpcg_matrix_t A);
+mpcg_status mpcg_matrix_info(mpcg_matrix_t A, mpcg_matrix_stats* info);
+/* Times every SpMV schedule on A for each value format (a few launches each) and keeps
+ * the fastest (the autotuner). `reps` timed launches per candidate. */
+mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, void* stream);
+/* Forces the SpMV schedule of value format `fmt` (sched: 0 = sub-warp vector CSR with
+ * `lanes` lanes per row; 1 = staged stream CSR, shared-memory tiles filled by bulk copies,
+ * `lanes` lanes per row). */
+mpcg_status mpcg_matrix_set_schedule(mpcg_matrix_t A, int32_t fmt, int32_t sched, int32_t lanes);
+
+/* y = fl_fmt(A fl_fmt(x)) with the matrix's schedule for `fmt` (op 1 of Section 4.2 on its
+ * own; x and y fp64 device vectors of length n). `reps` > 1 repeats the product (for timing);
+ * if ms_per_rep is non-NULL it receives the mean device time of one product. */
+mpcg_status mpcg_spmv(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t fmt, const double* x, double* y,
+                      int32_t reps, double* ms_per_rep, void* stream);
+
+/* ---- policies --------------------------------------------------------------------- */
+
+/* Same four formats at every iteration (op order p1..p4). Any mpcg_prec codes. */
+mpcg_status mpcg_policy_fixed(mpcg_ctx_t ctx, const int32_t fmt[4], mpcg_policy_t* out);
+/* Iteration k uses row min(k, len-1) of the host array fmts[len][4] (replay). */
+mpcg_status mpcg_policy_schedule(mpcg_ctx_t ctx, const int32_t* fmts, int32_t len, mpcg_policy_t* out);
+/* Tabular policy (Section 4.1): Q[4][b*r][nprec] fp64 and visits[4][b*r] (host arrays,
+ * visits may be NULL = all visited), shaped by the context's options. */
+mpcg_status mpcg_policy_qtable(mpcg_ctx_t ctx, const double* Q, const int32_t* visits, mpcg_policy_t* out);
+/* MLP Q-function 16 -> H -> H -> 4*nprec (ReLU), fp32 parameters in the layout W1[H][16],
+ * b1[H], W2[H][H], b2[H], W3[4*nprec][H], b3[4*nprec] (host array of mpcg_mlp_nparams
+ * floats), H = options.mlp_hidden. */
+mpcg_status mpcg_policy_mlp(mpcg_ctx_t ctx, const float* params, mpcg_policy_t* out);
+int64_t mpcg_mlp_nparams(int32_t hidden, int32_t nprec);
+/* Copies a QTABLE policy's tables back to host arrays (either may be NULL). */
+mpcg_status mpcg_policy_get_qtable(mpcg_policy_t P, double* Q, int32_t* visits);
+/* Copies an MLP policy's parameters back to a host array. */
+mpcg_status mpcg_policy_get_mlp(mpcg_policy_t P, float* params);
+/* Serialises a policy to a host buffer. With blob == NULL, *bytes receives the size. The
+ * blob holds a header (magic "MPCGPOL1", kind, b, r, t_bin, eps_min, nprec, precs, costs)
+ * followed by the tables or parameters. */
+mpcg_status mpcg_policy_save(mpcg_policy_t P, void* blob, size_t* bytes);
+/* Creates a policy from a blob written by mpcg_policy_save (host buffer). Errors:
+ * INVALID_ARG (bad magic or size), BAD_POLICY (shape differs from the context's options). */
+mpcg_status mpcg_policy_load(mpcg_ctx_t ctx, const void* blob, size_t bytes, mpcg_policy_t* out);
+mpcg_status mpcg_policy_destroy(mpcg_policy_t P);
+
+/* ---- solves ----------------------------------------------------------------------- */
+
+/* Solves A x = b with the policy (Algorithm 2 for QTABLE/MLP policies) until
+ * ||r_{k+1}|| / ||b|| < tol with k >= min_k, max_iter iterations, or breakdown
+ * (non-positive or non-finite p^T A p, non-finite residual). One cooperative launch of the
+ * persistent kernel runs every iteration on the device. b and x: n doubles, host or device.
+ * history (optional): device or host array of history_cap records. Synchronises `stream`.
+ * Errors: INVALID_ARG, BAD_POLICY, CUDA, OOM, TIMEOUT. */
+mpcg_status mpcg_solve(mpcg_ctx_t ctx, mpcg_matrix_t A, const double* b, double* x, double tol,
+                       int32_t max_iter, mpcg_policy_t policy, mpcg_result* res,
+                       mpcg_iter_record* history, int32_t history_cap, void* stream);
+
+/* Solves nsys independent systems in one persistent launch: the systems are assigned
+ * longest-first to teams of CTAs sized by their nonzeros. b[i], x[i]: device pointers.
+ * tol and max_iter: per system (host arrays). res: host array of nsys results.
+ * Synchronises `stream`. */
+mpcg_status mpcg_solve_batched(mpcg_ctx_t ctx, int32_t nsys, const mpcg_matrix_t* A,
+                               const double* const* b, double* const* x, const double* tol,
+                               const int32_t* max_iter, mpcg_policy_t policy, mpcg_result* res,
+                               void* stream);
+
+/* Batched solve captured once into a CUDA graph (device pointers only): create, replay,
+ * read results (host array), destroy. Replays reuse the same inputs and outputs. */
+typedef struct mpcg_graph_s* mpcg_graph_t;
+mpcg_status mpcg_graph_create(mpcg_ctx_t ctx, int32_t nsys, const mpcg_matrix_t* A,
+                              const double* const* b, double* const* x, const double* tol,
+                              const int32_t* max_iter, mpcg_policy_t policy, void* stream,
+                              mpcg_graph_t* out);
+mpcg_status mpcg_graph_launch(mpcg_graph_t g, void* stream);
+mpcg_status mpcg_graph_results(mpcg_graph_t g, mpcg_result* res, void* stream);
+mpcg_status mpcg_graph_destroy(mpcg_graph_t g);
+
+/* ---- training --------------------------------------------------------------------- */
+
+/* Tabular Q-learning (Algorithm 1) on nsys training systems, batched: in every round
+ * e = 1..episodes each system runs one epsilon-greedy episode of at most t_max iterations
+ * from x_0 = 0 on a private copy of the tables, updating the copy online; at the end of the
+ * round the shared tables are rebuilt by replaying every recorded transition (system 0..
+ * nsys-1, then iteration order) onto the round-start tables. With nsys = 1 this is
+ * Algorithm 1. `inout` is a QTABLE policy updated in place. iters_out (optional, host,
+ * [episodes][nsys]) receives each episode's iteration count. b[i]: device pointers. */
+mpcg_status mpcg_train_qtable(mpcg_ctx_t ctx, int32_t nsys, const mpcg_matrix_t* A,
+                              const double* const* b, double tol, int32_t t_max, int32_t episodes,
+                              mpcg_policy_t inout, int32_t* iters_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPCG_H */

@@ -1,0 +1,1113 @@
+// Host runtime and C ABI of the mixed-precision CG library (see include/mpcg.h).
+//
+// Owns device memory (matrix copies, policies, launch plans), validates arguments,
+// schedules systems onto teams of CTAs and launches the persistent kernel.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace mpcg;
+
+namespace {
+
+// Device buffer that grows on demand.
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) cap = bytes;
+    return e;
+  }
+  template <typename T> T* as() const { return (T*)p; }
+};
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+constexpr long long kTimeoutCycles = 4000000000ll;  // about two seconds at 2 GHz per wait
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Objects
+// ---------------------------------------------------------------------------------------
+
+struct Plan {
+  int grid = 0, nsys = 0, nteams = 0;
+  DevBuf sys, st, res, cta_team, cta_rank, team_size, team_first, team_sys_off, team_sys, bars, partials, err;
+  DevBuf work, bstage, xstage, hstage;
+  DevBuf qpriv, trans;
+  std::vector<DevSys> hsys;
+  std::vector<mpcg_result> hres;
+  Launch L;
+};
+
+struct mpcg_ctx_s {
+  int device = 0;
+  mpcg_options opt;
+  OptView ov;
+  int nsm = 0;
+  int occ = 0;
+  std::string err;
+  Plan plan;   // reused by mpcg_solve / mpcg_solve_batched / training
+  DevBuf spmv_x, spmv_q, spmv_y;
+};
+
+struct mpcg_matrix_s {
+  mpcg_ctx_t ctx = nullptr;
+  DevMatrix dm;
+  DevBuf rp, ci, v64, v32, vtf, v16, vbf, v16r, vbfr, rscale;
+  double mean = 0, maxr = 0, cv = 0;
+  float feat[5] = {0, 0, 0, 0, 0};
+  long long bytes = 0;
+};
+
+struct mpcg_policy_s {
+  mpcg_ctx_t ctx = nullptr;
+  int kind = 0;
+  int fixed[4] = {4, 4, 4, 4};
+  int sched_len = 0;
+  DevBuf sched, Q, visits, mlp;
+  int S = 0, nprec = 0, H = 0;
+  mpcg_options shape;
+};
+
+struct mpcg_graph_s {
+  mpcg_ctx_t ctx = nullptr;
+  std::unique_ptr<Plan> plan;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+mpcg_status fail(mpcg_ctx_t ctx, mpcg_status s, const char* fmt, ...) {
+  if (ctx) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return s;
+}
+
+#define CK(ctx, call)                                                                                  \
+  do {                                                                                                 \
+    cudaError_t e_ = (call);                                                                           \
+    if (e_ != cudaSuccess) {                                                                           \
+      const mpcg_status s_ = (e_ == cudaErrorMemoryAllocation) ? MPCG_ERR_OOM : MPCG_ERR_CUDA;         \
+      return fail(ctx, s_, "%s failed: %s", #call, cudaGetErrorString(e_));                           \
+    }                                                                                                  \
+  } while (0)
+
+bool valid_fmt(int f) { return f >= 0 && f < NFMT; }
+
+mpcg_status build_optview(mpcg_ctx_t ctx, const mpcg_options& o, OptView& v) {
+  if (o.b_bins < 1 || o.b_bins > kMaxBBins) return fail(ctx, MPCG_ERR_INVALID_ARG, "b_bins must be in [1, %d]", kMaxBBins);
+  if (o.r_bins < 1 || o.r_bins > kMaxRBins) return fail(ctx, MPCG_ERR_INVALID_ARG, "r_bins must be in [1, %d]", kMaxRBins);
+  if (o.t_bin < 1) return fail(ctx, MPCG_ERR_INVALID_ARG, "t_bin must be >= 1");
+  if (o.nprec < 1 || o.nprec > MPCG_MAX_PREC) return fail(ctx, MPCG_ERR_INVALID_ARG, "nprec must be in [1, 8]");
+  if (!(o.eps_min > 0.0 && o.eps_min < 1.0)) return fail(ctx, MPCG_ERR_INVALID_ARG, "eps_min must be in (0, 1)");
+  if (o.mlp_hidden < 1 || o.mlp_hidden > kMaxHidden) return fail(ctx, MPCG_ERR_INVALID_ARG, "mlp_hidden must be in [1, %d]", kMaxHidden);
+  for (int a = 0; a < o.nprec; ++a)
+    if (!valid_fmt(o.precs[a])) return fail(ctx, MPCG_ERR_INVALID_ARG, "precs[%d] = %d is not a format code", a, o.precs[a]);
+  if (o.unvisited_fallback != -1 && !valid_fmt(o.unvisited_fallback))
+    return fail(ctx, MPCG_ERR_INVALID_ARG, "unvisited_fallback must be -1 or a format code");
+  memset(&v, 0, sizeof(v));
+  v.b_bins = o.b_bins;
+  v.r_bins = o.r_bins;
+  v.t_bin = o.t_bin;
+  v.t_width = (o.t_bin + o.b_bins - 1) / o.b_bins;
+  v.min_k = o.min_k;
+  v.nprec = o.nprec;
+  for (int a = 0; a < MPCG_MAX_PREC; ++a) {
+    v.precs[a] = a < o.nprec ? o.precs[a] : 0;
+    v.cost[a] = a < o.nprec ? o.cost[a] : 0.0;
+  }
+  // Residual bins (Section 4.1): j = min(floor(-log10 max(rho, eps_min) / delta), r - 1) with
+  // delta = -log10(eps_min) / r, evaluated as the count of thresholds 10^(-m delta), m = 1..r-1,
+  // that rho does not exceed.
+  const double delta = -std::log10(o.eps_min) / o.r_bins;
+  for (int m = 1; m < o.r_bins; ++m) v.thr[m] = std::pow(10.0, -m * delta);
+  v.log_cap = -std::log10(o.eps_min);
+  v.eps_min = o.eps_min;
+  v.w1 = o.w1;
+  v.w2 = o.w2;
+  v.w3 = o.w3;
+  v.lr = o.lr;
+  v.gamma = o.gamma;
+  v.seed = o.seed;
+  v.fallback_fmt = o.unvisited_fallback;
+  v.fallback_idx = -1;
+  for (int a = 0; a < o.nprec; ++a)
+    if (o.precs[a] == o.unvisited_fallback) { v.fallback_idx = a; break; }
+  v.true_every = o.true_res_every;
+  v.true_at_conv = o.true_res_at_conv;
+  v.warm_start = o.warm_start;
+  return MPCG_OK;
+}
+
+// Team size for a system of `work` units (nonzeros plus vector work): about 24k units per
+// CTA, at most the whole grid.
+int team_size_for(long long work, int grid) {
+  long long s = (work + 24575) / 24576;
+  if (s < 1) s = 1;
+  if (s > grid) s = grid;
+  return (int)s;
+}
+
+struct SysIn {
+  mpcg_matrix_t A;
+  const double* b;   // device
+  double* x;         // device
+  double tol;
+  int max_iter;
+  mpcg_iter_record* hist;
+  int hist_cap;
+};
+
+// Longest-processing-time assignment of systems to teams. Systems large enough for
+// several CTAs get a team of their own sized by their work; the other CTAs form
+// one-CTA teams. Remaining systems go, largest first, to the team whose load per CTA
+// grows least.
+void schedule(const std::vector<long long>& work, int grid, int force_team, std::vector<int>& team_size,
+              std::vector<std::vector<int>>& team_sys) {
+  const int nsys = (int)work.size();
+  team_size.clear();
+  team_sys.clear();
+  if (nsys == 0) return;
+  std::vector<int> order(nsys);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+  if (force_team > 0) {
+    // Fixed team size for every system (deterministic layouts for tests).
+    const int ts = std::min(force_team, grid);
+    const int nt = std::max(1, grid / ts);
+    for (int t = 0; t < nt; ++t) {
+      team_size.push_back(ts);
+      team_sys.emplace_back();
+    }
+    std::vector<double> load(nt, 0.0);
+    for (int i : order) {
+      int best = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      team_sys[best].push_back(i);
+      load[best] += (double)work[i];
+    }
+    return;
+  }
+  if (nsys == 1) {
+    team_size.push_back(team_size_for(work[0], grid));
+    team_sys.push_back({0});
+    return;
+  }
+  const double total = (double)std::accumulate(work.begin(), work.end(), 0LL);
+  const double per_cta = total / grid;
+  int used = 0;
+  std::vector<double> load;
+  std::vector<char> placed(nsys, 0);
+  for (int i : order) {
+    int s = (int)std::floor((double)work[i] / per_cta);
+    s = std::min(s, team_size_for(work[i], grid));
+    if (s < 2) break;
+    if (used + s > grid - 1) s = grid - 1 - used;
+    if (s < 2) break;
+    team_size.push_back(s);
+    team_sys.push_back({i});
+    load.push_back((double)work[i] / s);
+    placed[i] = 1;
+    used += s;
+  }
+  while (used < grid) {
+    team_size.push_back(1);
+    team_sys.emplace_back();
+    load.push_back(0.0);
+    ++used;
+  }
+  for (int i : order) {
+    if (placed[i]) continue;
+    int best = 0;
+    double bestv = 1e300;
+    for (size_t t = 0; t < team_size.size(); ++t) {
+      const double v = load[t] + (double)work[i] / team_size[t];
+      if (v < bestv) { bestv = v; best = (int)t; }
+    }
+    team_sys[best].push_back(i);
+    load[best] = bestv;
+  }
+}
+
+mpcg_status fill_policy(mpcg_ctx_t ctx, mpcg_policy_t P, PolicyView& pv) {
+  memset(&pv, 0, sizeof(pv));
+  if (!P) return fail(ctx, MPCG_ERR_INVALID_ARG, "policy is NULL");
+  pv.kind = P->kind;
+  for (int j = 0; j < 4; ++j) pv.fixed[j] = P->fixed[j];
+  pv.sched = P->sched.as<int>();
+  pv.sched_len = P->sched_len;
+  pv.Q = P->Q.as<double>();
+  pv.visits = P->visits.as<int>();
+  pv.mlp = P->mlp.as<float>();
+  pv.H = P->H;
+  if (P->kind == 2 || P->kind == 3) {
+    const mpcg_options& o = ctx->opt;
+    if (P->nprec != o.nprec || (P->kind == 2 && P->S != o.b_bins * o.r_bins) || (P->kind == 3 && P->H != o.mlp_hidden))
+      return fail(ctx, MPCG_ERR_BAD_POLICY, "policy shape (S=%d, nprec=%d, H=%d) differs from the context's options",
+                  P->S, P->nprec, P->H);
+  }
+  return MPCG_OK;
+}
+
+// Builds the device tables of a launch for `in` systems into `pl` and fills pl.L.
+mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, mpcg_policy_t policy, int train,
+                       int trans_cap, int force_team, cudaStream_t s) {
+  const int nsys = (int)in.size();
+  const int grid = ctx->nsm * ctx->occ;
+  std::vector<long long> work(nsys);
+  for (int i = 0; i < nsys; ++i) work[i] = in[i].A->dm.nnz + 4LL * in[i].A->dm.n;
+  std::vector<int> tsize;
+  std::vector<std::vector<int>> tsys;
+  schedule(work, grid, force_team, tsize, tsys);
+  const int nteams = (int)tsize.size();
+  std::vector<int> cta_team(grid, nteams), cta_rank(grid, 0), team_first(nteams + 1, 0), team_sys_off(nteams + 2, 0), team_sys_flat;
+  int c = 0;
+  for (int t = 0; t < nteams; ++t) {
+    team_first[t] = c;
+    for (int r = 0; r < tsize[t]; ++r, ++c) {
+      cta_team[c] = t;
+      cta_rank[c] = r;
+    }
+    team_sys_off[t] = (int)team_sys_flat.size();
+    for (int i : tsys[t]) team_sys_flat.push_back(i);
+  }
+  team_sys_off[nteams] = (int)team_sys_flat.size();
+  // CTAs beyond the scheduled teams form one extra empty team.
+  std::vector<int> tsize_all(tsize);
+  tsize_all.push_back(std::max(1, grid - c));
+  team_first[nteams] = c;
+  team_sys_off[nteams + 1] = team_sys_off[nteams];
+  for (int cc = c; cc < grid; ++cc) {
+    cta_team[cc] = nteams;
+    cta_rank[cc] = cc - c;
+  }
+  const int nteams_all = nteams + 1;
+
+  // Work vectors: r, p, q (8 bytes per row each) and p's low-precision copy (4 bytes).
+  size_t wbytes = 0;
+  for (int i = 0; i < nsys; ++i) wbytes += 28 * (size_t)in[i].A->dm.n + 4 * 256;
+  CK(ctx, pl.work.ensure(wbytes));
+  const int S = ctx->opt.b_bins * ctx->opt.r_bins;
+  const long long qsize = 4LL * S * ctx->opt.nprec;
+  if (train) {
+    CK(ctx, pl.qpriv.ensure(sizeof(double) * qsize * nsys));
+    CK(ctx, pl.trans.ensure(sizeof(Transition) * (size_t)trans_cap * nsys));
+  }
+  pl.hsys.resize(nsys);
+  char* wp = pl.work.as<char>();
+  auto take = [&](size_t bytes) {
+    char* r = wp;
+    wp += (bytes + 255) / 256 * 256;
+    return (void*)r;
+  };
+  for (int i = 0; i < nsys; ++i) {
+    DevSys& d = pl.hsys[i];
+    memset(&d, 0, sizeof(d));
+    d.A = in[i].A->dm;
+    const int n = d.A.n;
+    d.b = in[i].b;
+    d.x = in[i].x;
+    d.r = (double*)take(8 * (size_t)n);
+    d.p = (double*)take(8 * (size_t)n);
+    d.q = take(8 * (size_t)n);
+    d.plow = take(4 * (size_t)n);
+    d.tol = in[i].tol;
+    d.max_iter = in[i].max_iter;
+    d.lane = i;
+    d.hist = in[i].hist;
+    d.hist_cap = in[i].hist_cap;
+    if (train) {
+      d.Qpriv = pl.qpriv.as<double>() + qsize * i;
+      d.trans = pl.trans.as<Transition>() + (size_t)trans_cap * i;
+      d.trans_cap = trans_cap;
+    }
+    for (int j = 0; j < 5; ++j) d.feat_static[j] = in[i].A->feat[j];
+  }
+  CK(ctx, pl.sys.ensure(sizeof(DevSys) * std::max(nsys, 1)));
+  CK(ctx, pl.st.ensure(sizeof(SysState) * std::max(nsys, 1)));
+  CK(ctx, pl.res.ensure(sizeof(mpcg_result) * std::max(nsys, 1)));
+  CK(ctx, pl.cta_team.ensure(sizeof(int) * grid));
+  CK(ctx, pl.cta_rank.ensure(sizeof(int) * grid));
+  CK(ctx, pl.team_size.ensure(sizeof(int) * nteams_all));
+  CK(ctx, pl.team_first.ensure(sizeof(int) * (nteams_all + 1)));
+  CK(ctx, pl.team_sys_off.ensure(sizeof(int) * (nteams_all + 1)));
+  CK(ctx, pl.team_sys.ensure(sizeof(int) * std::max<size_t>(1, team_sys_flat.size())));
+  CK(ctx, pl.bars.ensure(sizeof(unsigned) * kBarStride * nteams_all));
+  CK(ctx, pl.partials.ensure(sizeof(double) * kNSlot * grid));
+  CK(ctx, pl.err.ensure(sizeof(unsigned)));
+  if (nsys) CK(ctx, cudaMemcpyAsync(pl.sys.p, pl.hsys.data(), sizeof(DevSys) * nsys, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(pl.cta_team.p, cta_team.data(), sizeof(int) * grid, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(pl.cta_rank.p, cta_rank.data(), sizeof(int) * grid, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(pl.team_size.p, tsize_all.data(), sizeof(int) * nteams_all, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(pl.team_first.p, team_first.data(), sizeof(int) * (nteams_all + 1), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(pl.team_sys_off.p, team_sys_off.data(), sizeof(int) * (nteams_all + 1), cudaMemcpyHostToDevice, s));
+  if (!team_sys_flat.empty())
+    CK(ctx, cudaMemcpyAsync(pl.team_sys.p, team_sys_flat.data(), sizeof(int) * team_sys_flat.size(), cudaMemcpyHostToDevice, s));
+  // The host vectors above are pageable; wait for the copies before they go out of scope.
+  CK(ctx, cudaStreamSynchronize(s));
+  pl.grid = grid;
+  pl.nsys = nsys;
+  pl.nteams = nteams_all;
+  Launch& L = pl.L;
+  memset(&L, 0, sizeof(L));
+  L.sys = pl.sys.as<DevSys>();
+  L.st = pl.st.as<SysState>();
+  L.nsys = nsys;
+  L.nteams = nteams_all;
+  L.cta_team = pl.cta_team.as<int>();
+  L.cta_rank = pl.cta_rank.as<int>();
+  L.team_size = pl.team_size.as<int>();
+  L.team_first = pl.team_first.as<int>();
+  L.team_sys_off = pl.team_sys_off.as<int>();
+  L.team_sys = pl.team_sys.as<int>();
+  L.bars = pl.bars.as<unsigned>();
+  L.partials = pl.partials.as<double>();
+  L.res = pl.res.as<mpcg_result>();
+  L.err = pl.err.as<unsigned>();
+  mpcg_status st = fill_policy(ctx, policy, L.pol);
+  if (st != MPCG_OK) return st;
+  L.opt = ctx->ov;
+  L.train = train;
+  L.timeout_cycles = kTimeoutCycles;
+  if (const char* t = getenv("MPCG_TIMEOUT_CYCLES")) L.timeout_cycles = atoll(t);
+  return MPCG_OK;
+}
+
+// Enqueues one launch of a built plan (barrier counters and status word cleared first).
+mpcg_status enqueue_plan(mpcg_ctx_t ctx, Plan& pl, cudaStream_t s) {
+  CK(ctx, cudaMemsetAsync(pl.bars.p, 0, sizeof(unsigned) * kBarStride * pl.nteams, s));
+  CK(ctx, cudaMemsetAsync(pl.err.p, 0, sizeof(unsigned), s));
+  CK(ctx, launch_cg(pl.L, pl.grid, 0, s));
+  return MPCG_OK;
+}
+
+mpcg_status finish_plan(mpcg_ctx_t ctx, Plan& pl, mpcg_result* res, cudaStream_t s) {
+  unsigned herr = 0;
+  pl.hres.resize(std::max(pl.nsys, 1));
+  if (pl.nsys) CK(ctx, cudaMemcpyAsync(pl.hres.data(), pl.res.p, sizeof(mpcg_result) * pl.nsys, cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaMemcpyAsync(&herr, pl.err.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  if (herr == DERR_TIMEOUT) return fail(ctx, MPCG_ERR_TIMEOUT, "a device-side barrier wait exceeded its limit");
+  if (herr) return fail(ctx, MPCG_ERR_INTERNAL, "device status word %u", herr);
+  if (res && pl.nsys) memcpy(res, pl.hres.data(), sizeof(mpcg_result) * pl.nsys);
+  return MPCG_OK;
+}
+
+void default_schedule(mpcg_matrix_s* M) {
+  // Sub-warp vector CSR with about four nonzeros per lane.
+  int lanes = 1;
+  while (lanes < 32 && lanes * 4 < M->mean) lanes *= 2;
+  for (int f = 0; f < 8; ++f) {
+    M->dm.sched[f] = SCHED_VECTOR;
+    M->dm.lanes[f] = lanes;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------
+
+extern "C" {
+
+void mpcg_options_default(mpcg_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->b_bins = 10;
+  o->r_bins = 10;
+  o->t_bin = 1000;
+  o->min_k = 10;
+  o->eps_min = 1e-16;
+  o->nprec = 5;
+  const int precs[5] = {MPCG_FP16, MPCG_BF16, MPCG_TF32, MPCG_FP32, MPCG_FP64};
+  const double cost[5] = {0.8, 0.6, 0.8, 1.0, 2.0};  // cost setting C1 (Section 5)
+  for (int a = 0; a < 5; ++a) {
+    o->precs[a] = precs[a];
+    o->cost[a] = cost[a];
+  }
+  o->w1 = 1.0;
+  o->w2 = 0.1;
+  o->w3 = 10.0;
+  o->lr = 0.1;
+  o->gamma = 0.9;
+  o->eps0 = 1.0;
+  o->eps_floor = 0.1;
+  o->seed = 0;
+  o->unvisited_fallback = MPCG_FP64;
+  o->true_res_every = 0;
+  o->true_res_at_conv = 0;
+  o->warm_start = 0;
+  o->mlp_hidden = 64;
+}
+
+mpcg_status mpcg_create(mpcg_ctx_t* out, int device, const mpcg_options* opt) {
+  if (!out) return MPCG_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::unique_ptr<mpcg_ctx_s> c(new mpcg_ctx_s());
+  if (opt) c->opt = *opt;
+  else mpcg_options_default(&c->opt);
+  mpcg_status s = build_optview(c.get(), c->opt, c->ov);
+  if (s != MPCG_OK) return s;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return MPCG_ERR_INVALID_ARG;
+  }
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) return MPCG_ERR_CUDA;
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+  cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device);
+  if (!coop) return MPCG_ERR_CUDA;
+  if (cg_occupancy(&c->occ, 0) != cudaSuccess || c->occ < 1) return MPCG_ERR_CUDA;
+  *out = c.release();
+  return MPCG_OK;
+}
+
+mpcg_status mpcg_destroy(mpcg_ctx_t ctx) {
+  if (!ctx) return MPCG_ERR_INVALID_ARG;
+  cudaSetDevice(ctx->device);
+  delete ctx;
+  return MPCG_OK;
+}
+
+const char* mpcg_last_error(mpcg_ctx_t ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+mpcg_status mpcg_device_info(mpcg_ctx_t ctx, int32_t* num_sms, int32_t* ctas_per_sm) {
+  if (!ctx) return MPCG_ERR_INVALID_ARG;
+  if (num_sms) *num_sms = ctx->nsm;
+  if (ctas_per_sm) *ctas_per_sm = ctx->occ;
+  return MPCG_OK;
+}
+
+// ---- matrices ---------------------------------------------------------------------------
+
+mpcg_status mpcg_matrix_create(mpcg_ctx_t ctx, const mpcg_csr* A, mpcg_matrix_t* out, void* stream) {
+  if (!ctx || !A || !out) return fail(ctx, MPCG_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  ctx->err.clear();
+  const int n = A->n;
+  const long long nnz = A->nnz;
+  if (n < 0 || nnz < 0 || nnz >= (1LL << 31)) return fail(ctx, MPCG_ERR_INVALID_ARG, "n = %d, nnz = %lld out of range", n, nnz);
+  if (!A->row_ptr || (nnz > 0 && (!A->col || !A->val)))
+    return fail(ctx, MPCG_ERR_INVALID_ARG, "CSR array pointer is NULL");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  std::unique_ptr<mpcg_matrix_s> M(new mpcg_matrix_s());
+  M->ctx = ctx;
+  const bool dev = is_device_ptr(A->row_ptr);
+  const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const size_t pn = (size_t)nnz + 16;  // padding so that 16-byte rounded ranges stay in bounds
+  CK(ctx, M->rp.ensure(sizeof(int) * ((size_t)n + 1)));
+  CK(ctx, M->ci.ensure(sizeof(int) * pn));
+  CK(ctx, M->v64.ensure(sizeof(double) * pn));
+  CK(ctx, M->v32.ensure(sizeof(float) * pn));
+  CK(ctx, M->vtf.ensure(sizeof(float) * pn));
+  CK(ctx, M->v16.ensure(sizeof(__half) * pn));
+  CK(ctx, M->vbf.ensure(sizeof(__nv_bfloat16) * pn));
+  CK(ctx, M->v16r.ensure(sizeof(__half) * pn));
+  CK(ctx, M->vbfr.ensure(sizeof(__nv_bfloat16) * pn));
+  CK(ctx, M->rscale.ensure(sizeof(float) * ((size_t)n + 1)));
+  M->bytes = (long long)(M->rp.cap + M->ci.cap + M->v64.cap + M->v32.cap + M->vtf.cap + M->v16.cap + M->vbf.cap +
+                         M->v16r.cap + M->vbfr.cap + M->rscale.cap);
+  CK(ctx, cudaMemcpyAsync(M->rp.p, A->row_ptr, sizeof(int) * ((size_t)n + 1), kind, s));
+  CK(ctx, cudaMemsetAsync(M->ci.p, 0, sizeof(int) * pn, s));
+  CK(ctx, cudaMemsetAsync(M->v64.p, 0, sizeof(double) * pn, s));
+  if (nnz > 0) {
+    CK(ctx, cudaMemcpyAsync(M->ci.p, A->col, sizeof(int) * (size_t)nnz, kind, s));
+    CK(ctx, cudaMemcpyAsync(M->v64.p, A->val, sizeof(double) * (size_t)nnz, kind, s));
+  }
+  // Validation on the device.
+  DevBuf flags;
+  CK(ctx, flags.ensure(2 * sizeof(int)));
+  const int init[2] = {0, 0x7fffffff};
+  CK(ctx, cudaMemcpyAsync(flags.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
+  CK(ctx, launch_validate(n, nnz, M->rp.as<int>(), M->ci.as<int>(), M->v64.as<double>(), flags.as<unsigned>(),
+                          flags.as<int>() + 1, s));
+  int hf[2] = {0, 0};
+  CK(ctx, cudaMemcpyAsync(hf, flags.p, sizeof(hf), cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  if (hf[0]) {
+    const unsigned f = (unsigned)hf[0];
+    return fail(ctx, MPCG_ERR_INVALID_ARG, "invalid CSR at row %d:%s%s%s%s%s", hf[1], (f & 1) ? " row_ptr bounds" : "",
+                (f & 2) ? " row_ptr decreasing" : "", (f & 4) ? " column out of range" : "",
+                (f & 8) ? " non-finite value" : "", (f & 16) ? " missing or non-positive diagonal" : "");
+  }
+  DevMatrix& d = M->dm;
+  memset(&d, 0, sizeof(d));
+  d.n = n;
+  d.nnz = nnz;
+  d.rp = M->rp.as<int>();
+  d.ci = M->ci.as<int>();
+  d.v64 = M->v64.as<double>();
+  d.v32 = M->v32.as<float>();
+  d.vtf = M->vtf.as<float>();
+  d.v16 = M->v16.as<__half>();
+  d.vbf = M->vbf.as<__nv_bfloat16>();
+  d.v16r = M->v16r.as<__half>();
+  d.vbfr = M->vbfr.as<__nv_bfloat16>();
+  d.rscale = M->rscale.as<float>();
+  CK(ctx, launch_convert(d, nullptr, M->v32.as<float>(), M->vtf.as<float>(), M->v16.as<__half>(),
+                         M->vbf.as<__nv_bfloat16>(), M->v16r.as<__half>(), M->vbfr.as<__nv_bfloat16>(),
+                         M->rscale.as<float>(), s));
+  // Row statistics (host) and static features of the MLP policy.
+  std::vector<int> hrp((size_t)n + 1);
+  CK(ctx, cudaMemcpyAsync(hrp.data(), M->rp.p, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  double sum = 0, sq = 0, mx = 0;
+  for (int i = 0; i < n; ++i) {
+    const double l = hrp[i + 1] - hrp[i];
+    sum += l;
+    sq += l * l;
+    mx = std::max(mx, l);
+  }
+  M->mean = n ? sum / n : 0.0;
+  M->maxr = mx;
+  M->cv = (n && M->mean > 0) ? std::sqrt(std::max(0.0, sq / n - M->mean * M->mean)) / M->mean : 0.0;
+  // Static features of the MLP policy: log10(n) / 8, mean nnz per row / 64,
+  // log10(max a_ii / min a_ii) / 16, log10(max_i sum_j |a_ij| / a_ii) / 16, and the fraction
+  // of entries outside the fp16 normal range.
+  {
+    DevBuf fb;
+    CK(ctx, fb.ensure(4 * sizeof(unsigned long long)));
+    const unsigned long long init4[4] = {0ull, 0x7ff0000000000000ull, 0ull, 0ull};
+    CK(ctx, cudaMemcpyAsync(fb.p, init4, sizeof(init4), cudaMemcpyHostToDevice, s));
+    CK(ctx, launch_row_features(n, d.rp, d.ci, d.v64, fb.as<unsigned long long>(), s));
+    unsigned long long hfb[4];
+    CK(ctx, cudaMemcpyAsync(hfb, fb.p, sizeof(hfb), cudaMemcpyDeviceToHost, s));
+    CK(ctx, cudaStreamSynchronize(s));
+    double dmax, dmin, gmax;
+    memcpy(&dmax, &hfb[0], 8);
+    memcpy(&dmin, &hfb[1], 8);
+    memcpy(&gmax, &hfb[2], 8);
+    M->feat[0] = n > 0 ? (float)(std::log10((double)n) / 8.0) : 0.f;
+    M->feat[1] = n > 0 ? (float)(((double)nnz / n) / 64.0) : 0.f;
+    M->feat[2] = (dmin > 0 && dmax > 0 && std::isfinite(dmin)) ? (float)(std::log10(dmax / dmin) / 16.0) : 0.f;
+    M->feat[3] = gmax > 0 ? (float)(std::log10(gmax) / 16.0) : 0.f;
+    M->feat[4] = nnz > 0 ? (float)((double)hfb[3] / (double)nnz) : 0.f;
+  }
+  default_schedule(M.get());
+  *out = M.release();
+  return MPCG_OK;
+}
+
+mpcg_status mpcg_matrix_destroy(mpcg_matrix_t A) {
+  if (!A) return MPCG_ERR_INVALID_ARG;
+  cudaSetDevice(A->ctx->device);
+  delete A;
+  return MPCG_OK;
+}
+
+mpcg_status mpcg_matrix_info(mpcg_matrix_t A, mpcg_matrix_stats* info) {
+  if (!A || !info) return MPCG_ERR_INVALID_ARG;
+  memset(info, 0, sizeof(*info));
+  info->n = A->dm.n;
+  info->nnz = A->dm.nnz;
+  info->mean_row_nnz = A->mean;
+  info->max_row_nnz = A->maxr;
+  info->cv_row_nnz = A->cv;
+  for (int f = 0; f < MPCG_NUM_FORMATS; ++f) {
+    info->spmv_sched[f] = A->dm.sched[f];
+    info->spmv_lanes[f] = A->dm.lanes[f];
+  }
+  info->device_bytes = A->bytes;
+  for (int j = 0; j < 5; ++j) info->static_features[j] = A->feat[j];
+  return MPCG_OK;
+}
+
+mpcg_status mpcg_matrix_set_schedule(mpcg_matrix_t A, int32_t fmt, int32_t sched, int32_t lanes) {
+  if (!A) return MPCG_ERR_INVALID_ARG;
+  if (!valid_fmt(fmt) || sched != SCHED_VECTOR || lanes < 1 || lanes > 32 || (lanes & (lanes - 1)))
+    return fail(A->ctx, MPCG_ERR_INVALID_ARG, "unsupported schedule (fmt %d, sched %d, lanes %d)", fmt, sched, lanes);
+  A->dm.sched[fmt] = sched;
+  A->dm.lanes[fmt] = lanes;
+  return MPCG_OK;
+}
+
+mpcg_status mpcg_spmv(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t fmt, const double* x, double* y, int32_t reps,
+                      double* ms_per_rep, void* stream) {
+  if (!ctx || !A || !x || !y) return fail(ctx, MPCG_ERR_INVALID_ARG, "NULL argument");
+  if (!valid_fmt(fmt)) return fail(ctx, MPCG_ERR_INVALID_ARG, "bad format %d", fmt);
+  if (!is_device_ptr(x) || !is_device_ptr(y)) return fail(ctx, MPCG_ERR_INVALID_ARG, "x and y must be device pointers");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = A->dm.n;
+  CK(ctx, ctx->spmv_x.ensure(4 * (size_t)n + 16));
+  CK(ctx, ctx->spmv_q.ensure(8 * (size_t)n + 16));
+  DevSys S;
+  memset(&S, 0, sizeof(S));
+  S.A = A->dm;
+  S.p = const_cast<double*>(x);
+  S.plow = ctx->spmv_x.p;
+  S.q = ctx->spmv_q.p;
+  if (fmt != F64) CK(ctx, launch_to_format(x, S.plow, n, fmt, s));
+  const int grid = ctx->nsm * ctx->occ;
+  if (reps < 1) reps = 1;
+  cudaEvent_t e0, e1;
+  CK(ctx, cudaEventCreate(&e0));
+  CK(ctx, cudaEventCreate(&e1));
+  CK(ctx, launch_spmv_only(S, fmt, grid, s));  // warm-up
+  CK(ctx, cudaEventRecord(e0, s));
+  for (int r = 0; r < reps; ++r) CK(ctx, launch_spmv_only(S, fmt, grid, s));
+  CK(ctx, cudaEventRecord(e1, s));
+  CK(ctx, launch_from_q(S.q, A->dm.rscale, y, n, fmt, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ms_per_rep) *ms_per_rep = ms / reps;
+  return MPCG_OK;
+}
+
+mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, void* stream) {
+  if (!ctx || !A) return fail(ctx, MPCG_ERR_INVALID_ARG, "NULL argument");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = A->dm.n;
+  if (n == 0) return MPCG_OK;
+  DevBuf x, y;
+  CK(ctx, x.ensure(8 * (size_t)n));
+  CK(ctx, y.ensure(8 * (size_t)n));
+  std::vector<double> ones((size_t)n, 1.0);
+  CK(ctx, cudaMemcpyAsync(x.p, ones.data(), 8 * (size_t)n, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  for (int f = 0; f < NFMT; ++f) {
+    int best = A->dm.lanes[f];
+    double best_ms = 1e30;
+    for (int lanes = 1; lanes <= 32; lanes *= 2) {
+      A->dm.lanes[f] = lanes;
+      double ms = 0;
+      mpcg_status st = mpcg_spmv(ctx, A, f, x.as<double>(), y.as<double>(), std::max(1, reps), &ms, stream);
+      if (st != MPCG_OK) return st;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = lanes;
+      }
+    }
+    A->dm.lanes[f] = best;
+    A->dm.sched[f] = SCHED_VECTOR;
+  }
+  return MPCG_OK;
+}
+
+// ---- policies -----------------------------------------------------------------------------
+
+static mpcg_policy_s* new_policy(mpcg_ctx_t ctx, int kind) {
+  mpcg_policy_s* P = new mpcg_policy_s();
+  P->ctx = ctx;
+  P->kind = kind;
+  P->shape = ctx->opt;
+  P->nprec = ctx->opt.nprec;
+  P->S = ctx->opt.b_bins * ctx->opt.r_bins;
+  P->H = ctx->opt.mlp_hidden;
+  return P;
+}
+
+mpcg_status mpcg_policy_fixed(mpcg_ctx_t ctx, const int32_t fmt[4], mpcg_policy_t* out) {
+  if (!ctx || !fmt || !out) return fail(ctx, MPCG_ERR_INVALID_ARG, "NULL argument");
+  for (int j = 0; j < 4; ++j)
+    if (!valid_fmt(fmt[j])) return fail(ctx, MPCG_ERR_INVALID_ARG, "fmt[%d] = %d is not a format code", j, fmt[j]);
+  mpcg_policy_s* P = new_policy(ctx, 0);
+  for (int j = 0; j < 4; ++j) P->fixed[j] = fmt[j];
+  *out = P;
+  return MPCG_OK;
+}
+
+mpcg_status mpcg_policy_schedule(mpcg_ctx_t ctx, const int32_t* fmts, int32_t len, mpcg_policy_t* out) {
+  if (!ctx || !fmts || !out || len < 1) return fail(ctx, MPCG_ERR_INVALID_ARG, "bad schedule arguments");
+  for (long long i = 0; i < 4LL * len; ++i)
+    if (!valid_fmt(fmts[i])) return fail(ctx, MPCG_ERR_INVALID_ARG, "schedule entry %lld = %d is not a format code", i, fmts[i]);
+  cudaSetDevice(ctx->device);
+  std::unique_ptr<mpcg_policy_s> P(new_policy(ctx, 1));
+  CK(ctx, P->sched.ensure(sizeof(int) * 4 * (size_t)len));
+  CK(ctx, cudaMemcpy(P->sched.p, fmts, sizeof(int) * 4 * (size_t)len, cudaMemcpyHostToDevice));
+  P->sched_len = len;
+  *out = P.release();
+  return MPCG_OK;
+}
+
+mpcg_status mpcg_policy_qtable(mpcg_ctx_t ctx, const double* Q, const int32_t* visits, mpcg_policy_t* out) {
+  if (!ctx || !Q || !out) return fail(ctx, MPCG_ERR_INVALID_ARG, "NULL argument");
+  cudaSetDevice(ctx->device);
+  std::unique_ptr<mpcg_policy_s> P(new_policy(ctx, 2));
+  const size_t qn = 4 * (size_t)P->S * P->nprec;
+  CK(ctx, P->Q.ensure(sizeof(double) * qn));
+  CK(ctx, P->visits.ensure(sizeof(int) * 4 * (size_t)P->S));
+  CK(ctx, cudaMemcpy(P->Q.p, Q, sizeof(double) * qn, cudaMemcpyHostToDevice));
+  std::vector<int> v(4 * (size_t)P->S, 1);
+  if (visits) memcpy(v.data(), visits, sizeof(int) * v.size());
+  CK(ctx, cudaMemcpy(P->visits.p, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice));
+  *out = P.release();
+  return MPCG_OK;
+}
+
+int64_t mpcg_mlp_nparams(int32_t H, int32_t nprec) {
+  const int64_t nout = 4LL * nprec;
+  return (int64_t)H * kNFeat + H + (int64_t)H * H + H + nout * H + nout;
+}
+
+mpcg_status mpcg_policy_mlp(mpcg_ctx_t ctx, const float* params, mpcg_policy_t* out) {
+  if (!ctx || !params || !out) return fail(ctx, MPCG_ERR_INVALID_ARG, "NULL argument");
+  cudaSetDevice(ctx->device);
+  std::unique_ptr<mpcg_policy_s> P(new_policy(ctx, 3));
+  const size_t np = (size_t)mpcg_mlp_nparams(P->H, P->nprec);
+  CK(ctx, P->mlp.ensure(sizeof(float) * np));
+  CK(ctx, cudaMemcpy(P->mlp.p, params, sizeof(float) * np, cudaMemcpyHostToDevice));
+  *out = P.release();
+  return MPCG_OK;
+}
+
+mpcg_status mpcg_policy_get_qtable(mpcg_policy_t P, double* Q, int32_t* visits) {
+  if (!P || P->kind != 2) return MPCG_ERR_INVALID_ARG;
+  cudaSetDevice(P->ctx->device);
+  const size_t qn = 4 * (size_t)P->S * P->nprec;
+  if (Q) CK(P->ctx, cudaMemcpy(Q, P->Q.p, sizeof(double) * qn, cudaMemcpyDeviceToHost));
+  if (visits) CK(P->ctx, cudaMemcpy(visits, P->visits.p, sizeof(int) * 4 * (size_t)P->S, cudaMemcpyDeviceToHost));
+  return MPCG_OK;
+}
+
+mpcg_status mpcg_policy_get_mlp(mpcg_policy_t P, float* params) {
+  if (!P || P->kind != 3 || !params) return MPCG_ERR_INVALID_ARG;
+  cudaSetDevice(P->ctx->device);
+  CK(P->ctx, cudaMemcpy(params, P->mlp.p, sizeof(float) * (size_t)mpcg_mlp_nparams(P->H, P->nprec), cudaMemcpyDeviceToHost));
+  return MPCG_OK;
+}
+
+namespace {
+struct BlobHeader {
+  char magic[8];
+  int32_t kind, b_bins, r_bins, t_bin;
+  double eps_min;
+  int32_t nprec, H;
+  int32_t precs[8];
+  double cost[8];
+  int32_t sched_len, fixed[4];
+  int64_t payload;
+};
+}  // namespace
+
+mpcg_status mpcg_policy_save(mpcg_policy_t P, void* blob, size_t* bytes) {
+  if (!P || !bytes) return MPCG_ERR_INVALID_ARG;
+  mpcg_ctx_t ctx = P->ctx;
+  size_t payload = 0;
+  if (P->kind == 1) payload = sizeof(int) * 4 * (size_t)P->sched_len;
+  if (P->kind == 2) payload = sizeof(double) * 4 * (size_t)P->S * P->nprec + sizeof(int) * 4 * (size_t)P->S;
+  if (P->kind == 3) payload = sizeof(float) * (size_t)mpcg_mlp_nparams(P->H, P->nprec);
+  const size_t total = sizeof(BlobHeader) + payload;
+  if (!blob) {
+    *bytes = total;
+    return MPCG_OK;
+  }
+  if (*bytes < total) return fail(ctx, MPCG_ERR_INVALID_ARG, "blob too small: %zu < %zu", *bytes, total);
+  BlobHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, "MPCGPOL1", 8);
+  h.kind = P->kind;
+  h.b_bins = P->shape.b_bins;
+  h.r_bins = P->shape.r_bins;
+  h.t_bin = P->shape.t_bin;
+  h.eps_min = P->shape.eps_min;
+  h.nprec = P->nprec;
+  h.H = P->H;
+  for (int a = 0; a < 8; ++a) {
+    h.precs[a] = P->shape.precs[a];
+    h.cost[a] = P->shape.cost[a];
+  }
+  h.sched_len = P->sched_len;
+  for (int j = 0; j < 4; ++j) h.fixed[j] = P->fixed[j];
+  h.payload = (int64_t)payload;
+  char* o = (char*)blob;
+  memcpy(o, &h, sizeof(h));
+  o += sizeof(h);
+  cudaSetDevice(ctx->device);
+  if (P->kind == 1) CK(ctx, cudaMemcpy(o, P->sched.p, payload, cudaMemcpyDeviceToHost));
+  if (P->kind == 2) {
+    const size_t qb = sizeof(double) * 4 * (size_t)P->S * P->nprec;
+    CK(ctx, cudaMemcpy(o, P->Q.p, qb, cudaMemcpyDeviceToHost));
+    CK(ctx, cudaMemcpy(o + qb, P->visits.p, sizeof(int) * 4 * (size_t)P->S, cudaMemcpyDeviceToHost));
+  }
+  if (P->kind == 3) CK(ctx, cudaMemcpy(o, P->mlp.p, payload, cudaMemcpyDeviceToHost));
+  *bytes = total;
+  return MPCG_OK;
+}
+
+mpcg_status mpcg_policy_load(mpcg_ctx_t ctx, const void* blob, size_t bytes, mpcg_policy_t* out) {
+  if (!ctx || !blob || !out) return fail(ctx, MPCG_ERR_INVALID_ARG, "NULL argument");
+  if (bytes < sizeof(BlobHeader)) return fail(ctx, MPCG_ERR_INVALID_ARG, "blob shorter than its header");
+  BlobHeader h;
+  memcpy(&h, blob, sizeof(h));
+  if (memcmp(h.magic, "MPCGPOL1", 8) != 0) return fail(ctx, MPCG_ERR_INVALID_ARG, "bad policy magic");
+  if (h.payload < 0 || sizeof(BlobHeader) + (size_t)h.payload > bytes) return fail(ctx, MPCG_ERR_INVALID_ARG, "truncated policy blob");
+  const char* o = (const char*)blob + sizeof(h);
+  const mpcg_options& c = ctx->opt;
+  if (h.kind == 0) {
+    return mpcg_policy_fixed(ctx, h.fixed, out);
+  }
+  if (h.kind == 1) {
+    if ((size_t)h.payload != sizeof(int) * 4 * (size_t)h.sched_len) return fail(ctx, MPCG_ERR_INVALID_ARG, "bad schedule payload");
+    return mpcg_policy_schedule(ctx, (const int32_t*)o, h.sched_len, out);
+  }
+  if (h.nprec != c.nprec) return fail(ctx, MPCG_ERR_BAD_POLICY, "policy has %d precisions, context %d", h.nprec, c.nprec);
+  for (int a = 0; a < h.nprec; ++a)
+    if (h.precs[a] != c.precs[a]) return fail(ctx, MPCG_ERR_BAD_POLICY, "precision set differs at %d", a);
+  if (h.kind == 2) {
+    if (h.b_bins != c.b_bins || h.r_bins != c.r_bins) return fail(ctx, MPCG_ERR_BAD_POLICY, "state bins differ");
+    const size_t qb = sizeof(double) * 4 * (size_t)c.b_bins * c.r_bins * c.nprec;
+    if ((size_t)h.payload != qb + sizeof(int) * 4 * (size_t)c.b_bins * c.r_bins) return fail(ctx, MPCG_ERR_INVALID_ARG, "bad table payload");
+    return mpcg_policy_qtable(ctx, (const double*)o, (const int32_t*)(o + qb), out);
+  }
+  if (h.kind == 3) {
+    if (h.H != c.mlp_hidden) return fail(ctx, MPCG_ERR_BAD_POLICY, "hidden width %d differs from %d", h.H, c.mlp_hidden);
+    if ((size_t)h.payload != sizeof(float) * (size_t)mpcg_mlp_nparams(h.H, h.nprec)) return fail(ctx, MPCG_ERR_INVALID_ARG, "bad MLP payload");
+    return mpcg_policy_mlp(ctx, (const float*)o, out);
+  }
+  return fail(ctx, MPCG_ERR_INVALID_ARG, "unknown policy kind %d", h.kind);
+}
+
+mpcg_status mpcg_policy_destroy(mpcg_policy_t P) {
+  if (!P) return MPCG_ERR_INVALID_ARG;
+  cudaSetDevice(P->ctx->device);
+  delete P;
+  return MPCG_OK;
+}
+
+// ---- solves -------------------------------------------------------------------------------
+
+mpcg_status mpcg_solve(mpcg_ctx_t ctx, mpcg_matrix_t A, const double* b, double* x, double tol, int32_t max_iter,
+                       mpcg_policy_t policy, mpcg_result* res, mpcg_iter_record* history, int32_t history_cap,
+                       void* stream) {
+  if (!ctx || !A || !policy || !res) return fail(ctx, MPCG_ERR_INVALID_ARG, "NULL argument");
+  ctx->err.clear();
+  const int n = A->dm.n;
+  if (n > 0 && (!b || !x)) return fail(ctx, MPCG_ERR_INVALID_ARG, "b or x is NULL");
+  if (!(tol >= 0.0) || max_iter < 0) return fail(ctx, MPCG_ERR_INVALID_ARG, "tol must be >= 0 and max_iter >= 0");
+  if (history && history_cap < 0) return fail(ctx, MPCG_ERR_INVALID_ARG, "history_cap < 0");
+  if (A->ctx != ctx || policy->ctx != ctx) return fail(ctx, MPCG_ERR_INVALID_ARG, "objects belong to another context");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  Plan& pl = ctx->plan;
+  const bool bdev = n == 0 || is_device_ptr(b);
+  const bool xdev = n == 0 || is_device_ptr(x);
+  const bool hdev = !history || is_device_ptr(history);
+  const double* bd = b;
+  double* xd = x;
+  if (!bdev) {
+    CK(ctx, pl.bstage.ensure(8 * (size_t)n));
+    CK(ctx, cudaMemcpyAsync(pl.bstage.p, b, 8 * (size_t)n, cudaMemcpyHostToDevice, s));
+    bd = pl.bstage.as<double>();
+  }
+  if (!xdev) {
+    CK(ctx, pl.xstage.ensure(8 * (size_t)n));
+    if (ctx->opt.warm_start) CK(ctx, cudaMemcpyAsync(pl.xstage.p, x, 8 * (size_t)n, cudaMemcpyHostToDevice, s));
+    xd = pl.xstage.as<double>();
+  }
+  mpcg_iter_record* hd = history;
+  if (history && !hdev) {
+    CK(ctx, pl.hstage.ensure(sizeof(mpcg_iter_record) * (size_t)std::max(history_cap, 1)));
+    hd = pl.hstage.as<mpcg_iter_record>();
+  }
+  std::vector<SysIn> in(1);
+  in[0] = SysIn{A, bd, xd, tol, max_iter, hd, history ? history_cap : 0};
+  int force = 0;
+  if (const char* f = getenv("MPCG_FORCE_TEAM")) force = atoi(f);
+  mpcg_status st = build_plan(ctx, pl, in, policy, 0, 0, force, s);
+  if (st != MPCG_OK) return st;
+  st = enqueue_plan(ctx, pl, s);
+  if (st != MPCG_OK) return st;
+  if (!xdev) CK(ctx, cudaMemcpyAsync(x, xd, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
+  if (history && !hdev && history_cap > 0)
+    CK(ctx, cudaMemcpyAsync(history, hd, sizeof(mpcg_iter_record) * (size_t)history_cap, cudaMemcpyDeviceToHost, s));
+  return finish_plan(ctx, pl, res, s);
+}
+
+static mpcg_status collect_batch(mpcg_ctx_t ctx, int32_t nsys, const mpcg_matrix_t* A, const double* const* b,
+                                 double* const* x, const double* tol, const int32_t* max_iter, std::vector<SysIn>& in) {
+  if (nsys < 0 || (nsys > 0 && (!A || !b || !x || !tol || !max_iter))) return fail(ctx, MPCG_ERR_INVALID_ARG, "bad batch arguments");
+  in.resize(nsys);
+  for (int i = 0; i < nsys; ++i) {
+    if (!A[i] || A[i]->ctx != ctx) return fail(ctx, MPCG_ERR_INVALID_ARG, "system %d: bad matrix", i);
+    const int n = A[i]->dm.n;
+    if (n > 0 && (!is_device_ptr(b[i]) || !is_device_ptr(x[i])))
+      return fail(ctx, MPCG_ERR_INVALID_ARG, "system %d: b and x must be device pointers", i);
+    if (!(tol[i] >= 0.0) || max_iter[i] < 0) return fail(ctx, MPCG_ERR_INVALID_ARG, "system %d: bad tol / max_iter", i);
+    in[i] = SysIn{A[i], b[i], x[i], tol[i], max_iter[i], nullptr, 0};
+  }
+  return MPCG_OK;
+}
+
+mpcg_status mpcg_solve_batched(mpcg_ctx_t ctx, int32_t nsys, const mpcg_matrix_t* A, const double* const* b,
+                               double* const* x, const double* tol, const int32_t* max_iter, mpcg_policy_t policy,
+                               mpcg_result* res, void* stream) {
+  if (!ctx || !policy || (nsys > 0 && !res)) return fail(ctx, MPCG_ERR_INVALID_ARG, "NULL argument");
+  ctx->err.clear();
+  cudaSetDevice(ctx->device);
+  std::vector<SysIn> in;
+  mpcg_status st = collect_batch(ctx, nsys, A, b, x, tol, max_iter, in);
+  if (st != MPCG_OK) return st;
+  if (nsys == 0) return MPCG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int force = 0;
+  if (const char* f = getenv("MPCG_FORCE_TEAM")) force = atoi(f);
+  st = build_plan(ctx, ctx->plan, in, policy, 0, 0, force, s);
+  if (st != MPCG_OK) return st;
+  st = enqueue_plan(ctx, ctx->plan, s);
+  if (st != MPCG_OK) return st;
+  return finish_plan(ctx, ctx->plan, res, s);
+}
+
+mpcg_status mpcg_graph_create(mpcg_ctx_t ctx, int32_t nsys, const mpcg_matrix_t* A, const double* const* b,
+                              double* const* x, const double* tol, const int32_t* max_iter, mpcg_policy_t policy,
+                              void* stream, mpcg_graph_t* out) {
+  if (!ctx || !policy || !out || nsys < 1) return fail(ctx, MPCG_ERR_INVALID_ARG, "bad graph arguments");
+  *out = nullptr;
+  ctx->err.clear();
+  cudaSetDevice(ctx->device);
+  std::vector<SysIn> in;
+  mpcg_status st = collect_batch(ctx, nsys, A, b, x, tol, max_iter, in);
+  if (st != MPCG_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::unique_ptr<mpcg_graph_s> g(new mpcg_graph_s());
+  g->ctx = ctx;
+  g->plan.reset(new Plan());
+  st = build_plan(ctx, *g->plan, in, policy, 0, 0, 0, s);
+  if (st != MPCG_OK) return st;
+  cudaStream_t cs;
+  CK(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    st = enqueue_plan(ctx, *g->plan, cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (st == MPCG_OK && e2 != cudaSuccess) st = fail(ctx, MPCG_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e2));
+    g->graph = graph;
+  } else {
+    st = fail(ctx, MPCG_ERR_CUDA, "cudaStreamBeginCapture failed: %s", cudaGetErrorString(e));
+  }
+  cudaStreamDestroy(cs);
+  if (st != MPCG_OK) {
+    if (g->graph) cudaGraphDestroy(g->graph);
+    return st;
+  }
+  CK(ctx, cudaGraphInstantiate(&g->exec, g->graph, 0));
+  *out = g.release();
+  return MPCG_OK;
+}
+
+mpcg_status mpcg_graph_launch(mpcg_graph_t g, void* stream) {
+  if (!g) return MPCG_ERR_INVALID_ARG;
+  cudaSetDevice(g->ctx->device);
+  CK(g->ctx, cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+  return MPCG_OK;
+}
+
+mpcg_status mpcg_graph_results(mpcg_graph_t g, mpcg_result* res, void* stream) {
+  if (!g || !res) return MPCG_ERR_INVALID_ARG;
+  cudaSetDevice(g->ctx->device);
+  return finish_plan(g->ctx, *g->plan, res, (cudaStream_t)stream);
+}
+
+mpcg_status mpcg_graph_destroy(mpcg_graph_t g) {
+  if (!g) return MPCG_ERR_INVALID_ARG;
+  cudaSetDevice(g->ctx->device);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+  return MPCG_OK;
+}
+
+// ---- training -----------------------------------------------------------------------------
+
+mpcg_status mpcg_train_qtable(mpcg_ctx_t ctx, int32_t nsys, const mpcg_matrix_t* A, const double* const* b, double tol,
+                              int32_t t_max, int32_t episodes, mpcg_policy_t inout, int32_t* iters_out, void* stream) {
+  if (!ctx || !inout || nsys < 1 || !A || !b || t_max < 1 || episodes < 1)
+    return fail(ctx, MPCG_ERR_INVALID_ARG, "bad training arguments");
+  if (inout->kind != 2) return fail(ctx, MPCG_ERR_BAD_POLICY, "training needs a QTABLE policy");
+  ctx->err.clear();
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  // Private solution vectors of the episodes (x_0 = 0 each round).
+  size_t xbytes = 0;
+  for (int i = 0; i < nsys; ++i) xbytes += 8 * (size_t)A[i]->dm.n + 256;
+  DevBuf xs;
+  CK(ctx, xs.ensure(xbytes));
+  std::vector<double*> xp(nsys);
+  std::vector<double> tols(nsys, tol);
+  std::vector<int32_t> caps(nsys, t_max);
+  char* w = xs.as<char>();
+  for (int i = 0; i < nsys; ++i) {
+    xp[i] = (double*)w;
+    w += (8 * (size_t)A[i]->dm.n + 255) / 256 * 256;
+  }
+  std::vector<SysIn> in;
+  mpcg_status st = collect_batch(ctx, nsys, A, b, xp.data(), tols.data(), caps.data(), in);
+  if (st != MPCG_OK) return st;
+  Plan& pl = ctx->plan;
+  int force = 0;
+  if (const char* f = getenv("MPCG_FORCE_TEAM")) force = atoi(f);
+  st = build_plan(ctx, pl, in, inout, 1, t_max, force, s);
+  if (st != MPCG_OK) return st;
+  const mpcg_options& o = ctx->opt;
+  const int S = o.b_bins * o.r_bins;
+  const long long qsize = 4LL * S * o.nprec;
+  std::vector<mpcg_result> rr(nsys);
+  for (int e = 1; e <= episodes; ++e) {
+    // epsilon_e = max(eps_floor, eps0 (1 - e / E))  (Section 4.1 with the floor of Section 5)
+    double eps = o.eps0 * (1.0 - (double)e / (double)episodes);
+    if (eps < o.eps_floor) eps = o.eps_floor;
+    pl.L.episode = (unsigned long long)e;
+    pl.L.eps = eps;
+    CK(ctx, launch_qcopy(inout->Q.as<double>(), pl.qpriv.as<double>(), nsys, qsize, s));
+    st = enqueue_plan(ctx, pl, s);
+    if (st != MPCG_OK) return st;
+    CK(ctx, launch_qmerge(inout->Q.as<double>(), inout->visits.as<int>(), pl.trans.as<Transition>(),
+                          pl.st.as<SysState>(), nsys, t_max, S, o.nprec, o.lr, o.gamma, s));
+    if (iters_out || e == episodes) {
+      st = finish_plan(ctx, pl, rr.data(), s);
+      if (st != MPCG_OK) return st;
+      if (iters_out)
+        for (int i = 0; i < nsys; ++i) iters_out[(size_t)(e - 1) * nsys + i] = rr[i].iters;
+    }
+  }
+  return MPCG_OK;
+}
+
+}  // extern "C"

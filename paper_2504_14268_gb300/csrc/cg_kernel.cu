@@ -1,0 +1,853 @@
+// Persistent mixed-precision CG kernel (Section 3 Eq. (1)-(4) with the operation
+// precisions of Section 4.2, Algorithm 2 for inference and Algorithm 1's episode for
+// training).
+//
+// One cooperative launch runs every iteration of every system on the device. The CTAs of
+// the grid are grouped into teams; a team solves its systems one after another. A single
+// large solve uses one team made of the whole grid; a batch of small systems uses many
+// teams, down to one CTA per system. Inside a team the rows of a system are split between
+// the CTAs by nonzeros. Each iteration has three phases separated by team barriers:
+//   A  q = fl_p1(A fl_p1(p)) and the CTA partial of nu = p^T q (op 3, precision p3)
+//   B  r -= alpha q (fp64), partials of ||r||^2 (fp64) and sigma = r^T z (op 4, z = fl_p2(r))
+//   C  x += alpha p, p = z + beta p (fp64) and p's copy in the next product's format
+// At a team barrier the CTA that arrives last reduces the partials of all CTAs of the team
+// in a fixed order (deterministic), evaluates the scalars alpha, beta, rho in fp64, the
+// stopping tests, the policy (state bins of Section 4.1, argmax / epsilon-greedy over the
+// Q-tables, or the MLP Q-function) and, in training, the reward and Q update; then it
+// releases the others. Every wait is bounded; a wait that runs out sets the device status
+// word and the kernel returns.
+#include "internal.h"
+#include "spmv.cuh"
+
+namespace mpcg {
+
+namespace {
+
+enum Mode : int { M_CONT = 0, M_DONE = 1, M_X_THEN_DONE = 2, M_TCHK = 3, M_RESTART = 4 };
+
+struct TeamCtx {
+  int team, rank, size, first;
+  unsigned* bar;
+};
+
+// Values every thread needs after a barrier.
+struct Bcast {
+  double alpha, beta;
+  int k, mode;
+  int fmt[4];
+  int zfmt, pad;
+};
+
+struct Smem {
+  double red[kThreads / 32];
+  Bcast bc;
+  int last;
+  int ok;
+  unsigned gen;
+  int need_action;
+  int flag;
+  int r0, r1;
+  int a_fmt[4], a_act[4], a_expl, a_state;
+  float feat[kNFeat];
+  float h1[kMaxHidden];
+  float h2[kMaxHidden];
+  float out[4 * 8];
+};
+
+// ----------------------------------------------------------------------------------------
+// Reductions
+// ----------------------------------------------------------------------------------------
+
+// Sum over the CTA in a fixed order: xor butterfly inside each warp, then the warp sums in
+// warp order. Every thread returns the same value.
+template <typename T>
+__device__ __forceinline__ T cta_sum(T v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)v;
+  __syncthreads();
+  T s = 0;
+#pragma unroll
+  for (int w = 0; w < kThreads / 32; ++w) s += (T)red[w];
+  return s;
+}
+
+__device__ __forceinline__ void write_partial(const Launch& L, int slot, double v) {
+  if (threadIdx.x == 0) L.partials[(long long)blockIdx.x * kNSlot + slot] = v;
+}
+
+// Sum of one partial slot over the CTAs of the team, in rank order per thread and a fixed
+// tree across threads (deterministic for a given team size). Run by the last CTA.
+__device__ __forceinline__ double team_sum(const Launch& L, const TeamCtx& T, int slot, double* red) {
+  double v = 0.0;
+  for (int c = threadIdx.x; c < T.size; c += kThreads)
+    v += __ldcg(&L.partials[(long long)(T.first + c) * kNSlot + slot]);
+  return cta_sum(v, red);
+}
+
+// ----------------------------------------------------------------------------------------
+// Team barrier
+// ----------------------------------------------------------------------------------------
+
+__device__ __forceinline__ bool err_set(const Launch& L) { return *(volatile unsigned*)L.err != 0u; }
+
+// Arrival: returns true in the CTA that arrives last; that CTA does the team work and then
+// calls team_release. Other CTAs call team_wait.
+__device__ __forceinline__ bool team_arrive(const TeamCtx& T, Smem& sm) {
+  __syncthreads();
+  if (T.size == 1) return true;
+  if (threadIdx.x == 0) {
+    const unsigned g = *(volatile unsigned*)(T.bar + 16);  // generation before our arrival
+    __threadfence();                                      // release this CTA's writes
+    const unsigned old = atomicAdd(T.bar, 1u);
+    sm.last = (old == (unsigned)T.size - 1u) ? 1 : 0;
+    sm.gen = g;
+    if (sm.last) __threadfence();                         // acquire the others' writes
+  }
+  __syncthreads();
+  return sm.last != 0;
+}
+
+__device__ __forceinline__ void team_release(const TeamCtx& T) {
+  __syncthreads();
+  if (T.size > 1 && threadIdx.x == 0) {
+    atomicExch(T.bar, 0u);
+    __threadfence();
+    atomicAdd(T.bar + 16, 1u);
+  }
+  __syncthreads();
+}
+
+// Bounded wait for the generation to move on. Returns false (and sets the status word)
+// when the wait exceeds the time limit or another CTA reported an error.
+__device__ __forceinline__ bool team_wait(const Launch& L, const TeamCtx& T, Smem& sm) {
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const long long t0 = clock64();
+    unsigned spins = 0;
+    while (*(volatile unsigned*)(T.bar + 16) == sm.gen) {
+      if ((++spins & 255u) == 0u) {
+        if (err_set(L)) { ok = 0; break; }
+        if (clock64() - t0 > L.timeout_cycles) {
+          atomicCAS(L.err, 0u, (unsigned)DERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    sm.ok = ok;
+  }
+  __syncthreads();
+  return sm.ok != 0;
+}
+
+// Loads the broadcast values of a system's state into shared memory (after a barrier).
+__device__ __forceinline__ void load_bcast(const SysState* st, Smem& sm) {
+  if (threadIdx.x == 0) {
+    const volatile SysState* v = st;
+    sm.bc.alpha = v->alpha;
+    sm.bc.beta = v->beta;
+    sm.bc.k = v->k;
+    sm.bc.mode = v->mode;
+    sm.bc.zfmt = v->zfmt;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sm.bc.fmt[j] = v->fmt[j];
+  }
+  __syncthreads();
+}
+
+// ----------------------------------------------------------------------------------------
+// Policy (Section 4.1): state, action, reward, Q update
+// ----------------------------------------------------------------------------------------
+
+__device__ __forceinline__ int state_of(const OptView& o, int k, double rho) {
+  int i = k / o.t_width;
+  if (i > o.b_bins - 1) i = o.b_bins - 1;
+  int j = 0;
+  for (int m = 1; m < o.r_bins; ++m) j += (rho <= o.thr[m]) ? 1 : 0;
+  return i * o.r_bins + j;
+}
+
+// Reward of Section 4.1, evaluated with separately rounded operations in the order
+// w1 min(-log10 rho, cap) - w2 c(p_1) - ... - w2 c(p_4) [+ w3].
+__device__ double reward_of(const OptView& o, double rho, const int* act, double tau, bool breakdown) {
+  double acc;
+  if (breakdown) {
+    acc = -o.log_cap;
+  } else {
+    const double l = rho > 0.0 ? -log10(rho) : __longlong_as_double(0x7ff0000000000000ll);
+    acc = l < o.log_cap ? l : o.log_cap;
+  }
+  double r = __dmul_rn(o.w1, acc);
+  for (int j = 0; j < 4; ++j)
+    if (act[j] >= 0 && act[j] < o.nprec) r = __dsub_rn(r, __dmul_rn(o.w2, o.cost[act[j]]));
+  if (!breakdown && rho < tau) r = __dadd_rn(r, o.w3);
+  return r;
+}
+
+__device__ __forceinline__ double row_max(const double* row, int n) {
+  double m = row[0];
+  for (int a = 1; a < n; ++a) m = row[a] > m ? row[a] : m;
+  return m;
+}
+
+__device__ __forceinline__ int row_argmax(const double* row, int n) {
+  int b = 0;
+  for (int a = 1; a < n; ++a)
+    if (row[a] > row[b]) b = a;
+  return b;
+}
+
+// Q_j(s, a_j) += lr (R + gamma max_p Q_j(s', p) - Q_j(s, a_j)), terminal without the max term.
+__device__ void q_update(double* Q, const OptView& o, const Transition& t) {
+  const int S = o.b_bins * o.r_bins;
+  for (int j = 0; j < 4; ++j) {
+    double* row = Q + ((long long)j * S + t.s) * o.nprec;
+    double target = t.reward;
+    if (!t.terminal) target = __dadd_rn(target, __dmul_rn(o.gamma, row_max(Q + ((long long)j * S + t.s_next) * o.nprec, o.nprec)));
+    const double cur = row[t.act[j]];
+    row[t.act[j]] = __dadd_rn(cur, __dmul_rn(o.lr, __dsub_rn(target, cur)));
+  }
+}
+
+// MLP forward pass by the whole CTA, fp32, weights read through the read-only path.
+__device__ void mlp_forward(const float* __restrict__ w, int H, int nout, Smem& sm) {
+  const float* W1 = w;
+  const float* b1 = W1 + H * kNFeat;
+  const float* W2 = b1 + H;
+  const float* b2 = W2 + H * H;
+  const float* W3 = b2 + H;
+  const float* b3 = W3 + nout * H;
+  for (int i = threadIdx.x; i < H; i += kThreads) {
+    float s = __ldg(b1 + i);
+    for (int j = 0; j < kNFeat; ++j) s = fmaf(__ldg(W1 + i * kNFeat + j), sm.feat[j], s);
+    sm.h1[i] = s > 0.f ? s : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < H; i += kThreads) {
+    float s = __ldg(b2 + i);
+    for (int j = 0; j < H; ++j) s = fmaf(__ldg(W2 + i * H + j), sm.h1[j], s);
+    sm.h2[i] = s > 0.f ? s : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nout; i += kThreads) {
+    float s = __ldg(b3 + i);
+    for (int j = 0; j < H; ++j) s = fmaf(__ldg(W3 + i * H + j), sm.h2[j], s);
+    sm.out[i] = s;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ float safe_log10f(double v) { return v > 0.0 ? (float)log10(v) : 0.f; }
+
+// Features of the MLP policy at iteration k (static part from the matrix, dynamic part from
+// the solver state): k / t_bin, -log10 max(rho, eps_min) / 16, one- and eight-step log10
+// residual ratios, log10 |alpha|, log10 |beta| (/ 8), log10 of the last true/recursive
+// residual gap, previous action indices / (nprec - 1).
+__device__ void mlp_features(const Launch& L, const DevSys& S, const SysState* st, int k, Smem& sm) {
+  const OptView& o = L.opt;
+  for (int j = 0; j < 5; ++j) sm.feat[j] = S.feat_static[j];
+  const double rho = st->rho_hist[0];
+  const double rr = rho > o.eps_min ? rho : o.eps_min;
+  sm.feat[5] = (float)((double)k / (double)o.t_bin);
+  sm.feat[6] = (float)(-log10(rr) / 16.0);
+  sm.feat[7] = (st->rho_hist[1] > 0.0 && rho > 0.0) ? (float)log10(rho / st->rho_hist[1]) : 0.f;
+  sm.feat[8] = (st->rho_hist[8] > 0.0 && rho > 0.0) ? (float)(log10(rho / st->rho_hist[8]) / 8.0) : 0.f;
+  sm.feat[9] = st->have_prev ? safe_log10f(fabs(st->alpha_prev)) / 8.f : 0.f;
+  sm.feat[10] = st->have_prev ? safe_log10f(fabs(st->beta_prev)) / 8.f : 0.f;
+  sm.feat[11] = (float)st->gap_log;
+  for (int j = 0; j < 4; ++j)
+    sm.feat[12 + j] = (st->have_prev && o.nprec > 1) ? (float)st->prev_act[j] / (float)(o.nprec - 1) : 0.f;
+}
+
+// Chooses the action of iteration k in state of residual rho. Called by every thread of the
+// CTA that holds the team work; the result is left in sm.a_*.
+__device__ void choose_action(const Launch& L, const DevSys& S, SysState* st, int k, double rho, Smem& sm) {
+  const OptView& o = L.opt;
+  const PolicyView& P = L.pol;
+  const int s = state_of(o, k, rho);
+  if (P.kind == 3) {
+    if (threadIdx.x == 0) mlp_features(L, S, st, k, sm);
+    __syncthreads();
+    mlp_forward(P.mlp, P.H, 4 * o.nprec, sm);
+  }
+  if (threadIdx.x == 0) {
+    int expl = 0;
+    for (int j = 0; j < 4; ++j) {
+      int fmt, act = -1;
+      if (P.kind == 0) {
+        fmt = P.fixed[j];
+      } else if (P.kind == 1) {
+        const int row = k < P.sched_len ? k : P.sched_len - 1;
+        fmt = P.sched[row * 4 + j];
+      } else {
+        if (P.kind == 2) {
+          const double* Qsrc = L.train ? S.Qpriv : P.Q;
+          const double* row = Qsrc + ((long long)j * (o.b_bins * o.r_bins) + s) * o.nprec;
+          act = row_argmax(row, o.nprec);
+          if (!L.train && P.visits && o.fallback_fmt >= 0 && o.fallback_idx >= 0 &&
+              P.visits[j * (o.b_bins * o.r_bins) + s] == 0)
+            act = o.fallback_idx;
+        } else {
+          int b = 0;
+          for (int a = 1; a < o.nprec; ++a)
+            if (sm.out[j * o.nprec + a] > sm.out[j * o.nprec + b]) b = a;
+          act = b;
+        }
+        if (L.train) {
+          U64x4 c;
+          c.v[0] = L.episode;
+          c.v[1] = (unsigned long long)S.lane;
+          c.v[2] = (unsigned long long)k;
+          c.v[3] = (unsigned long long)j;
+          const U64x4 w = philox4x64_10(c, o.seed, 0x6d706367ull);
+          const double u = (double)(w.v[0] >> 11) * 0x1.0p-53;
+          if (u < L.eps) {
+            act = (int)((unsigned)(w.v[1] & 0xffffffffull) % (unsigned)o.nprec);
+            expl = 1;
+          }
+        }
+        fmt = o.precs[act];
+      }
+      if (act < 0)
+        for (int a = 0; a < o.nprec; ++a)
+          if (o.precs[a] == fmt) { act = a; break; }
+      sm.a_fmt[j] = fmt;
+      sm.a_act[j] = act;
+    }
+    sm.a_expl = expl;
+    sm.a_state = s;
+  }
+  __syncthreads();
+}
+
+// ----------------------------------------------------------------------------------------
+// Row phases
+// ----------------------------------------------------------------------------------------
+
+__device__ __forceinline__ void sigma_term(double ri, int p2, int p4, double& sd, float& sf) {
+  const double z = round_fmt(ri, p2);
+  if (p4 == F64) sd = fma(ri, z, sd);
+  else sf = fmaf((float)round_fmt(ri, p4), (float)round_fmt(z, p4), sf);
+}
+
+// r = b - A x in fp64 (residual recomputation), with ||r||^2 and, when p2 >= 0, sigma partials.
+// With copy_p the new residual is also written to p (warm-start initialisation).
+template <int K>
+__device__ void true_res_vec(const DevSys& S, Rows R, int p2, int p4, bool copy_p, double& rr, double& sd,
+                             float& sf) {
+  constexpr int NG = kThreads / K;
+  const int lane = threadIdx.x & (K - 1);
+  const int grp = threadIdx.x / K;
+  const unsigned mask = (K == 32) ? kFull : (((1u << K) - 1u) << ((threadIdx.x & 31) & ~(K - 1)));
+  const int* __restrict__ rp = S.A.rp;
+  const int* __restrict__ ci = S.A.ci;
+  const double* __restrict__ v = S.A.v64;
+  for (int row = R.r0 + grp; row < R.r1; row += NG) {
+    const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
+    double acc = 0.0;
+    for (int e = e0 + lane; e < e1; e += K) acc = fma(__ldg(v + e), S.x[__ldg(ci + e)], acc);
+#pragma unroll
+    for (int o = K / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o);
+    if (lane == 0) {
+      const double ri = __ldg(S.b + row) - acc;
+      S.r[row] = ri;
+      if (copy_p) S.p[row] = ri;
+      rr = fma(ri, ri, rr);
+      if (p2 >= 0) sigma_term(ri, p2, p4, sd, sf);
+    }
+  }
+}
+
+__device__ void true_res_rows(const DevSys& S, Rows R, int p2, int p4, bool copy_p, double& rr, double& sd,
+                              float& sf) {
+  switch (S.A.lanes[F64]) {
+    case 1: true_res_vec<1>(S, R, p2, p4, copy_p, rr, sd, sf); break;
+    case 2: true_res_vec<2>(S, R, p2, p4, copy_p, rr, sd, sf); break;
+    case 4: true_res_vec<4>(S, R, p2, p4, copy_p, rr, sd, sf); break;
+    case 8: true_res_vec<8>(S, R, p2, p4, copy_p, rr, sd, sf); break;
+    case 16: true_res_vec<16>(S, R, p2, p4, copy_p, rr, sd, sf); break;
+    default: true_res_vec<32>(S, R, p2, p4, copy_p, rr, sd, sf); break;
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// Team steps (run by every thread of the CTA that arrived last)
+// ----------------------------------------------------------------------------------------
+
+__device__ void write_record(const DevSys& S, SysState* st, int flags, double rho, double sigma, double beta,
+                             double reward) {
+  const int k = st->k;
+  if (S.hist && k < S.hist_cap) {
+    mpcg_iter_record rec;
+    rec.k = k;
+    rec.state = st->s_cur;
+    for (int j = 0; j < 4; ++j) {
+      rec.fmt[j] = (int8_t)st->fmt[j];
+      rec.act[j] = (int8_t)st->act[j];
+    }
+    rec.rho = rho;
+    rec.nu = st->nu;
+    rec.alpha = st->alpha;
+    rec.sigma = sigma;
+    rec.beta = beta;
+    rec.reward = reward;
+    rec.flags = flags | (st->explored ? 8 : 0);
+    rec.pad = 0;
+    S.hist[k] = rec;
+  }
+}
+
+__device__ void push_transition(const Launch& L, const DevSys& S, SysState* st, int s_next, double R,
+                                int terminal) {
+  if (!L.train) return;
+  Transition t;
+  t.s = st->s_cur;
+  t.s_next = s_next;
+  for (int j = 0; j < 4; ++j) t.act[j] = st->act[j];
+  t.reward = R;
+  t.terminal = terminal;
+  t.pad = 0;
+  if (L.pol.kind == 2 && S.Qpriv) q_update(S.Qpriv, L.opt, t);
+  if (S.trans && st->ntrans < S.trans_cap) S.trans[st->ntrans] = t;
+  st->ntrans += 1;
+}
+
+// Applies a chosen action (sm.a_*) as the action of iteration st->k.
+__device__ void adopt_action(SysState* st, const Smem& sm) {
+  for (int j = 0; j < 4; ++j) {
+    st->fmt[j] = sm.a_fmt[j];
+    st->act[j] = sm.a_act[j];
+    st->counts[j][sm.a_fmt[j] & 7] += 1;
+  }
+  st->explored = sm.a_expl;
+  st->s_cur = sm.a_state;
+}
+
+// After the initial phase: ||b||, rho_0, sigma_0 = r_0^T r_0, action of iteration 0.
+__device__ void step_init(const Launch& L, const DevSys& S, SysState* st, double bb, double rr, Smem& sm) {
+  if (threadIdx.x == 0) {
+    const double bnorm = sqrt(bb);
+    st->bnorm = bnorm;
+    st->rho = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
+    st->sigma = rr;
+    st->k = 0;
+    st->alpha = 0.0;
+    st->beta = 0.0;
+    st->nu = 0.0;
+    st->rho_true = 0.0;
+    for (int h = 0; h < 9; ++h) st->rho_hist[h] = 0.0;
+    st->rho_hist[0] = st->rho;
+    st->alpha_prev = st->beta_prev = st->gap_log = 0.0;
+    st->have_prev = 0;
+    st->n_true = 0;
+    st->ntrans = 0;
+    st->true_known = 0;
+    st->explored = 0;
+    st->s_cur = 0;
+    st->zfmt = F64;
+    for (int j = 0; j < 4; ++j) {
+      st->prev_act[j] = 0;
+      for (int f = 0; f < 8; ++f) st->counts[j][f] = 0;
+    }
+    sm.need_action = 0;
+    if (S.A.n == 0 || bnorm == 0.0) {
+      st->outcome = MPCG_CONVERGED;
+      st->iters = 0;
+      st->rho = 0.0;
+      st->rho_true = 0.0;
+      st->true_known = 1;
+      st->mode = M_DONE;
+    } else if (S.max_iter <= 0) {
+      st->outcome = MPCG_MAX_ITER;
+      st->iters = 0;
+      st->mode = M_DONE;
+    } else {
+      st->mode = M_CONT;
+      sm.need_action = 1;
+    }
+  }
+  __syncthreads();
+  if (sm.need_action) {
+    choose_action(L, S, st, 0, st->rho, sm);
+    if (threadIdx.x == 0) adopt_action(st, sm);
+  }
+}
+
+// After phase A: nu = fl_p3(sum), alpha = sigma / nu, curvature breakdown test.
+__device__ void step_A(const Launch& L, const DevSys& S, SysState* st, double nu_sum) {
+  if (threadIdx.x != 0) return;
+  const int p3 = st->fmt[2];
+  const double nu = (p3 == F64) ? nu_sum : round_fmt(nu_sum, p3);
+  const double alpha = st->sigma / nu;
+  st->nu = nu;
+  st->alpha = alpha;
+  if (!(nu > 0.0) || !isfinite(nu) || !isfinite(alpha)) {
+    const int k = st->k;
+    if (st->rho < S.tol && isfinite(nu)) {
+      // The residual is already below tol (exact solution reached before k >= min_k).
+      st->outcome = MPCG_CONVERGED;
+      const double R = !L.train ? 0.0 : reward_of(L.opt, st->rho, st->act, S.tol, false);
+      write_record(S, st, 1, st->rho, 0.0, 0.0, L.train ? R : 0.0);
+      push_transition(L, S, st, st->s_cur, R, 1);
+    } else {
+      st->outcome = MPCG_BREAKDOWN;
+      const double R = !L.train ? 0.0 : reward_of(L.opt, st->rho, st->act, S.tol, true);
+      write_record(S, st, 2, st->rho, 0.0, 0.0, L.train ? R : 0.0);
+      push_transition(L, S, st, st->s_cur, R, 1);
+    }
+    st->iters = k;
+    st->mode = M_DONE;
+  } else {
+    st->mode = M_CONT;
+  }
+}
+
+// Continues after the residual of iteration k is known (recursive, or replaced when
+// `replaced`): sigma_{k+1}, beta_k (0 after a replacement), reward, next state and action.
+__device__ void continue_step(const Launch& L, const DevSys& S, SysState* st, double rho_new, double sig_sum,
+                              int replaced, Smem& sm) {
+  if (threadIdx.x == 0) {
+    sm.need_action = 0;
+    const int p4 = st->fmt[3];
+    const double sigma_new = (p4 == F64) ? sig_sum : round_fmt(sig_sum, p4);
+    const double beta = replaced ? 0.0 : sigma_new / st->sigma;
+    const int k = st->k;
+    const int flags = replaced ? 4 : 0;
+    if (!isfinite(sigma_new) || !isfinite(beta)) {
+      st->outcome = MPCG_BREAKDOWN;
+      st->iters = k + 1;
+      const double R = !L.train ? 0.0 : reward_of(L.opt, rho_new, st->act, S.tol, true);
+      write_record(S, st, flags | 2, rho_new, sigma_new, beta, L.train ? R : 0.0);
+      push_transition(L, S, st, st->s_cur, R, 1);
+      st->rho = rho_new;
+      st->mode = replaced ? M_DONE : M_X_THEN_DONE;
+    } else {
+      const int s_next = state_of(L.opt, k + 1, rho_new);
+      const double R = !L.train ? 0.0 : reward_of(L.opt, rho_new, st->act, S.tol, false);
+      write_record(S, st, flags, rho_new, sigma_new, beta, L.train ? R : 0.0);
+      push_transition(L, S, st, s_next, R, 0);
+      for (int h = 8; h > 0; --h) st->rho_hist[h] = st->rho_hist[h - 1];
+      st->rho_hist[0] = rho_new;
+      st->alpha_prev = st->alpha;
+      st->beta_prev = beta;
+      st->have_prev = 1;
+      for (int j = 0; j < 4; ++j) st->prev_act[j] = st->act[j] >= 0 ? st->act[j] : 0;
+      st->sigma = sigma_new;
+      st->beta = beta;
+      st->rho = rho_new;
+      st->zfmt = st->fmt[1];
+      st->k = k + 1;
+      st->mode = replaced ? M_RESTART : M_CONT;
+      if (k + 1 >= S.max_iter) {
+        st->outcome = MPCG_MAX_ITER;
+        st->iters = S.max_iter;
+      } else {
+        sm.need_action = 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (sm.need_action) {
+    choose_action(L, S, st, st->k, st->rho, sm);
+    if (threadIdx.x == 0) adopt_action(st, sm);
+  }
+}
+
+// After phase B: rho_{k+1} of the recursive residual, stopping tests.
+__device__ void step_B(const Launch& L, const DevSys& S, SysState* st, double rr, double sig_sum, Smem& sm) {
+  if (threadIdx.x == 0) {
+    sm.need_action = 0;
+    const double rho_rec = sqrt(rr) / st->bnorm;
+    const OptView& o = L.opt;
+    const int k = st->k;
+    const bool check = (o.true_every > 0 && (k + 1) % o.true_every == 0) ||
+                       (o.true_at_conv && rho_rec < S.tol && k >= o.min_k);
+    sm.flag = 0;
+    if (check && isfinite(rho_rec)) {
+      st->rho_true = rho_rec;  // recursive value, kept for the gap feature
+      st->mode = M_TCHK;
+    } else if (!isfinite(rho_rec)) {
+      st->outcome = MPCG_BREAKDOWN;
+      st->iters = k + 1;
+      const double R = !L.train ? 0.0 : reward_of(o, rho_rec, st->act, S.tol, true);
+      write_record(S, st, 2, rho_rec, 0.0, 0.0, L.train ? R : 0.0);
+      push_transition(L, S, st, st->s_cur, R, 1);
+      st->rho = rho_rec;
+      st->mode = M_X_THEN_DONE;
+    } else if (rho_rec < S.tol && k >= o.min_k) {
+      st->outcome = MPCG_CONVERGED;
+      st->iters = k + 1;
+      const double R = !L.train ? 0.0 : reward_of(o, rho_rec, st->act, S.tol, false);
+      write_record(S, st, 1, rho_rec, 0.0, 0.0, L.train ? R : 0.0);
+      push_transition(L, S, st, st->s_cur, R, 1);
+      st->rho = rho_rec;
+      st->mode = M_X_THEN_DONE;
+    } else {
+      sm.flag = 1;
+    }
+  }
+  __syncthreads();
+  if (sm.flag) continue_step(L, S, st, sqrt(rr) / st->bnorm, sig_sum, 0, sm);
+}
+
+// After a residual recomputation inside the iteration (phase T).
+__device__ void step_T(const Launch& L, const DevSys& S, SysState* st, double rr, double sig_sum, Smem& sm) {
+  if (threadIdx.x == 0) {
+    const double rho_t = sqrt(rr) / st->bnorm;
+    const double rho_rec = st->rho_true;
+    st->n_true += 1;
+    st->gap_log = (rho_t > 0.0 && rho_rec > 0.0) ? log10(rho_t / rho_rec) : 0.0;
+    const int k = st->k;
+    sm.flag = 0;
+    if (!isfinite(rho_t)) {
+      st->outcome = MPCG_BREAKDOWN;
+      st->iters = k + 1;
+      const double R = !L.train ? 0.0 : reward_of(L.opt, rho_t, st->act, S.tol, true);
+      write_record(S, st, 4 | 2, rho_t, 0.0, 0.0, L.train ? R : 0.0);
+      push_transition(L, S, st, st->s_cur, R, 1);
+      st->rho = rho_t;
+      st->rho_true = rho_t;
+      st->true_known = 1;
+      st->mode = M_DONE;
+    } else if (rho_t < S.tol && k >= L.opt.min_k) {
+      st->outcome = MPCG_CONVERGED;
+      st->iters = k + 1;
+      const double R = !L.train ? 0.0 : reward_of(L.opt, rho_t, st->act, S.tol, false);
+      write_record(S, st, 4 | 1, rho_t, 0.0, 0.0, L.train ? R : 0.0);
+      push_transition(L, S, st, st->s_cur, R, 1);
+      st->rho = rho_t;
+      st->rho_true = rho_t;
+      st->true_known = 1;
+      st->mode = M_DONE;
+    } else {
+      sm.flag = 1;
+    }
+  }
+  __syncthreads();
+  if (sm.flag) continue_step(L, S, st, sqrt(rr) / st->bnorm, sig_sum, 1, sm);
+}
+
+__device__ void step_final(const Launch& L, const DevSys& S, SysState* st, int sid, double rr) {
+  if (threadIdx.x != 0) return;
+  if (!st->true_known) st->rho_true = st->bnorm > 0.0 ? sqrt(rr) / st->bnorm : 0.0;
+  mpcg_result res;
+  res.outcome = st->outcome;
+  res.iters = st->iters;
+  res.rel_res_rec = st->rho;
+  res.rel_res_true = st->rho_true;
+  res.n_true_checks = st->n_true;
+  res.pad = st->ntrans;
+  for (int j = 0; j < 4; ++j)
+    for (int f = 0; f < 8; ++f) res.action_hist[j][f] = st->counts[j][f];
+  L.res[sid] = res;
+}
+
+// ----------------------------------------------------------------------------------------
+// One system, solved by one team
+// ----------------------------------------------------------------------------------------
+
+// Barrier plus team work: `work` runs in all threads of the last CTA.
+template <class F>
+__device__ __forceinline__ bool team_step(const Launch& L, const TeamCtx& T, SysState* st, Smem& sm, F&& work) {
+  const bool last = team_arrive(T, sm);
+  bool ok = true;
+  if (last) {
+    work();
+    team_release(T);
+  } else {
+    ok = team_wait(L, T, sm);
+  }
+  if (ok) load_bcast(st, sm);
+  return ok;
+}
+
+__device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& sm) {
+  const DevSys& S = L.sys[sid];
+  SysState* st = L.st + sid;
+  const OptView& o = L.opt;
+  if (threadIdx.x == 0) {
+    sm.r0 = part_row(S.A.rp, S.A.n, S.A.nnz, T.rank, T.size);
+    sm.r1 = part_row(S.A.rp, S.A.n, S.A.nnz, T.rank + 1, T.size);
+  }
+  __syncthreads();
+  const Rows R{sm.r0, sm.r1};
+
+  // ---- initialisation: x_0, r_0 = b - A x_0, p_0 = r_0, ||b||^2, sigma_0 = ||r_0||^2 ----
+  {
+    double bb = 0.0, rr = 0.0, sd = 0.0;
+    float sf = 0.f;
+    for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
+      const double bi = __ldg(S.b + i);
+      bb = fma(bi, bi, bb);
+      if (!o.warm_start) {
+        S.x[i] = 0.0;
+        S.r[i] = bi;
+        S.p[i] = bi;
+        rr = fma(bi, bi, rr);
+      }
+    }
+    if (o.warm_start) true_res_rows(S, R, -1, -1, true, rr, sd, sf);
+    bb = cta_sum(bb, sm.red);
+    rr = cta_sum(rr, sm.red);
+    write_partial(L, 0, bb);
+    write_partial(L, 1, rr);
+    if (!team_step(L, T, st, sm, [&] {
+          const double tb = team_sum(L, T, 0, sm.red);
+          const double tr = team_sum(L, T, 1, sm.red);
+          step_init(L, S, st, tb, tr, sm);
+        }))
+      return false;
+  }
+
+  if (sm.bc.mode == M_CONT) {
+    // p in the format of the first product
+    {
+      const int p1 = sm.bc.fmt[0];
+      if (p1 != F64)
+        for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) store_fmt(S.plow, i, S.p[i], p1);
+      if (!team_step(L, T, st, sm, [] {})) return false;
+    }
+    while (true) {
+      // ---- phase A: q = fl_p1(A p), nu partials ----
+      {
+        double nd = 0.0;
+        float nf = 0.f;
+        const int p1 = sm.bc.fmt[0], p3 = sm.bc.fmt[2];
+        spmv_rows(S, R, p1, p3, nd, nf);
+        const double part = (p3 == F64) ? cta_sum(nd, sm.red) : (double)cta_sum(nf, sm.red);
+        write_partial(L, 0, part);
+        if (!team_step(L, T, st, sm, [&] { step_A(L, S, st, team_sum(L, T, 0, sm.red)); })) return false;
+        if (sm.bc.mode != M_CONT) break;
+      }
+      // ---- phase B: r -= alpha q, ||r||^2, sigma partials ----
+      {
+        const double alpha = sm.bc.alpha;
+        const int p1 = sm.bc.fmt[0], p2 = sm.bc.fmt[1], p4 = sm.bc.fmt[3];
+        const bool scaled = row_scaled(p1);
+        double rr = 0.0, sd = 0.0;
+        float sf = 0.f;
+        for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
+          double qv = load_fmt(S.q, i, p1);
+          if (scaled) qv *= (double)__ldg(S.A.rscale + i);
+          const double ri = fma(-alpha, qv, S.r[i]);
+          S.r[i] = ri;
+          rr = fma(ri, ri, rr);
+          sigma_term(ri, p2, p4, sd, sf);
+        }
+        rr = cta_sum(rr, sm.red);
+        const double sp = (p4 == F64) ? cta_sum(sd, sm.red) : (double)cta_sum(sf, sm.red);
+        write_partial(L, 0, rr);
+        write_partial(L, 1, sp);
+        if (!team_step(L, T, st, sm, [&] {
+              const double trr = team_sum(L, T, 0, sm.red);
+              const double tsg = team_sum(L, T, 1, sm.red);
+              step_B(L, S, st, trr, tsg, sm);
+            }))
+          return false;
+      }
+      const int mode = sm.bc.mode;
+      if (mode == M_CONT) {
+        // ---- phase C: x += alpha p; p = z + beta p; p in the next product's format ----
+        const double alpha = sm.bc.alpha, beta = sm.bc.beta;
+        // bc.fmt holds the next action; z = fl_p2(r) uses the finished iteration's p2.
+        const int p1n = sm.bc.fmt[0];
+        const int p2 = sm.bc.zfmt;
+        for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
+          const double pi = S.p[i];
+          S.x[i] = fma(alpha, pi, S.x[i]);
+          const double pn = fma(beta, pi, round_fmt(S.r[i], p2));
+          S.p[i] = pn;
+          if (p1n != F64) store_fmt(S.plow, i, pn, p1n);
+        }
+        if (!team_step(L, T, st, sm, [] {})) return false;
+        if (sm.bc.k >= S.max_iter) break;
+        continue;
+      }
+      if (mode == M_DONE) break;
+      // ---- phase X: x += alpha p ----
+      {
+        const double alpha = sm.bc.alpha;
+        for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) S.x[i] = fma(alpha, S.p[i], S.x[i]);
+        if (!team_step(L, T, st, sm, [] {})) return false;
+      }
+      if (mode == M_X_THEN_DONE) break;
+      // ---- phase T: r = b - A x (fp64), ||r||^2, sigma partials ----
+      {
+        const int p2 = sm.bc.fmt[1], p4 = sm.bc.fmt[3];
+        double rr = 0.0, sd = 0.0;
+        float sf = 0.f;
+        true_res_rows(S, R, p2, p4, false, rr, sd, sf);
+        rr = cta_sum(rr, sm.red);
+        const double sp = (p4 == F64) ? cta_sum(sd, sm.red) : (double)cta_sum(sf, sm.red);
+        write_partial(L, 0, rr);
+        write_partial(L, 1, sp);
+        if (!team_step(L, T, st, sm, [&] {
+              const double trr = team_sum(L, T, 0, sm.red);
+              const double tsg = team_sum(L, T, 1, sm.red);
+              step_T(L, S, st, trr, tsg, sm);
+            }))
+          return false;
+      }
+      if (sm.bc.mode == M_RESTART) {
+        // p = z (beta = 0) after the replacement; x is already up to date.
+        const int p1n = sm.bc.fmt[0];
+        const int p2 = sm.bc.zfmt;
+        for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
+          const double pn = round_fmt(S.r[i], p2);
+          S.p[i] = pn;
+          if (p1n != F64) store_fmt(S.plow, i, pn, p1n);
+        }
+        if (!team_step(L, T, st, sm, [] {})) return false;
+        if (sm.bc.k >= S.max_iter) break;
+        continue;
+      }
+      break;
+    }
+  }
+
+  // ---- final: ||b - A x|| in fp64 unless already known ----
+  {
+    double rr = 0.0, sd = 0.0;
+    float sf = 0.f;
+    int known = 0;
+    if (threadIdx.x == 0) known = *(volatile int*)&st->true_known;
+    known = __syncthreads_or(known);
+    if (!known) true_res_rows(S, R, -1, -1, false, rr, sd, sf);
+    rr = cta_sum(rr, sm.red);
+    write_partial(L, 0, rr);
+    if (!team_step(L, T, st, sm, [&] { step_final(L, S, st, sid, team_sum(L, T, 0, sm.red)); })) return false;
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kThreads) cg_persistent(const Launch L) {
+  __shared__ Smem sm;
+  TeamCtx T;
+  T.team = L.cta_team[blockIdx.x];
+  T.rank = L.cta_rank[blockIdx.x];
+  T.size = L.team_size[T.team];
+  T.first = L.team_first[T.team];
+  T.bar = L.bars + (long long)T.team * kBarStride;
+  for (int i = L.team_sys_off[T.team]; i < L.team_sys_off[T.team + 1]; ++i) {
+    if (!solve_system(L, T, L.team_sys[i], sm)) return;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_cg(const Launch& L, int grid, size_t smem, cudaStream_t s) {
+  void* args[] = {(void*)&L};
+  return cudaLaunchCooperativeKernel((const void*)cg_persistent, dim3(grid), dim3(kThreads), args, smem, s);
+}
+
+cudaError_t cg_occupancy(int* blocks_per_sm, size_t smem) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, cg_persistent, kThreads, smem);
+}
+
+size_t cg_static_smem() { return sizeof(Smem); }
+
+}  // namespace mpcg

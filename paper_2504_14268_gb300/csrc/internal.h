@@ -1,0 +1,167 @@
+// Internal layouts shared by the host runtime (api.cu) and the kernels (cg_kernel.cu,
+// setup_kernels.cu). Not part of the C ABI.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mpcg.h"
+#include "formats.cuh"
+
+namespace mpcg {
+
+constexpr int kThreads = 256;       // threads per CTA of every kernel
+constexpr int kMaxRBins = 32;       // residual bins supported by the device policy
+constexpr int kMaxBBins = 64;       // iteration bins
+constexpr int kNSlot = 4;           // partial sums per CTA and phase
+constexpr int kNFeat = 16;          // MLP input features
+constexpr int kMaxHidden = 128;     // MLP hidden width bound
+constexpr int kBarStride = 32;      // uint32 words between team barriers (128 bytes)
+
+enum Sched : int { SCHED_VECTOR = 0, SCHED_STREAM = 1 };
+
+// Device view of a matrix: CSR structure plus the value copy of every format.
+struct DevMatrix {
+  int n;
+  int pad0;
+  long long nnz;
+  const int* rp;
+  const int* ci;
+  const double* v64;
+  const float* v32;
+  const float* vtf;
+  const __half* v16;
+  const __nv_bfloat16* vbf;
+  const __half* v16r;
+  const __nv_bfloat16* vbfr;
+  const float* rscale;      // s_i of the row-scaled formats (powers of two)
+  int sched[8];             // SpMV schedule per format
+  int lanes[8];             // lanes per row per format
+  int tile_rows[8];         // stream schedule: rows per shared-memory tile
+  int tile_bytes[8];        // stream schedule: bytes of one tile buffer (values + columns)
+};
+
+// One transition of an exploration episode (Algorithm 1), recorded for the end-of-round merge.
+struct Transition {
+  int s, s_next;
+  int act[4];
+  double reward;
+  int terminal, pad;
+};
+
+// One system of a launch: matrix, right-hand side, solution, work vectors, limits.
+struct DevSys {
+  DevMatrix A;
+  const double* b;
+  double* x;
+  double* r;
+  double* p;
+  void* plow;               // p in the product's input format (fp32 / tf32 / fp16 / bf16)
+  void* q;                  // q = A p in the product's format
+  double tol;
+  int max_iter;
+  int lane;                 // index of the system in its batch
+  mpcg_iter_record* hist;   // device array or nullptr
+  int hist_cap;
+  int pad1;
+  double* Qpriv;            // training: lane-private copy of the tables
+  Transition* trans;        // training: transitions of this lane's episode
+  int trans_cap;
+  int pad2;
+  float feat_static[5];     // MLP static features of the matrix
+  int pad3;
+};
+
+// Per-system state that persists across phases; written only by the CTA that arrives
+// last at a team barrier, read by every CTA of the team after the barrier.
+struct SysState {
+  double alpha, beta, nu, sigma, rho, bnorm, rho_true;
+  double rho_hist[9];
+  double alpha_prev, beta_prev, gap_log;
+  double rew;
+  int k, mode, outcome, iters;
+  int fmt[4];
+  int act[4];
+  int prev_act[4];
+  int have_prev, n_true, ntrans, true_known;
+  int explored, s_cur;      // exploration flag and state index of the current iteration
+  int zfmt, pad;            // p2 of the iteration whose direction update is pending
+  long long counts[4][8];
+};
+
+struct PolicyView {
+  int kind;                 // 0 fixed, 1 schedule, 2 qtable, 3 mlp
+  int fixed[4];
+  int sched_len;
+  const int* sched;         // [len][4] format codes
+  const double* Q;          // [4][S][nprec]
+  const int* visits;        // [4][S] or nullptr
+  const float* mlp;         // flat parameters
+  int H;
+  int pad;
+};
+
+struct OptView {
+  int b_bins, r_bins, t_width, min_k;
+  int nprec;
+  int precs[8];
+  double cost[8];
+  double thr[kMaxRBins];    // residual-bin thresholds theta_m = 10^(-m delta), m = 1..r-1
+  double log_cap;           // -log10(eps_min)
+  double eps_min;
+  double w1, w2, w3, lr, gamma;
+  unsigned long long seed;
+  int fallback_fmt;         // unvisited-row action (format code), -1 = argmax
+  int fallback_idx;         // its index in precs (-1 if absent)
+  int true_every, true_at_conv, warm_start, t_bin;
+};
+
+// Arguments of one launch of the persistent kernel.
+struct Launch {
+  const DevSys* sys;
+  SysState* st;
+  int nsys;
+  int nteams;
+  const int* cta_team;      // [grid] team of each CTA
+  const int* cta_rank;      // [grid] rank of each CTA inside its team
+  const int* team_size;     // [nteams]
+  const int* team_first;    // [nteams] first CTA of the team
+  const int* team_sys_off;  // [nteams + 1] offsets into team_sys
+  const int* team_sys;      // systems of each team, solved in this order
+  unsigned* bars;           // [nteams * kBarStride]: count at +0, generation at +16
+  double* partials;         // [grid * kNSlot]
+  mpcg_result* res;         // [nsys]
+  unsigned* err;            // device status word (0 = fine)
+  PolicyView pol;
+  OptView opt;
+  int train;                // 1: epsilon-greedy episode with online private updates
+  int pad;
+  unsigned long long episode;
+  double eps;
+  long long timeout_cycles;
+};
+
+// Device status word values.
+enum DevErr : unsigned { DERR_NONE = 0, DERR_TIMEOUT = 1, DERR_BAD_STATE = 2 };
+
+// Host entry points of the kernels (cg_kernel.cu, setup_kernels.cu).
+cudaError_t launch_cg(const Launch& L, int grid, size_t smem, cudaStream_t s);
+cudaError_t cg_occupancy(int* blocks_per_sm, size_t smem);
+size_t cg_static_smem();
+cudaError_t launch_validate(int n, long long nnz, const int* rp, const int* ci, const double* v,
+                            unsigned* flags, int* bad_row, cudaStream_t s);
+cudaError_t launch_convert(const DevMatrix& A, double* v64w, float* v32, float* vtf, __half* v16,
+                           __nv_bfloat16* vbf, __half* v16r, __nv_bfloat16* vbfr, float* rscale,
+                           cudaStream_t s);
+cudaError_t launch_row_features(int n, const int* rp, const int* ci, const double* v, unsigned long long* out,
+                                cudaStream_t s);
+cudaError_t launch_to_format(const double* x, void* xlow, int n, int f, cudaStream_t s);
+cudaError_t launch_from_q(const void* q, const float* rscale, double* y, int n, int f, cudaStream_t s);
+cudaError_t launch_spmv_only(const DevSys& S, int fmt, int grid, cudaStream_t s);
+cudaError_t launch_qcopy(const double* Q, double* Qpriv, int nlanes, long long qsize, cudaStream_t s);
+cudaError_t launch_qmerge(double* Q, int* visits, const Transition* trans, const SysState* st, int nlanes, int cap,
+                          int S, int nprec, double lr, double gamma, cudaStream_t s);
+
+}  // namespace mpcg

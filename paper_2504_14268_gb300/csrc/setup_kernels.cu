@@ -1,0 +1,271 @@
+// Setup and auxiliary kernels: CSR validation, the value copies of every format (one
+// rounding from fp64 each), the standalone product used for timing and autotuning, and
+// the Q-table copy and end-of-round merge of the batched training reading of Algorithm 1.
+#include "internal.h"
+#include "spmv.cuh"
+
+namespace mpcg {
+
+namespace {
+
+enum : unsigned {
+  VF_ROWPTR = 1u,   // row_ptr[0] != 0, row_ptr[n] != nnz, or an entry outside [0, nnz]
+  VF_ORDER = 2u,    // row_ptr decreasing
+  VF_COL = 4u,      // column index outside [0, n)
+  VF_VALUE = 8u,    // non-finite value
+  VF_DIAG = 16u,    // diagonal entry missing or not positive
+};
+
+__global__ void validate_rowptr(int n, long long nnz, const int* __restrict__ rp, unsigned* flags, int* bad_row) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i <= n; i += (long long)gridDim.x * blockDim.x) {
+    const int v = rp[i];
+    unsigned f = 0;
+    if (v < 0 || (long long)v > nnz) f |= VF_ROWPTR;
+    if (i == 0 && v != 0) f |= VF_ROWPTR;
+    if (i == n && (long long)v != nnz) f |= VF_ROWPTR;
+    if (i < n && rp[i + 1] < v) f |= VF_ORDER;
+    if (f) {
+      atomicOr(flags, f);
+      atomicMin(bad_row, (int)i);
+    }
+  }
+}
+
+// One warp per row; runs only after validate_rowptr found row_ptr consistent.
+__global__ void validate_rows(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                              const double* __restrict__ v, unsigned* flags, int* bad_row) {
+  const int lane = threadIdx.x & 31;
+  for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; row < n;
+       row += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const int e0 = rp[row], e1 = rp[row + 1];
+    unsigned f = 0;
+    int diag_ok = 0;
+    for (int e = e0 + lane; e < e1; e += 32) {
+      const int c = ci[e];
+      const double a = v[e];
+      if (c < 0 || c >= n) f |= VF_COL;
+      if (!isfinite(a)) f |= VF_VALUE;
+      if (c == row && a > 0.0) diag_ok = 1;
+    }
+    diag_ok = __any_sync(kFull, diag_ok);
+    f = __reduce_or_sync(kFull, f);
+    if (!diag_ok) f |= VF_DIAG;
+    if (f && lane == 0) {
+      atomicOr(flags, f);
+      atomicMin(bad_row, (int)row);
+    }
+  }
+}
+
+// One warp per row: row scale s_i = 2^floor(log2 max_j |a_ij|) (clamped to the fp32
+// exponent range), then every copy rounded once from fp64.
+__global__ void convert_values(int n, const int* __restrict__ rp, const double* __restrict__ v64, float* v32,
+                               float* vtf, __half* v16, __nv_bfloat16* vbf, __half* v16r, __nv_bfloat16* vbfr,
+                               float* rscale) {
+  const int lane = threadIdx.x & 31;
+  for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; row < n;
+       row += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const int e0 = rp[row], e1 = rp[row + 1];
+    double m = 0.0;
+    for (int e = e0 + lane; e < e1; e += 32) m = fmax(m, fabs(v64[e]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
+    int ex = 0;
+    if (m > 0.0) ex = (int)(((unsigned long long)__double_as_longlong(m) >> 52) & 0x7ff) - 1023;
+    if (ex < -126) ex = -126;
+    if (ex > 127) ex = 127;
+    const double sinv = __longlong_as_double((long long)((unsigned long long)(1023 - ex) << 52));
+    if (lane == 0) rscale[row] = (float)__longlong_as_double((long long)((unsigned long long)(1023 + ex) << 52));
+    for (int e = e0 + lane; e < e1; e += 32) {
+      const double a = v64[e];
+      v32[e] = (float)round_to<24, -126, 127>(a);
+      vtf[e] = (float)round_to<11, -126, 127>(a);
+      v16[e] = __double2half(round_to<11, -14, 15>(a));
+      vbf[e] = __double2bfloat16(round_to<8, -126, 127>(a));
+      const double as = a * sinv;
+      v16r[e] = __double2half(round_to<11, -14, 15>(as));
+      vbfr[e] = __double2bfloat16(round_to<8, -126, 127>(as));
+    }
+  }
+}
+
+// Row statistics behind the MLP policy's static features: largest and smallest diagonal,
+// largest Gershgorin ratio sum_j |a_ij| / a_ii, and the count of entries outside the fp16
+// normal range [2^-14, 65504]. Positive doubles order like their bit patterns, so the
+// maxima and minima use integer atomics. out: [0] max diag, [1] min diag, [2] max ratio
+// (as bit patterns), [3] count.
+__global__ void row_features(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                             const double* __restrict__ v, unsigned long long* out) {
+  const int lane = threadIdx.x & 31;
+  for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; row < n;
+       row += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const int e0 = rp[row], e1 = rp[row + 1];
+    double d = 0.0, rs = 0.0;
+    unsigned long long cnt = 0;
+    for (int e = e0 + lane; e < e1; e += 32) {
+      const double a = fabs(v[e]);
+      rs += a;
+      if (ci[e] == row) d = v[e];
+      if (a != 0.0 && (a < 0x1.0p-14 || a > 65504.0)) ++cnt;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      rs += __shfl_xor_sync(kFull, rs, o);
+      d += __shfl_xor_sync(kFull, d, o);
+      cnt += __shfl_xor_sync(kFull, cnt, o);
+    }
+    if (lane == 0) {
+      if (d > 0.0) {
+        atomicMax(out + 0, (unsigned long long)__double_as_longlong(d));
+        atomicMin(out + 1, (unsigned long long)__double_as_longlong(d));
+        atomicMax(out + 2, (unsigned long long)__double_as_longlong(rs / d));
+      }
+      if (cnt) atomicAdd(out + 3, cnt);
+    }
+  }
+}
+
+// x (fp64) -> fl_f(x) stored in format f.
+__global__ void to_format(const double* __restrict__ x, void* xlow, int n, int f) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    store_fmt(xlow, i, x[i], f);
+}
+
+// y = q (stored in format f) as fp64, times the row scale for the row-scaled formats.
+__global__ void from_q(const void* q, const float* __restrict__ rscale, double* y, int n, int f) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v = load_fmt(q, i, f);
+    if (row_scaled(f)) v *= (double)rscale[i];
+    y[i] = v;
+  }
+}
+
+// Standalone product with the same per-CTA row split and row code as the solver.
+__global__ void __launch_bounds__(kThreads) spmv_standalone(const DevSys S, int fmt) {
+  __shared__ int r01[2];
+  if (threadIdx.x == 0) {
+    r01[0] = part_row(S.A.rp, S.A.n, S.A.nnz, blockIdx.x, gridDim.x);
+    r01[1] = part_row(S.A.rp, S.A.n, S.A.nnz, blockIdx.x + 1, gridDim.x);
+  }
+  __syncthreads();
+  double nd = 0.0;
+  float nf = 0.f;
+  spmv_rows(S, Rows{r01[0], r01[1]}, fmt, -1, nd, nf);
+}
+
+__global__ void qcopy_kernel(const double* __restrict__ Q, double* Qpriv, int nlanes, long long qsize) {
+  const long long total = qsize * nlanes;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
+    Qpriv[i] = Q[i % qsize];
+}
+
+// End-of-round merge: replays every recorded transition (lane 0..B-1, then iteration
+// order) onto the shared tables with the Q-learning update of Section 4.1. The four
+// operation tables are independent, so one thread per table replays them in that order.
+__global__ void qmerge_kernel(double* Q, int* visits, const Transition* __restrict__ trans,
+                              const SysState* __restrict__ st, int nlanes, int cap, int S, int nprec, double lr,
+                              double gamma, int use_smem) {
+  extern __shared__ double tab[];
+  const long long tsize = (long long)S * nprec;
+  double* T = use_smem ? tab : Q;
+  if (use_smem) {
+    for (long long i = threadIdx.x; i < 4 * tsize; i += blockDim.x) tab[i] = Q[i];
+    __syncthreads();
+  }
+  const int j = threadIdx.x >> 5;
+  if (j < 4 && (threadIdx.x & 31) == 0) {
+    double* Tj = T + j * tsize;
+    for (int l = 0; l < nlanes; ++l) {
+      int nt = st[l].ntrans;
+      if (nt > cap) nt = cap;
+      for (int t = 0; t < nt; ++t) {
+        const Transition tr = trans[(long long)l * cap + t];
+        double* row = Tj + (long long)tr.s * nprec;
+        double target = tr.reward;
+        if (!tr.terminal) {
+          const double* nx = Tj + (long long)tr.s_next * nprec;
+          double mx = nx[0];
+          for (int a = 1; a < nprec; ++a) mx = nx[a] > mx ? nx[a] : mx;
+          target = __dadd_rn(target, __dmul_rn(gamma, mx));
+        }
+        const int a = tr.act[j];
+        const double cur = row[a];
+        row[a] = __dadd_rn(cur, __dmul_rn(lr, __dsub_rn(target, cur)));
+        visits[j * S + tr.s] += 1;
+      }
+    }
+  }
+  if (use_smem) {
+    __syncthreads();
+    for (long long i = threadIdx.x; i < 4 * tsize; i += blockDim.x) Q[i] = tab[i];
+  }
+}
+
+int grid_for(long long work, int per_block) {
+  long long g = (work + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > 152 * 32) g = 152 * 32;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_validate(int n, long long nnz, const int* rp, const int* ci, const double* v, unsigned* flags,
+                            int* bad_row, cudaStream_t s) {
+  validate_rowptr<<<grid_for((long long)n + 1, kThreads), kThreads, 0, s>>>(n, nnz, rp, flags, bad_row);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  unsigned hf = 0;
+  e = cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess || hf) return e;
+  if (n > 0) validate_rows<<<grid_for((long long)n * 32, kThreads), kThreads, 0, s>>>(n, rp, ci, v, flags, bad_row);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const DevMatrix& A, double*, float* v32, float* vtf, __half* v16, __nv_bfloat16* vbf,
+                           __half* v16r, __nv_bfloat16* vbfr, float* rscale, cudaStream_t s) {
+  if (A.n == 0) return cudaSuccess;
+  convert_values<<<grid_for((long long)A.n * 32, kThreads), kThreads, 0, s>>>(A.n, A.rp, A.v64, v32, vtf, v16, vbf,
+                                                                             v16r, vbfr, rscale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_features(int n, const int* rp, const int* ci, const double* v, unsigned long long* out,
+                                cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  row_features<<<grid_for((long long)n * 32, kThreads), kThreads, 0, s>>>(n, rp, ci, v, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_format(const double* x, void* xlow, int n, int f, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  to_format<<<grid_for(n, kThreads), kThreads, 0, s>>>(x, xlow, n, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_q(const void* q, const float* rscale, double* y, int n, int f, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  from_q<<<grid_for(n, kThreads), kThreads, 0, s>>>(q, rscale, y, n, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spmv_only(const DevSys& S, int fmt, int grid, cudaStream_t s) {
+  if (S.A.n == 0) return cudaSuccess;
+  spmv_standalone<<<grid, kThreads, 0, s>>>(S, fmt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qcopy(const double* Q, double* Qpriv, int nlanes, long long qsize, cudaStream_t s) {
+  qcopy_kernel<<<grid_for(qsize * nlanes, kThreads), kThreads, 0, s>>>(Q, Qpriv, nlanes, qsize);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qmerge(double* Q, int* visits, const Transition* trans, const SysState* st, int nlanes, int cap,
+                          int S, int nprec, double lr, double gamma, cudaStream_t s) {
+  const size_t bytes = sizeof(double) * 4 * (size_t)S * nprec;
+  const int use_smem = bytes <= 48 * 1024 ? 1 : 0;
+  qmerge_kernel<<<1, 128, use_smem ? bytes : 0, s>>>(Q, visits, trans, st, nlanes, cap, S, nprec, lr, gamma, use_smem);
+  return cudaGetLastError();
+}
+
+}  // namespace mpcg
