@@ -122,15 +122,19 @@ typedef struct {
   int64_t action_hist[MPCG_NUM_OPS][MPCG_MAX_PREC]; /* iterations per (op, format)       */
 } mpcg_result;
 
-/* One record per iteration k (64 bytes). rho is rho_{k+1} after the iteration (the true
+/* One record per iteration k (80 bytes). rho is rho_{k+1} after the iteration (the true
  * relative residual when r was replaced). flags: bit0 converged here, bit1 breakdown here,
- * bit2 r replaced by b - A x, bit3 an operation explored (training). */
+ * bit2 r replaced by b - A x, bit3 an operation explored (training). ns_a / ns_b / ns_c:
+ * device time (globaltimer, ns) from the previous team barrier to the barriers that close
+ * phase A (product and nu), phase B (residual update, norms) and phase C (x and p update)
+ * of the iteration, including the barrier itself. */
 typedef struct {
   int32_t k, state;
   int8_t fmt[4];
   int8_t act[4];
   double rho, nu, alpha, sigma, beta, reward;
-  int32_t flags, pad;
+  int32_t flags;
+  uint32_t ns_a, ns_b, ns_c;
 } mpcg_iter_record;
 
 /* Matrix statistics filled by mpcg_matrix_info. */

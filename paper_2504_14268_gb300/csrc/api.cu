@@ -84,7 +84,8 @@ struct mpcg_ctx_s {
 struct mpcg_matrix_s {
   mpcg_ctx_t ctx = nullptr;
   DevMatrix dm;
-  DevBuf rp, ci, v64, v32, vtf, v16, vbf, v16r, vbfr, rscale;
+  DevBuf rp, ci, v64, v32, vtf, v16, vbf, v16r, vbfr, rexp;
+  int device = 0;
   double mean = 0, maxr = 0, cv = 0;
   float feat[5] = {0, 0, 0, 0, 0};
   long long bytes = 0;
@@ -97,11 +98,13 @@ struct mpcg_policy_s {
   int sched_len = 0;
   DevBuf sched, Q, visits, mlp;
   int S = 0, nprec = 0, H = 0;
+  int device = 0;
   mpcg_options shape;
 };
 
 struct mpcg_graph_s {
   mpcg_ctx_t ctx = nullptr;
+  int device = 0;
   std::unique_ptr<Plan> plan;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -414,6 +417,7 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
 mpcg_status enqueue_plan(mpcg_ctx_t ctx, Plan& pl, cudaStream_t s) {
   CK(ctx, cudaMemsetAsync(pl.bars.p, 0, sizeof(unsigned) * kBarStride * pl.nteams, s));
   CK(ctx, cudaMemsetAsync(pl.err.p, 0, sizeof(unsigned), s));
+  cudaGetLastError();
   CK(ctx, launch_cg(pl.L, pl.grid, 0, s));
   return MPCG_OK;
 }
@@ -533,6 +537,7 @@ mpcg_status mpcg_matrix_create(mpcg_ctx_t ctx, const mpcg_csr* A, mpcg_matrix_t*
   cudaStream_t s = (cudaStream_t)stream;
   std::unique_ptr<mpcg_matrix_s> M(new mpcg_matrix_s());
   M->ctx = ctx;
+  M->device = ctx->device;
   const bool dev = is_device_ptr(A->row_ptr);
   const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const size_t pn = (size_t)nnz + 16;  // padding so that 16-byte rounded ranges stay in bounds
@@ -545,9 +550,9 @@ mpcg_status mpcg_matrix_create(mpcg_ctx_t ctx, const mpcg_csr* A, mpcg_matrix_t*
   CK(ctx, M->vbf.ensure(sizeof(__nv_bfloat16) * pn));
   CK(ctx, M->v16r.ensure(sizeof(__half) * pn));
   CK(ctx, M->vbfr.ensure(sizeof(__nv_bfloat16) * pn));
-  CK(ctx, M->rscale.ensure(sizeof(float) * ((size_t)n + 1)));
+  CK(ctx, M->rexp.ensure(sizeof(short) * ((size_t)n + 8)));
   M->bytes = (long long)(M->rp.cap + M->ci.cap + M->v64.cap + M->v32.cap + M->vtf.cap + M->v16.cap + M->vbf.cap +
-                         M->v16r.cap + M->vbfr.cap + M->rscale.cap);
+                         M->v16r.cap + M->vbfr.cap + M->rexp.cap);
   CK(ctx, cudaMemcpyAsync(M->rp.p, A->row_ptr, sizeof(int) * ((size_t)n + 1), kind, s));
   CK(ctx, cudaMemsetAsync(M->ci.p, 0, sizeof(int) * pn, s));
   CK(ctx, cudaMemsetAsync(M->v64.p, 0, sizeof(double) * pn, s));
@@ -584,10 +589,9 @@ mpcg_status mpcg_matrix_create(mpcg_ctx_t ctx, const mpcg_csr* A, mpcg_matrix_t*
   d.vbf = M->vbf.as<__nv_bfloat16>();
   d.v16r = M->v16r.as<__half>();
   d.vbfr = M->vbfr.as<__nv_bfloat16>();
-  d.rscale = M->rscale.as<float>();
-  CK(ctx, launch_convert(d, nullptr, M->v32.as<float>(), M->vtf.as<float>(), M->v16.as<__half>(),
-                         M->vbf.as<__nv_bfloat16>(), M->v16r.as<__half>(), M->vbfr.as<__nv_bfloat16>(),
-                         M->rscale.as<float>(), s));
+  d.rexp = M->rexp.as<short>();
+  CK(ctx, launch_convert(d, M->v32.as<float>(), M->vtf.as<float>(), M->v16.as<__half>(), M->vbf.as<__nv_bfloat16>(),
+                         M->v16r.as<__half>(), M->vbfr.as<__nv_bfloat16>(), M->rexp.as<short>(), s));
   // Row statistics (host) and static features of the MLP policy.
   std::vector<int> hrp((size_t)n + 1);
   CK(ctx, cudaMemcpyAsync(hrp.data(), M->rp.p, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToHost, s));
@@ -631,7 +635,7 @@ mpcg_status mpcg_matrix_create(mpcg_ctx_t ctx, const mpcg_csr* A, mpcg_matrix_t*
 
 mpcg_status mpcg_matrix_destroy(mpcg_matrix_t A) {
   if (!A) return MPCG_ERR_INVALID_ARG;
-  cudaSetDevice(A->ctx->device);
+  cudaSetDevice(A->device);
   delete A;
   return MPCG_OK;
 }
@@ -688,7 +692,7 @@ mpcg_status mpcg_spmv(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t fmt, const double
   CK(ctx, cudaEventRecord(e0, s));
   for (int r = 0; r < reps; ++r) CK(ctx, launch_spmv_only(S, fmt, grid, s));
   CK(ctx, cudaEventRecord(e1, s));
-  CK(ctx, launch_from_q(S.q, A->dm.rscale, y, n, fmt, s));
+  CK(ctx, launch_from_q(S.q, A->dm.rexp, y, n, fmt, s));
   CK(ctx, cudaStreamSynchronize(s));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
@@ -734,6 +738,7 @@ mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, 
 static mpcg_policy_s* new_policy(mpcg_ctx_t ctx, int kind) {
   mpcg_policy_s* P = new mpcg_policy_s();
   P->ctx = ctx;
+  P->device = ctx->device;
   P->kind = kind;
   P->shape = ctx->opt;
   P->nprec = ctx->opt.nprec;
@@ -905,7 +910,7 @@ mpcg_status mpcg_policy_load(mpcg_ctx_t ctx, const void* blob, size_t bytes, mpc
 
 mpcg_status mpcg_policy_destroy(mpcg_policy_t P) {
   if (!P) return MPCG_ERR_INVALID_ARG;
-  cudaSetDevice(P->ctx->device);
+  cudaSetDevice(P->device);
   delete P;
   return MPCG_OK;
 }
@@ -1007,6 +1012,7 @@ mpcg_status mpcg_graph_create(mpcg_ctx_t ctx, int32_t nsys, const mpcg_matrix_t*
   cudaStream_t s = (cudaStream_t)stream;
   std::unique_ptr<mpcg_graph_s> g(new mpcg_graph_s());
   g->ctx = ctx;
+  g->device = ctx->device;
   g->plan.reset(new Plan());
   st = build_plan(ctx, *g->plan, in, policy, 0, 0, 0, s);
   if (st != MPCG_OK) return st;
@@ -1047,7 +1053,7 @@ mpcg_status mpcg_graph_results(mpcg_graph_t g, mpcg_result* res, void* stream) {
 
 mpcg_status mpcg_graph_destroy(mpcg_graph_t g) {
   if (!g) return MPCG_ERR_INVALID_ARG;
-  cudaSetDevice(g->ctx->device);
+  cudaSetDevice(g->device);
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   delete g;

@@ -328,17 +328,16 @@ __device__ void choose_action(const Launch& L, const DevSys& S, SysState* st, in
 // Row phases
 // ----------------------------------------------------------------------------------------
 
-__device__ __forceinline__ void sigma_term(double ri, int p2, int p4, double& sd, float& sf) {
+// sigma term of row i: fl_p4(r_i) fl_p4(z_i) with z_i = fl_p2(r_i), accumulated in fp64.
+__device__ __forceinline__ void sigma_term(double ri, int p2, int p4, double& sd) {
   const double z = round_fmt(ri, p2);
-  if (p4 == F64) sd = fma(ri, z, sd);
-  else sf = fmaf((float)round_fmt(ri, p4), (float)round_fmt(z, p4), sf);
+  sd = fma(round_fmt(ri, p4), round_fmt(z, p4), sd);
 }
 
 // r = b - A x in fp64 (residual recomputation), with ||r||^2 and, when p2 >= 0, sigma partials.
 // With copy_p the new residual is also written to p (warm-start initialisation).
 template <int K>
-__device__ void true_res_vec(const DevSys& S, Rows R, int p2, int p4, bool copy_p, double& rr, double& sd,
-                             float& sf) {
+__device__ void true_res_vec(const DevSys& S, Rows R, int p2, int p4, bool copy_p, double& rr, double& sd) {
   constexpr int NG = kThreads / K;
   const int lane = threadIdx.x & (K - 1);
   const int grp = threadIdx.x / K;
@@ -357,26 +356,39 @@ __device__ void true_res_vec(const DevSys& S, Rows R, int p2, int p4, bool copy_
       S.r[row] = ri;
       if (copy_p) S.p[row] = ri;
       rr = fma(ri, ri, rr);
-      if (p2 >= 0) sigma_term(ri, p2, p4, sd, sf);
+      if (p2 >= 0) sigma_term(ri, p2, p4, sd);
     }
   }
 }
 
-__device__ void true_res_rows(const DevSys& S, Rows R, int p2, int p4, bool copy_p, double& rr, double& sd,
-                              float& sf) {
+__device__ void true_res_rows(const DevSys& S, Rows R, int p2, int p4, bool copy_p, double& rr, double& sd) {
   switch (S.A.lanes[F64]) {
-    case 1: true_res_vec<1>(S, R, p2, p4, copy_p, rr, sd, sf); break;
-    case 2: true_res_vec<2>(S, R, p2, p4, copy_p, rr, sd, sf); break;
-    case 4: true_res_vec<4>(S, R, p2, p4, copy_p, rr, sd, sf); break;
-    case 8: true_res_vec<8>(S, R, p2, p4, copy_p, rr, sd, sf); break;
-    case 16: true_res_vec<16>(S, R, p2, p4, copy_p, rr, sd, sf); break;
-    default: true_res_vec<32>(S, R, p2, p4, copy_p, rr, sd, sf); break;
+    case 1: true_res_vec<1>(S, R, p2, p4, copy_p, rr, sd); break;
+    case 2: true_res_vec<2>(S, R, p2, p4, copy_p, rr, sd); break;
+    case 4: true_res_vec<4>(S, R, p2, p4, copy_p, rr, sd); break;
+    case 8: true_res_vec<8>(S, R, p2, p4, copy_p, rr, sd); break;
+    case 16: true_res_vec<16>(S, R, p2, p4, copy_p, rr, sd); break;
+    default: true_res_vec<32>(S, R, p2, p4, copy_p, rr, sd); break;
   }
 }
 
 // ----------------------------------------------------------------------------------------
 // Team steps (run by every thread of the CTA that arrived last)
 // ----------------------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Nanoseconds since the previous team barrier of this system (and restarts the clock).
+__device__ __forceinline__ unsigned stamp(SysState* st) {
+  const unsigned long long t = gtime();
+  const unsigned long long d = t - st->t_last;
+  st->t_last = t;
+  return d > 0xffffffffull ? 0xffffffffu : (unsigned)d;
+}
 
 __device__ void write_record(const DevSys& S, SysState* st, int flags, double rho, double sigma, double beta,
                              double reward) {
@@ -396,7 +408,9 @@ __device__ void write_record(const DevSys& S, SysState* st, int flags, double rh
     rec.beta = beta;
     rec.reward = reward;
     rec.flags = flags | (st->explored ? 8 : 0);
-    rec.pad = 0;
+    rec.ns_a = st->ns_a;
+    rec.ns_b = st->ns_b;
+    rec.ns_c = 0;
     S.hist[k] = rec;
   }
 }
@@ -449,6 +463,8 @@ __device__ void step_init(const Launch& L, const DevSys& S, SysState* st, double
     st->explored = 0;
     st->s_cur = 0;
     st->zfmt = F64;
+    st->ns_a = st->ns_b = 0;
+    st->t_last = gtime();
     for (int j = 0; j < 4; ++j) {
       st->prev_act[j] = 0;
       for (int f = 0; f < 8; ++f) st->counts[j][f] = 0;
@@ -480,6 +496,8 @@ __device__ void step_init(const Launch& L, const DevSys& S, SysState* st, double
 // After phase A: nu = fl_p3(sum), alpha = sigma / nu, curvature breakdown test.
 __device__ void step_A(const Launch& L, const DevSys& S, SysState* st, double nu_sum) {
   if (threadIdx.x != 0) return;
+  st->ns_a = stamp(st);
+  st->ns_b = 0;
   const int p3 = st->fmt[2];
   const double nu = (p3 == F64) ? nu_sum : round_fmt(nu_sum, p3);
   const double alpha = st->sigma / nu;
@@ -560,6 +578,7 @@ __device__ void continue_step(const Launch& L, const DevSys& S, SysState* st, do
 // After phase B: rho_{k+1} of the recursive residual, stopping tests.
 __device__ void step_B(const Launch& L, const DevSys& S, SysState* st, double rr, double sig_sum, Smem& sm) {
   if (threadIdx.x == 0) {
+    st->ns_b = stamp(st);
     sm.need_action = 0;
     const double rho_rec = sqrt(rr) / st->bnorm;
     const OptView& o = L.opt;
@@ -679,7 +698,6 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
   // ---- initialisation: x_0, r_0 = b - A x_0, p_0 = r_0, ||b||^2, sigma_0 = ||r_0||^2 ----
   {
     double bb = 0.0, rr = 0.0, sd = 0.0;
-    float sf = 0.f;
     for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
       const double bi = __ldg(S.b + i);
       bb = fma(bi, bi, bb);
@@ -690,7 +708,7 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
         rr = fma(bi, bi, rr);
       }
     }
-    if (o.warm_start) true_res_rows(S, R, -1, -1, true, rr, sd, sf);
+    if (o.warm_start) true_res_rows(S, R, -1, -1, true, rr, sd);
     bb = cta_sum(bb, sm.red);
     rr = cta_sum(rr, sm.red);
     write_partial(L, 0, bb);
@@ -715,11 +733,9 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
       // ---- phase A: q = fl_p1(A p), nu partials ----
       {
         double nd = 0.0;
-        float nf = 0.f;
         const int p1 = sm.bc.fmt[0], p3 = sm.bc.fmt[2];
-        spmv_rows(S, R, p1, p3, nd, nf);
-        const double part = (p3 == F64) ? cta_sum(nd, sm.red) : (double)cta_sum(nf, sm.red);
-        write_partial(L, 0, part);
+        spmv_rows(S, R, p1, p3, nd);
+        write_partial(L, 0, cta_sum(nd, sm.red));
         if (!team_step(L, T, st, sm, [&] { step_A(L, S, st, team_sum(L, T, 0, sm.red)); })) return false;
         if (sm.bc.mode != M_CONT) break;
       }
@@ -729,17 +745,16 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
         const int p1 = sm.bc.fmt[0], p2 = sm.bc.fmt[1], p4 = sm.bc.fmt[3];
         const bool scaled = row_scaled(p1);
         double rr = 0.0, sd = 0.0;
-        float sf = 0.f;
         for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
           double qv = load_fmt(S.q, i, p1);
-          if (scaled) qv *= (double)__ldg(S.A.rscale + i);
+          if (scaled) qv *= pow2(__ldg(S.A.rexp + i));
           const double ri = fma(-alpha, qv, S.r[i]);
           S.r[i] = ri;
           rr = fma(ri, ri, rr);
-          sigma_term(ri, p2, p4, sd, sf);
+          sigma_term(ri, p2, p4, sd);
         }
         rr = cta_sum(rr, sm.red);
-        const double sp = (p4 == F64) ? cta_sum(sd, sm.red) : (double)cta_sum(sf, sm.red);
+        const double sp = cta_sum(sd, sm.red);
         write_partial(L, 0, rr);
         write_partial(L, 1, sp);
         if (!team_step(L, T, st, sm, [&] {
@@ -763,7 +778,14 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
           S.p[i] = pn;
           if (p1n != F64) store_fmt(S.plow, i, pn, p1n);
         }
-        if (!team_step(L, T, st, sm, [] {})) return false;
+        if (!team_step(L, T, st, sm, [&] {
+              if (threadIdx.x == 0) {
+                const unsigned d = stamp(st);
+                const int kd = st->k - 1;
+                if (S.hist && kd >= 0 && kd < S.hist_cap) S.hist[kd].ns_c = d;
+              }
+            }))
+          return false;
         if (sm.bc.k >= S.max_iter) break;
         continue;
       }
@@ -779,10 +801,9 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
       {
         const int p2 = sm.bc.fmt[1], p4 = sm.bc.fmt[3];
         double rr = 0.0, sd = 0.0;
-        float sf = 0.f;
-        true_res_rows(S, R, p2, p4, false, rr, sd, sf);
+        true_res_rows(S, R, p2, p4, false, rr, sd);
         rr = cta_sum(rr, sm.red);
-        const double sp = (p4 == F64) ? cta_sum(sd, sm.red) : (double)cta_sum(sf, sm.red);
+        const double sp = cta_sum(sd, sm.red);
         write_partial(L, 0, rr);
         write_partial(L, 1, sp);
         if (!team_step(L, T, st, sm, [&] {
@@ -812,11 +833,10 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
   // ---- final: ||b - A x|| in fp64 unless already known ----
   {
     double rr = 0.0, sd = 0.0;
-    float sf = 0.f;
     int known = 0;
     if (threadIdx.x == 0) known = *(volatile int*)&st->true_known;
     known = __syncthreads_or(known);
-    if (!known) true_res_rows(S, R, -1, -1, false, rr, sd, sf);
+    if (!known) true_res_rows(S, R, -1, -1, false, rr, sd);
     rr = cta_sum(rr, sm.red);
     write_partial(L, 0, rr);
     if (!team_step(L, T, st, sm, [&] { step_final(L, S, st, sid, team_sum(L, T, 0, sm.red)); })) return false;

@@ -36,7 +36,7 @@ struct DevMatrix {
   const __nv_bfloat16* vbf;
   const __half* v16r;
   const __nv_bfloat16* vbfr;
-  const float* rscale;      // s_i of the row-scaled formats (powers of two)
+  const short* rexp;        // e_i of the row scales s_i = 2^e_i of the row-scaled formats
   int sched[8];             // SpMV schedule per format
   int lanes[8];             // lanes per row per format
   int tile_rows[8];         // stream schedule: rows per shared-memory tile
@@ -88,6 +88,8 @@ struct SysState {
   int have_prev, n_true, ntrans, true_known;
   int explored, s_cur;      // exploration flag and state index of the current iteration
   int zfmt, pad;            // p2 of the iteration whose direction update is pending
+  unsigned long long t_last;  // globaltimer at the previous team barrier
+  unsigned ns_a, ns_b;        // phase times of the current iteration
   long long counts[4][8];
 };
 
@@ -152,13 +154,12 @@ cudaError_t cg_occupancy(int* blocks_per_sm, size_t smem);
 size_t cg_static_smem();
 cudaError_t launch_validate(int n, long long nnz, const int* rp, const int* ci, const double* v,
                             unsigned* flags, int* bad_row, cudaStream_t s);
-cudaError_t launch_convert(const DevMatrix& A, double* v64w, float* v32, float* vtf, __half* v16,
-                           __nv_bfloat16* vbf, __half* v16r, __nv_bfloat16* vbfr, float* rscale,
-                           cudaStream_t s);
+cudaError_t launch_convert(const DevMatrix& A, float* v32, float* vtf, __half* v16, __nv_bfloat16* vbf,
+                           __half* v16r, __nv_bfloat16* vbfr, short* rexp, cudaStream_t s);
 cudaError_t launch_row_features(int n, const int* rp, const int* ci, const double* v, unsigned long long* out,
                                 cudaStream_t s);
 cudaError_t launch_to_format(const double* x, void* xlow, int n, int f, cudaStream_t s);
-cudaError_t launch_from_q(const void* q, const float* rscale, double* y, int n, int f, cudaStream_t s);
+cudaError_t launch_from_q(const void* q, const short* rexp, double* y, int n, int f, cudaStream_t s);
 cudaError_t launch_spmv_only(const DevSys& S, int fmt, int grid, cudaStream_t s);
 cudaError_t launch_qcopy(const double* Q, double* Qpriv, int nlanes, long long qsize, cudaStream_t s);
 cudaError_t launch_qmerge(double* Q, int* visits, const Transition* trans, const SysState* st, int nlanes, int cap,

@@ -57,11 +57,12 @@ __global__ void validate_rows(int n, const int* __restrict__ rp, const int* __re
   }
 }
 
-// One warp per row: row scale s_i = 2^floor(log2 max_j |a_ij|) (clamped to the fp32
-// exponent range), then every copy rounded once from fp64.
+// One warp per row: row scale s_i = 2^e_i with e_i = floor(log2 max_j |a_ij|) (rows whose
+// largest entry is below the fp64 normal range use e_i = -1022), then every copy rounded
+// once from fp64.
 __global__ void convert_values(int n, const int* __restrict__ rp, const double* __restrict__ v64, float* v32,
                                float* vtf, __half* v16, __nv_bfloat16* vbf, __half* v16r, __nv_bfloat16* vbfr,
-                               float* rscale) {
+                               short* rexp) {
   const int lane = threadIdx.x & 31;
   for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; row < n;
        row += ((long long)gridDim.x * blockDim.x) >> 5) {
@@ -71,17 +72,17 @@ __global__ void convert_values(int n, const int* __restrict__ rp, const double* 
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
     int ex = 0;
     if (m > 0.0) ex = (int)(((unsigned long long)__double_as_longlong(m) >> 52) & 0x7ff) - 1023;
-    if (ex < -126) ex = -126;
-    if (ex > 127) ex = 127;
-    const double sinv = __longlong_as_double((long long)((unsigned long long)(1023 - ex) << 52));
-    if (lane == 0) rscale[row] = (float)__longlong_as_double((long long)((unsigned long long)(1023 + ex) << 52));
+    if (ex < -1022) ex = -1022;
+    // 2^-ex, split in two factors so that it stays representable for every ex
+    const double s1 = pow2(-ex / 2), s2 = pow2(-ex - (-ex / 2));
+    if (lane == 0) rexp[row] = (short)ex;
     for (int e = e0 + lane; e < e1; e += 32) {
       const double a = v64[e];
       v32[e] = (float)round_to<24, -126, 127>(a);
       vtf[e] = (float)round_to<11, -126, 127>(a);
       v16[e] = __double2half(round_to<11, -14, 15>(a));
       vbf[e] = __double2bfloat16(round_to<8, -126, 127>(a));
-      const double as = a * sinv;
+      const double as = (a * s1) * s2;
       v16r[e] = __double2half(round_to<11, -14, 15>(as));
       vbfr[e] = __double2bfloat16(round_to<8, -126, 127>(as));
     }
@@ -130,10 +131,10 @@ __global__ void to_format(const double* __restrict__ x, void* xlow, int n, int f
 }
 
 // y = q (stored in format f) as fp64, times the row scale for the row-scaled formats.
-__global__ void from_q(const void* q, const float* __restrict__ rscale, double* y, int n, int f) {
+__global__ void from_q(const void* q, const short* __restrict__ rexp, double* y, int n, int f) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     double v = load_fmt(q, i, f);
-    if (row_scaled(f)) v *= (double)rscale[i];
+    if (row_scaled(f)) v *= pow2(rexp[i]);
     y[i] = v;
   }
 }
@@ -147,8 +148,7 @@ __global__ void __launch_bounds__(kThreads) spmv_standalone(const DevSys S, int 
   }
   __syncthreads();
   double nd = 0.0;
-  float nf = 0.f;
-  spmv_rows(S, Rows{r01[0], r01[1]}, fmt, -1, nd, nf);
+  spmv_rows(S, Rows{r01[0], r01[1]}, fmt, -1, nd);
 }
 
 __global__ void qcopy_kernel(const double* __restrict__ Q, double* Qpriv, int nlanes, long long qsize) {
@@ -210,6 +210,7 @@ int grid_for(long long work, int per_block) {
 
 cudaError_t launch_validate(int n, long long nnz, const int* rp, const int* ci, const double* v, unsigned* flags,
                             int* bad_row, cudaStream_t s) {
+  cudaGetLastError();
   validate_rowptr<<<grid_for((long long)n + 1, kThreads), kThreads, 0, s>>>(n, nnz, rp, flags, bad_row);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -222,40 +223,46 @@ cudaError_t launch_validate(int n, long long nnz, const int* rp, const int* ci, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_convert(const DevMatrix& A, double*, float* v32, float* vtf, __half* v16, __nv_bfloat16* vbf,
-                           __half* v16r, __nv_bfloat16* vbfr, float* rscale, cudaStream_t s) {
+cudaError_t launch_convert(const DevMatrix& A, float* v32, float* vtf, __half* v16, __nv_bfloat16* vbf,
+                           __half* v16r, __nv_bfloat16* vbfr, short* rexp, cudaStream_t s) {
   if (A.n == 0) return cudaSuccess;
+  cudaGetLastError();
   convert_values<<<grid_for((long long)A.n * 32, kThreads), kThreads, 0, s>>>(A.n, A.rp, A.v64, v32, vtf, v16, vbf,
-                                                                             v16r, vbfr, rscale);
+                                                                             v16r, vbfr, rexp);
   return cudaGetLastError();
 }
 
 cudaError_t launch_row_features(int n, const int* rp, const int* ci, const double* v, unsigned long long* out,
                                 cudaStream_t s) {
   if (n == 0) return cudaSuccess;
+  cudaGetLastError();
   row_features<<<grid_for((long long)n * 32, kThreads), kThreads, 0, s>>>(n, rp, ci, v, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_to_format(const double* x, void* xlow, int n, int f, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
+  cudaGetLastError();
   to_format<<<grid_for(n, kThreads), kThreads, 0, s>>>(x, xlow, n, f);
   return cudaGetLastError();
 }
 
-cudaError_t launch_from_q(const void* q, const float* rscale, double* y, int n, int f, cudaStream_t s) {
+cudaError_t launch_from_q(const void* q, const short* rexp, double* y, int n, int f, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  from_q<<<grid_for(n, kThreads), kThreads, 0, s>>>(q, rscale, y, n, f);
+  cudaGetLastError();
+  from_q<<<grid_for(n, kThreads), kThreads, 0, s>>>(q, rexp, y, n, f);
   return cudaGetLastError();
 }
 
 cudaError_t launch_spmv_only(const DevSys& S, int fmt, int grid, cudaStream_t s) {
   if (S.A.n == 0) return cudaSuccess;
+  cudaGetLastError();
   spmv_standalone<<<grid, kThreads, 0, s>>>(S, fmt);
   return cudaGetLastError();
 }
 
 cudaError_t launch_qcopy(const double* Q, double* Qpriv, int nlanes, long long qsize, cudaStream_t s) {
+  cudaGetLastError();
   qcopy_kernel<<<grid_for(qsize * nlanes, kThreads), kThreads, 0, s>>>(Q, Qpriv, nlanes, qsize);
   return cudaGetLastError();
 }
@@ -264,6 +271,7 @@ cudaError_t launch_qmerge(double* Q, int* visits, const Transition* trans, const
                           int S, int nprec, double lr, double gamma, cudaStream_t s) {
   const size_t bytes = sizeof(double) * 4 * (size_t)S * nprec;
   const int use_smem = bytes <= 48 * 1024 ? 1 : 0;
+  cudaGetLastError();
   qmerge_kernel<<<1, 128, use_smem ? bytes : 0, s>>>(Q, visits, trans, st, nlanes, cap, S, nprec, lr, gamma, use_smem);
   return cudaGetLastError();
 }

@@ -28,43 +28,47 @@ __device__ __forceinline__ int part_row(const int* rp, int n, long long nnz, int
   return lo;
 }
 
-__device__ __forceinline__ void nu_term(double pi, double qi, int p3, double& nd, float& nf) {
-  if (p3 == F64) nd = fma(pi, qi, nd);
-  else nf = fmaf((float)round_fmt(pi, p3), (float)round_fmt(qi, p3), nf);
+// nu term of row i: fl_p3(p_i) fl_p3(q_i), products of rounded inputs accumulated in fp64
+// (exact for every format of the set), the sum rounded to p3 by the caller.
+__device__ __forceinline__ void nu_term(double pi, double qi, int p3, double& nd) {
+  nd = fma(round_fmt(pi, p3), round_fmt(qi, p3), nd);
 }
 
-// Rounds the accumulator of row i onto the product's format, stores it in q and returns the
-// row's value of q (times the row scale for the row-scaled formats) as fp64.
-__device__ __forceinline__ double store_q(void* q, int i, float acc, int p1, float scale) {
+// 2^e as fp64 (e in [-1022, 1023]).
+__device__ __forceinline__ double pow2(int e) {
+  return __longlong_as_double((long long)((unsigned long long)(e + 1023) << 52));
+}
+
+// Rounds the row sum onto the product's format p1 (one rounding), stores it in q and
+// returns the row's value of q (times 2^e_i for the row-scaled formats) as fp64.
+__device__ __forceinline__ double store_q(void* q, int i, double tot, int p1, double scale) {
+  const double r = round_fmt(tot, p1);
   switch (store_of(p1)) {
-    case ST_HALF: {
-      const __half h = __float2half_rn(acc);
-      ((__half*)q)[i] = h;
-      return (double)__half2float(h) * (double)scale;
-    }
-    case ST_BF16: {
-      const __nv_bfloat16 h = __float2bfloat16_rn(acc);
-      ((__nv_bfloat16*)q)[i] = h;
-      return (double)__bfloat162float(h) * (double)scale;
-    }
-    default: {
-      const float v = (base_fmt(p1) == TF32) ? round_tf32(acc) : acc;
-      ((float*)q)[i] = v;
-      return (double)v;
-    }
+    case ST_HALF: store_exact((__half*)q, i, r); break;
+    case ST_BF16: store_exact((__nv_bfloat16*)q, i, r); break;
+    case ST_FLOAT: store_exact((float*)q, i, r); break;
+    default: store_exact((double*)q, i, r); break;
   }
-}
-__device__ __forceinline__ double store_q(void* q, int i, double acc, int, float) {
-  ((double*)q)[i] = acc;
-  return acc;
+  return r * scale;
 }
 
-// Sub-warp vector CSR: K lanes per row, rows strided over the CTA, lane sums combined by an
-// xor butterfly in the accumulator precision. With nu_fmt < 0 no nu partial is formed.
+// s + t = a + b exactly (Knuth's TwoSum), fp32, without contraction.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Sub-warp vector CSR: K lanes per row, rows strided over the CTA.
+// fp64 values: fp64 accumulation. Lower formats: the products of the rounded inputs are
+// summed with a compensated fp32 accumulator (sum and error term, TwoSum; fp32 products
+// carry their FMA error term too), i.e. the dot product "Dot2" of Ogita, Rump and Oishi
+// (SIAM J. Sci. Comput. 2005) in fp32, so the row sum is accurate to about 2^-48 and its
+// single rounding onto p1 matches a wide-accumulator sum. The K lane results are combined
+// by an xor butterfly of (sum, error) pairs. With nu_fmt < 0 no nu partial is formed.
 template <typename VT, int K>
 __device__ void spmv_vec(const DevSys& S, const VT* __restrict__ vals, const VT* xin, Rows R, int p1,
-                         int nu_fmt, double& nd, float& nf) {
-  using Acc = typename AccOf<VT>::type;
+                         int nu_fmt, double& nd) {
   constexpr int NG = kThreads / K;
   const int lane = threadIdx.x & (K - 1);
   const int grp = threadIdx.x / K;
@@ -72,42 +76,66 @@ __device__ void spmv_vec(const DevSys& S, const VT* __restrict__ vals, const VT*
   const int* __restrict__ rp = S.A.rp;
   const int* __restrict__ ci = S.A.ci;
   const bool scaled = row_scaled(p1);
+  const short* __restrict__ rexp = S.A.rexp;
   for (int row = R.r0 + grp; row < R.r1; row += NG) {
     const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
-    Acc acc = 0;
-    for (int e = e0 + lane; e < e1; e += K) acc += to_acc(__ldg(vals + e)) * to_acc(xin[__ldg(ci + e)]);
+    double tot;
+    if constexpr (sizeof(VT) == 8) {
+      double acc = 0.0;
+      for (int e = e0 + lane; e < e1; e += K) acc = fma(__ldg(vals + e), xin[__ldg(ci + e)], acc);
 #pragma unroll
-    for (int o = K / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o);
+      for (int o = K / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o);
+      tot = acc;
+    } else {
+      float sum = 0.f, err = 0.f;
+      for (int e = e0 + lane; e < e1; e += K) {
+        const float a = to_acc(__ldg(vals + e)), xv = to_acc(xin[__ldg(ci + e)]);
+        const float pr = __fmul_rn(a, xv);
+        float t;
+        two_sum(sum, pr, sum, t);
+        if constexpr (sizeof(VT) == 4) t = __fadd_rn(t, __fmaf_rn(a, xv, -pr));
+        err = __fadd_rn(err, t);
+      }
+#pragma unroll
+      for (int o = K / 2; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(mask, sum, o), e2 = __shfl_xor_sync(mask, err, o);
+        float t;
+        two_sum(sum, s2, sum, t);
+        err = __fadd_rn(__fadd_rn(err, e2), t);
+      }
+      // an infinite or NaN partial (format overflow) makes the error term meaningless
+      tot = isfinite(sum) ? (double)sum + (double)err : (double)sum;
+    }
     if (lane == 0) {
-      const double qv = store_q(S.q, row, acc, p1, scaled ? __ldg(S.A.rscale + row) : 1.f);
-      if (nu_fmt >= 0) nu_term(S.p[row], qv, nu_fmt, nd, nf);
+      const double qv = store_q(S.q, row, tot, p1, scaled ? pow2(__ldg(rexp + row)) : 1.0);
+      if (nu_fmt >= 0) nu_term(S.p[row], qv, nu_fmt, nd);
     }
   }
 }
 
 template <typename VT>
 __device__ void spmv_dispatch_k(const DevSys& S, const VT* vals, const VT* xin, Rows R, int p1, int nu_fmt,
-                                double& nd, float& nf) {
+                                double& nd) {
   switch (S.A.lanes[p1]) {
-    case 1: spmv_vec<VT, 1>(S, vals, xin, R, p1, nu_fmt, nd, nf); break;
-    case 2: spmv_vec<VT, 2>(S, vals, xin, R, p1, nu_fmt, nd, nf); break;
-    case 4: spmv_vec<VT, 4>(S, vals, xin, R, p1, nu_fmt, nd, nf); break;
-    case 8: spmv_vec<VT, 8>(S, vals, xin, R, p1, nu_fmt, nd, nf); break;
-    case 16: spmv_vec<VT, 16>(S, vals, xin, R, p1, nu_fmt, nd, nf); break;
-    default: spmv_vec<VT, 32>(S, vals, xin, R, p1, nu_fmt, nd, nf); break;
+    case 1: spmv_vec<VT, 1>(S, vals, xin, R, p1, nu_fmt, nd); break;
+    case 2: spmv_vec<VT, 2>(S, vals, xin, R, p1, nu_fmt, nd); break;
+    case 4: spmv_vec<VT, 4>(S, vals, xin, R, p1, nu_fmt, nd); break;
+    case 8: spmv_vec<VT, 8>(S, vals, xin, R, p1, nu_fmt, nd); break;
+    case 16: spmv_vec<VT, 16>(S, vals, xin, R, p1, nu_fmt, nd); break;
+    default: spmv_vec<VT, 32>(S, vals, xin, R, p1, nu_fmt, nd); break;
   }
 }
 
 // Phase A: q = fl_p1(A fl_p1(p)) for the CTA's rows, plus nu partials.
-__device__ void spmv_rows(const DevSys& S, Rows R, int p1, int nu_fmt, double& nd, float& nf) {
+__device__ void spmv_rows(const DevSys& S, Rows R, int p1, int nu_fmt, double& nd) {
   switch (p1) {
-    case F64: spmv_dispatch_k<double>(S, S.A.v64, S.p, R, p1, nu_fmt, nd, nf); break;
-    case F32: spmv_dispatch_k<float>(S, S.A.v32, (const float*)S.plow, R, p1, nu_fmt, nd, nf); break;
-    case TF32: spmv_dispatch_k<float>(S, S.A.vtf, (const float*)S.plow, R, p1, nu_fmt, nd, nf); break;
-    case F16: spmv_dispatch_k<__half>(S, S.A.v16, (const __half*)S.plow, R, p1, nu_fmt, nd, nf); break;
-    case BF16: spmv_dispatch_k<__nv_bfloat16>(S, S.A.vbf, (const __nv_bfloat16*)S.plow, R, p1, nu_fmt, nd, nf); break;
-    case F16R: spmv_dispatch_k<__half>(S, S.A.v16r, (const __half*)S.plow, R, p1, nu_fmt, nd, nf); break;
-    default: spmv_dispatch_k<__nv_bfloat16>(S, S.A.vbfr, (const __nv_bfloat16*)S.plow, R, p1, nu_fmt, nd, nf); break;
+    case F64: spmv_dispatch_k<double>(S, S.A.v64, S.p, R, p1, nu_fmt, nd); break;
+    case F32: spmv_dispatch_k<float>(S, S.A.v32, (const float*)S.plow, R, p1, nu_fmt, nd); break;
+    case TF32: spmv_dispatch_k<float>(S, S.A.vtf, (const float*)S.plow, R, p1, nu_fmt, nd); break;
+    case F16: spmv_dispatch_k<__half>(S, S.A.v16, (const __half*)S.plow, R, p1, nu_fmt, nd); break;
+    case BF16: spmv_dispatch_k<__nv_bfloat16>(S, S.A.vbf, (const __nv_bfloat16*)S.plow, R, p1, nu_fmt, nd); break;
+    case F16R: spmv_dispatch_k<__half>(S, S.A.v16r, (const __half*)S.plow, R, p1, nu_fmt, nd); break;
+    default: spmv_dispatch_k<__nv_bfloat16>(S, S.A.vbfr, (const __nv_bfloat16*)S.plow, R, p1, nu_fmt, nd); break;
   }
 }
 

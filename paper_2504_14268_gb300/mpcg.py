@@ -61,9 +61,10 @@ class CStats(C.Structure):
 REC_DTYPE = np.dtype([
     ("k", np.int32), ("state", np.int32), ("fmt", np.int8, 4), ("act", np.int8, 4),
     ("rho", np.float64), ("nu", np.float64), ("alpha", np.float64), ("sigma", np.float64),
-    ("beta", np.float64), ("reward", np.float64), ("flags", np.int32), ("pad", np.int32),
+    ("beta", np.float64), ("reward", np.float64), ("flags", np.int32), ("ns_a", np.uint32),
+    ("ns_b", np.uint32), ("ns_c", np.uint32),
 ])
-assert REC_DTYPE.itemsize == 72
+assert REC_DTYPE.itemsize == 80
 
 # Every entry point declared in include/mpcg.h, with (restype, argtypes).
 _vp, _i32, _i64, _d, _sz = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_size_t

@@ -40,7 +40,7 @@ def test_struct_layouts():
     from paper_2504_14268_gb300 import mpcg
 
     assert ctypes.sizeof(mpcg.CResult) == 288
-    assert mpcg.REC_DTYPE.itemsize == 72
+    assert mpcg.REC_DTYPE.itemsize == 80
     assert ctypes.sizeof(mpcg.COptions) == 216
     assert ctypes.sizeof(mpcg.Csr) == 40
 
