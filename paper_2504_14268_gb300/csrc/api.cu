@@ -75,10 +75,12 @@ struct mpcg_ctx_s {
   mpcg_options opt;
   OptView ov;
   int nsm = 0;
-  int occ = 0;
+  int occ = 0;      // CTAs per SM of the solver kernel without the stream ring
+  int occ_s = 0;    // ... with the stream ring (2 * kStageBytes of dynamic shared memory)
+  int socc = 0, socc_s = 0;  // same for the standalone product kernel
   std::string err;
   Plan plan;   // reused by mpcg_solve / mpcg_solve_batched / training
-  DevBuf spmv_x, spmv_q, spmv_y;
+  DevBuf spmv_x, spmv_q, spmv_y, spmv_err;
 };
 
 struct mpcg_matrix_s {
@@ -87,6 +89,8 @@ struct mpcg_matrix_s {
   DevBuf rp, ci, v64, v32, vtf, v16, vbf, v16r, vbfr, rexp;
   int device = 0;
   double mean = 0, maxr = 0, cv = 0;
+  long long win[4] = {0, 0, 0, 0};  // largest nonzero count of 256, 128, 64, 32 consecutive rows
+  bool force_stream_shape = false;  // autotuner: time every candidate in the stream launch shape
   float feat[5] = {0, 0, 0, 0, 0};
   long long bytes = 0;
 };
@@ -134,6 +138,25 @@ mpcg_status fail(mpcg_ctx_t ctx, mpcg_status s, const char* fmt, ...) {
   } while (0)
 
 bool valid_fmt(int f) { return f >= 0 && f < NFMT; }
+
+int lanes_index(int lanes) { return lanes == 1 ? 0 : lanes == 2 ? 1 : lanes == 4 ? 2 : lanes == 8 ? 3 : -1; }
+
+// Value-region bytes of a stream-schedule stage for (format, lanes), or -1 when a tile of
+// kThreads / lanes rows does not fit in one stage.
+int stream_vreg(const mpcg_matrix_s* M, int fmt, int lanes) {
+  const int li = lanes_index(lanes);
+  if (li < 0) return -1;
+  const long long w = M->win[li];
+  const long long vreg = (w * bytes_of(fmt) + 16 + 15) / 16 * 16;
+  const long long creg = (w * 4 + 16 + 15) / 16 * 16;
+  return vreg + creg <= kStageBytes ? (int)vreg : -1;
+}
+
+bool uses_stream(const DevMatrix& d) {
+  for (int f = 0; f < NFMT; ++f)
+    if (d.sched[f] == SCHED_STREAM) return true;
+  return false;
+}
 
 mpcg_status build_optview(mpcg_ctx_t ctx, const mpcg_options& o, OptView& v) {
   if (o.b_bins < 1 || o.b_bins > kMaxBBins) return fail(ctx, MPCG_ERR_INVALID_ARG, "b_bins must be in [1, %d]", kMaxBBins);
@@ -293,7 +316,9 @@ mpcg_status fill_policy(mpcg_ctx_t ctx, mpcg_policy_t P, PolicyView& pv) {
 mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, mpcg_policy_t policy, int train,
                        int trans_cap, int force_team, cudaStream_t s) {
   const int nsys = (int)in.size();
-  const int grid = ctx->nsm * ctx->occ;
+  bool stream_shape = false;
+  for (int i = 0; i < nsys; ++i) stream_shape = stream_shape || uses_stream(in[i].A->dm);
+  const int grid = ctx->nsm * (stream_shape ? ctx->occ_s : ctx->occ);
   std::vector<long long> work(nsys);
   for (int i = 0; i < nsys; ++i) work[i] = in[i].A->dm.nnz + 4LL * in[i].A->dm.n;
   std::vector<int> tsize;
@@ -408,6 +433,7 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
   if (st != MPCG_OK) return st;
   L.opt = ctx->ov;
   L.train = train;
+  L.stream_stage = stream_shape ? kStageBytes : 0;
   L.timeout_cycles = kTimeoutCycles;
   if (const char* t = getenv("MPCG_TIMEOUT_CYCLES")) L.timeout_cycles = atoll(t);
   return MPCG_OK;
@@ -418,7 +444,7 @@ mpcg_status enqueue_plan(mpcg_ctx_t ctx, Plan& pl, cudaStream_t s) {
   CK(ctx, cudaMemsetAsync(pl.bars.p, 0, sizeof(unsigned) * kBarStride * pl.nteams, s));
   CK(ctx, cudaMemsetAsync(pl.err.p, 0, sizeof(unsigned), s));
   cudaGetLastError();
-  CK(ctx, launch_cg(pl.L, pl.grid, 0, s));
+  CK(ctx, launch_cg(pl.L, pl.grid, pl.L.stream_stage > 0 ? 2 * (size_t)pl.L.stream_stage : 0, s));
   return MPCG_OK;
 }
 
@@ -501,7 +527,13 @@ mpcg_status mpcg_create(mpcg_ctx_t* out, int device, const mpcg_options* opt) {
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
   cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device);
   if (!coop) return MPCG_ERR_CUDA;
+  if (set_smem_limits(2 * (size_t)kStageBytes) != cudaSuccess) return MPCG_ERR_CUDA;
   if (cg_occupancy(&c->occ, 0) != cudaSuccess || c->occ < 1) return MPCG_ERR_CUDA;
+  if (cg_occupancy(&c->occ_s, 2 * (size_t)kStageBytes) != cudaSuccess || c->occ_s < 1) return MPCG_ERR_CUDA;
+  if (spmv_occupancy(&c->socc, 0) != cudaSuccess || spmv_occupancy(&c->socc_s, 2 * (size_t)kStageBytes) != cudaSuccess)
+    return MPCG_ERR_CUDA;
+  c->socc = std::min(c->socc, c->occ);
+  c->socc_s = std::min(c->socc_s, c->occ_s);
   *out = c.release();
   return MPCG_OK;
 }
@@ -605,6 +637,12 @@ mpcg_status mpcg_matrix_create(mpcg_ctx_t ctx, const mpcg_csr* A, mpcg_matrix_t*
   }
   M->mean = n ? sum / n : 0.0;
   M->maxr = mx;
+  for (int li = 0; li < 4; ++li) {
+    const int tr = kThreads >> li;
+    long long w = 0;
+    for (int i = 0; i < n; ++i) w = std::max(w, (long long)hrp[std::min(i + tr, n)] - hrp[i]);
+    M->win[li] = w;
+  }
   M->cv = (n && M->mean > 0) ? std::sqrt(std::max(0.0, sq / n - M->mean * M->mean)) / M->mean : 0.0;
   // Static features of the MLP policy: log10(n) / 8, mean nnz per row / 64,
   // log10(max a_ii / min a_ii) / 16, log10(max_i sum_j |a_ij| / a_ii) / 16, and the fraction
@@ -659,8 +697,18 @@ mpcg_status mpcg_matrix_info(mpcg_matrix_t A, mpcg_matrix_stats* info) {
 
 mpcg_status mpcg_matrix_set_schedule(mpcg_matrix_t A, int32_t fmt, int32_t sched, int32_t lanes) {
   if (!A) return MPCG_ERR_INVALID_ARG;
-  if (!valid_fmt(fmt) || sched != SCHED_VECTOR || lanes < 1 || lanes > 32 || (lanes & (lanes - 1)))
+  if (!valid_fmt(fmt) || lanes < 1 || lanes > 32 || (lanes & (lanes - 1)))
     return fail(A->ctx, MPCG_ERR_INVALID_ARG, "unsupported schedule (fmt %d, sched %d, lanes %d)", fmt, sched, lanes);
+  if (sched == SCHED_STREAM) {
+    const int vreg = stream_vreg(A, fmt, lanes);
+    if (vreg < 0)
+      return fail(A->ctx, MPCG_ERR_INVALID_ARG, "stream schedule with %d lanes does not fit a %d-byte stage", lanes,
+                  kStageBytes);
+    A->dm.tile_rows[fmt] = kThreads / lanes;
+    A->dm.tile_bytes[fmt] = vreg;
+  } else if (sched != SCHED_VECTOR) {
+    return fail(A->ctx, MPCG_ERR_INVALID_ARG, "unknown schedule %d", sched);
+  }
   A->dm.sched[fmt] = sched;
   A->dm.lanes[fmt] = lanes;
   return MPCG_OK;
@@ -683,14 +731,20 @@ mpcg_status mpcg_spmv(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t fmt, const double
   S.plow = ctx->spmv_x.p;
   S.q = ctx->spmv_q.p;
   if (fmt != F64) CK(ctx, launch_to_format(x, S.plow, n, fmt, s));
-  const int grid = ctx->nsm * ctx->occ;
+  // The launch shape the solver uses for this matrix: with the stream ring when any format
+  // of the matrix uses the stream schedule.
+  const bool stream_shape = A->force_stream_shape || uses_stream(A->dm);
+  const int grid = ctx->nsm * (stream_shape ? ctx->occ_s : ctx->occ);
+  const int stage = stream_shape ? kStageBytes : 0;
+  CK(ctx, ctx->spmv_err.ensure(sizeof(unsigned)));
+  CK(ctx, cudaMemsetAsync(ctx->spmv_err.p, 0, sizeof(unsigned), s));
   if (reps < 1) reps = 1;
   cudaEvent_t e0, e1;
   CK(ctx, cudaEventCreate(&e0));
   CK(ctx, cudaEventCreate(&e1));
-  CK(ctx, launch_spmv_only(S, fmt, grid, s));  // warm-up
+  CK(ctx, launch_spmv_only(S, fmt, grid, stage, ctx->spmv_err.as<unsigned>(), s));  // warm-up
   CK(ctx, cudaEventRecord(e0, s));
-  for (int r = 0; r < reps; ++r) CK(ctx, launch_spmv_only(S, fmt, grid, s));
+  for (int r = 0; r < reps; ++r) CK(ctx, launch_spmv_only(S, fmt, grid, stage, ctx->spmv_err.as<unsigned>(), s));
   CK(ctx, cudaEventRecord(e1, s));
   CK(ctx, launch_from_q(S.q, A->dm.rexp, y, n, fmt, s));
   CK(ctx, cudaStreamSynchronize(s));
@@ -698,6 +752,9 @@ mpcg_status mpcg_spmv(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t fmt, const double
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  unsigned herr = 0;
+  CK(ctx, cudaMemcpy(&herr, ctx->spmv_err.p, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (herr) return fail(ctx, MPCG_ERR_TIMEOUT, "a bulk-copy wait of the product exceeded its limit");
   if (ms_per_rep) *ms_per_rep = ms / reps;
   return MPCG_OK;
 }
@@ -705,31 +762,72 @@ mpcg_status mpcg_spmv(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t fmt, const double
 mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, void* stream) {
   if (!ctx || !A) return fail(ctx, MPCG_ERR_INVALID_ARG, "NULL argument");
   cudaSetDevice(ctx->device);
-  cudaStream_t s = (cudaStream_t)stream;
   const int n = A->dm.n;
   if (n == 0) return MPCG_OK;
   DevBuf x, y;
   CK(ctx, x.ensure(8 * (size_t)n));
   CK(ctx, y.ensure(8 * (size_t)n));
   std::vector<double> ones((size_t)n, 1.0);
-  CK(ctx, cudaMemcpyAsync(x.p, ones.data(), 8 * (size_t)n, cudaMemcpyHostToDevice, s));
-  CK(ctx, cudaStreamSynchronize(s));
+  CK(ctx, cudaMemcpy(x.p, ones.data(), 8 * (size_t)n, cudaMemcpyHostToDevice));
+  reps = std::max(1, reps);
+  auto time_it = [&](int f, int sched, int lanes, double& ms) -> mpcg_status {
+    mpcg_status st = mpcg_matrix_set_schedule(A, f, sched, lanes);
+    if (st != MPCG_OK) return st;
+    return mpcg_spmv(ctx, A, f, x.as<double>(), y.as<double>(), reps, &ms, stream);
+  };
+  // Configuration P: every format on the sub-warp vector schedule, no stream ring.
+  int bestP[NFMT];
+  double sumP = 0;
+  for (int f = 0; f < NFMT; ++f) A->dm.sched[f] = SCHED_VECTOR;
   for (int f = 0; f < NFMT; ++f) {
-    int best = A->dm.lanes[f];
-    double best_ms = 1e30;
+    double best = 1e30;
+    bestP[f] = A->dm.lanes[f];
     for (int lanes = 1; lanes <= 32; lanes *= 2) {
-      A->dm.lanes[f] = lanes;
       double ms = 0;
-      mpcg_status st = mpcg_spmv(ctx, A, f, x.as<double>(), y.as<double>(), std::max(1, reps), &ms, stream);
+      mpcg_status st = time_it(f, SCHED_VECTOR, lanes, ms);
       if (st != MPCG_OK) return st;
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = lanes;
-      }
+      if (ms < best) { best = ms; bestP[f] = lanes; }
     }
-    A->dm.lanes[f] = best;
-    A->dm.sched[f] = SCHED_VECTOR;
+    A->dm.lanes[f] = bestP[f];
+    sumP += best;
   }
+  // Configuration S: launch shape with the stream ring; each format takes the faster of the
+  // stream schedule and the vector schedule measured in that shape.
+  bool any = false;
+  for (int f = 0; f < NFMT && !any; ++f)
+    for (int lanes = 1; lanes <= 8; lanes *= 2) any = any || stream_vreg(A, f, lanes) >= 0;
+  if (any) {
+    int schedS[NFMT], lanesS[NFMT];
+    double sumS = 0;
+    A->force_stream_shape = true;
+    for (int f = 0; f < NFMT; ++f) {
+      double best = 1e30;
+      schedS[f] = SCHED_VECTOR;
+      lanesS[f] = bestP[f];
+      for (int lanes = 1; lanes <= 32; lanes *= 2) {
+        for (int sched = 0; sched < 2; ++sched) {
+          if (sched == SCHED_STREAM && stream_vreg(A, f, lanes) < 0) continue;
+          double ms = 0;
+          mpcg_status st = time_it(f, sched, lanes, ms);
+          if (st != MPCG_OK) {
+            A->force_stream_shape = false;
+            return st;
+          }
+          if (ms < best) { best = ms; schedS[f] = sched; lanesS[f] = lanes; }
+        }
+      }
+      mpcg_matrix_set_schedule(A, f, schedS[f], lanesS[f]);
+      sumS += best;
+    }
+    A->force_stream_shape = false;
+    bool s_uses = false;
+    for (int f = 0; f < NFMT; ++f) s_uses = s_uses || schedS[f] == SCHED_STREAM;
+    if (s_uses && sumS < sumP) {
+      for (int f = 0; f < NFMT; ++f) mpcg_matrix_set_schedule(A, f, schedS[f], lanesS[f]);
+      return MPCG_OK;
+    }
+  }
+  for (int f = 0; f < NFMT; ++f) mpcg_matrix_set_schedule(A, f, SCHED_VECTOR, bestP[f]);
   return MPCG_OK;
 }
 

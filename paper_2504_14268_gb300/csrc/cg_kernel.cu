@@ -39,7 +39,7 @@ struct Bcast {
 };
 
 struct Smem {
-  double red[kThreads / 32];
+  double red[2 * (kThreads / 32)];
   Bcast bc;
   int last;
   int ok;
@@ -48,6 +48,8 @@ struct Smem {
   int flag;
   int r0, r1;
   int a_fmt[4], a_act[4], a_expl, a_state;
+  unsigned long long mbar[2];
+  unsigned mbar_phase;
   float feat[kNFeat];
   float h1[kMaxHidden];
   float h2[kMaxHidden];
@@ -71,6 +73,30 @@ __device__ __forceinline__ T cta_sum(T v, double* red) {
 #pragma unroll
   for (int w = 0; w < kThreads / 32; ++w) s += (T)red[w];
   return s;
+}
+
+// Reduction of a dot accumulator over the CTA in a fixed order: the fp64 part by
+// cta_sum, the compensated fp32 pair by an xor butterfly of TwoSum steps, then the warp
+// pairs in warp order; returns d + s + c in fp64.
+__device__ __forceinline__ double cta_dot(DotAcc a, double* red) {
+  const double d = cta_sum(a.d, red);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(kFull, a.s, o), c2 = __shfl_xor_sync(kFull, a.c, o);
+    float t;
+    two_sum(a.s, s2, a.s, t);
+    a.c = __fadd_rn(__fadd_rn(a.c, c2), t);
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = (double)a.s;
+    red[(threadIdx.x >> 5) + kThreads / 32] = (double)a.c;
+  }
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int w = 0; w < kThreads / 32; ++w) s += red[w] + red[w + kThreads / 32];
+  return d + s;
 }
 
 __device__ __forceinline__ void write_partial(const Launch& L, int slot, double v) {
@@ -328,16 +354,54 @@ __device__ void choose_action(const Launch& L, const DevSys& S, SysState* st, in
 // Row phases
 // ----------------------------------------------------------------------------------------
 
-// sigma term of row i: fl_p4(r_i) fl_p4(z_i) with z_i = fl_p2(r_i), accumulated in fp64.
-__device__ __forceinline__ void sigma_term(double ri, int p2, int p4, double& sd) {
-  const double z = round_fmt(ri, p2);
-  sd = fma(round_fmt(ri, p4), round_fmt(z, p4), sd);
+// sigma term of row i: fl_p4(r_i) fl_p4(z_i) with z_i = fl_p2(r_i): a DFMA when p4 = fp64,
+// otherwise the compensated fp32 pair. Roundings that are identities (p4's value set
+// contains p2's) are skipped.
+__device__ __forceinline__ void sigma_term(double ri, int p2, int p4, DotAcc& sg) {
+  if (p4 == F64) {
+    const double z = (p2 == F64) ? ri : f2d(round_d2f(ri, p2));
+    sg.d = fma(ri, z, sg.d);
+  } else {
+    const float a = round_d2f(ri, p4);
+    float b;
+    if (p2 == F64 || base_fmt(p2) == base_fmt(p4)) b = a;
+    else {
+      const float zf = round_d2f(ri, p2);
+      b = contains_fmt(p4, p2) ? zf : round_f2f(zf, p4);
+    }
+    dot_low(sg, a, b, p4);
+  }
+}
+
+// z = fl_p2(r) as fp64.
+__device__ __forceinline__ double z_of(double ri, int p2) { return p2 == F64 ? ri : f2d(round_d2f(ri, p2)); }
+
+// Element i of q (stored in p1's format) as fp64, times 2^e_i for the row-scaled formats.
+__device__ __forceinline__ double load_q(const DevSys& S, int i, int p1) {
+  double v;
+  switch (store_of(p1)) {
+    case ST_HALF: v = f2d(__half2float(((const __half*)S.q)[i])); break;
+    case ST_BF16: v = f2d(__bfloat162float(((const __nv_bfloat16*)S.q)[i])); break;
+    case ST_FLOAT: v = f2d(((const float*)S.q)[i]); break;
+    default: return ((const double*)S.q)[i];
+  }
+  return row_scaled(p1) ? scale2(v, __ldg(S.A.rexp + i)) : v;
+}
+
+// Stores fl_f(v) (f other than fp64) in the low-precision copy of p.
+__device__ __forceinline__ void store_low(void* plow, int i, double v, int f) {
+  const float r = round_d2f(v, f);
+  switch (store_of(f)) {
+    case ST_HALF: ((__half*)plow)[i] = __float2half_rn(r); break;
+    case ST_BF16: ((__nv_bfloat16*)plow)[i] = __float2bfloat16_rn(r); break;
+    default: ((float*)plow)[i] = r; break;
+  }
 }
 
 // r = b - A x in fp64 (residual recomputation), with ||r||^2 and, when p2 >= 0, sigma partials.
 // With copy_p the new residual is also written to p (warm-start initialisation).
 template <int K>
-__device__ void true_res_vec(const DevSys& S, Rows R, int p2, int p4, bool copy_p, double& rr, double& sd) {
+__device__ void true_res_vec(const DevSys& S, Rows R, int p2, int p4, bool copy_p, double& rr, DotAcc& sg) {
   constexpr int NG = kThreads / K;
   const int lane = threadIdx.x & (K - 1);
   const int grp = threadIdx.x / K;
@@ -356,19 +420,19 @@ __device__ void true_res_vec(const DevSys& S, Rows R, int p2, int p4, bool copy_
       S.r[row] = ri;
       if (copy_p) S.p[row] = ri;
       rr = fma(ri, ri, rr);
-      if (p2 >= 0) sigma_term(ri, p2, p4, sd);
+      if (p2 >= 0) sigma_term(ri, p2, p4, sg);
     }
   }
 }
 
-__device__ void true_res_rows(const DevSys& S, Rows R, int p2, int p4, bool copy_p, double& rr, double& sd) {
+__device__ void true_res_rows(const DevSys& S, Rows R, int p2, int p4, bool copy_p, double& rr, DotAcc& sg) {
   switch (S.A.lanes[F64]) {
-    case 1: true_res_vec<1>(S, R, p2, p4, copy_p, rr, sd); break;
-    case 2: true_res_vec<2>(S, R, p2, p4, copy_p, rr, sd); break;
-    case 4: true_res_vec<4>(S, R, p2, p4, copy_p, rr, sd); break;
-    case 8: true_res_vec<8>(S, R, p2, p4, copy_p, rr, sd); break;
-    case 16: true_res_vec<16>(S, R, p2, p4, copy_p, rr, sd); break;
-    default: true_res_vec<32>(S, R, p2, p4, copy_p, rr, sd); break;
+    case 1: true_res_vec<1>(S, R, p2, p4, copy_p, rr, sg); break;
+    case 2: true_res_vec<2>(S, R, p2, p4, copy_p, rr, sg); break;
+    case 4: true_res_vec<4>(S, R, p2, p4, copy_p, rr, sg); break;
+    case 8: true_res_vec<8>(S, R, p2, p4, copy_p, rr, sg); break;
+    case 16: true_res_vec<16>(S, R, p2, p4, copy_p, rr, sg); break;
+    default: true_res_vec<32>(S, R, p2, p4, copy_p, rr, sg); break;
   }
 }
 
@@ -684,7 +748,18 @@ __device__ __forceinline__ bool team_step(const Launch& L, const TeamCtx& T, Sys
   return ok;
 }
 
-__device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& sm) {
+// Stage-C stamp: phase C of the finished iteration closes at this barrier.
+__device__ __forceinline__ void stamp_c(const DevSys& S, SysState* st) {
+  if (threadIdx.x == 0) {
+    const unsigned d = stamp(st);
+    const int kd = st->k - 1;
+    if (S.hist && kd >= 0 && kd < S.hist_cap) S.hist[kd].ns_c = d;
+  }
+}
+
+constexpr int kUnroll = 4;  // rows per thread in flight in the vector phases
+
+__device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& sm, const StreamCtx* sc) {
   const DevSys& S = L.sys[sid];
   SysState* st = L.st + sid;
   const OptView& o = L.opt;
@@ -697,7 +772,8 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
 
   // ---- initialisation: x_0, r_0 = b - A x_0, p_0 = r_0, ||b||^2, sigma_0 = ||r_0||^2 ----
   {
-    double bb = 0.0, rr = 0.0, sd = 0.0;
+    double bb = 0.0, rr = 0.0;
+    DotAcc unused{0.0, 0.f, 0.f};
     for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
       const double bi = __ldg(S.b + i);
       bb = fma(bi, bi, bb);
@@ -708,7 +784,7 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
         rr = fma(bi, bi, rr);
       }
     }
-    if (o.warm_start) true_res_rows(S, R, -1, -1, true, rr, sd);
+    if (o.warm_start) true_res_rows(S, R, -1, -1, true, rr, unused);
     bb = cta_sum(bb, sm.red);
     rr = cta_sum(rr, sm.red);
     write_partial(L, 0, bb);
@@ -726,35 +802,48 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
     {
       const int p1 = sm.bc.fmt[0];
       if (p1 != F64)
-        for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) store_fmt(S.plow, i, S.p[i], p1);
+        for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) store_low(S.plow, i, S.p[i], p1);
       if (!team_step(L, T, st, sm, [] {})) return false;
     }
     while (true) {
       // ---- phase A: q = fl_p1(A p), nu partials ----
       {
-        double nd = 0.0;
+        DotAcc nu{0.0, 0.f, 0.f};
         const int p1 = sm.bc.fmt[0], p3 = sm.bc.fmt[2];
-        spmv_rows(S, R, p1, p3, nd);
-        write_partial(L, 0, cta_sum(nd, sm.red));
+        spmv_rows(S, R, p1, p3, nu, sc);
+        write_partial(L, 0, cta_dot(nu, sm.red));
         if (!team_step(L, T, st, sm, [&] { step_A(L, S, st, team_sum(L, T, 0, sm.red)); })) return false;
         if (sm.bc.mode != M_CONT) break;
       }
-      // ---- phase B: r -= alpha q, ||r||^2, sigma partials ----
+      // ---- phase B: r -= alpha q (fp64), ||r||^2 (fp64), sigma partials ----
       {
         const double alpha = sm.bc.alpha;
         const int p1 = sm.bc.fmt[0], p2 = sm.bc.fmt[1], p4 = sm.bc.fmt[3];
-        const bool scaled = row_scaled(p1);
-        double rr = 0.0, sd = 0.0;
-        for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
-          double qv = load_fmt(S.q, i, p1);
-          if (scaled) qv *= pow2(__ldg(S.A.rexp + i));
-          const double ri = fma(-alpha, qv, S.r[i]);
-          S.r[i] = ri;
-          rr = fma(ri, ri, rr);
-          sigma_term(ri, p2, p4, sd);
+        double rr = 0.0;
+        DotAcc sg{0.0, 0.f, 0.f};
+        for (int i0 = R.r0 + threadIdx.x; i0 < R.r1; i0 += kUnroll * kThreads) {
+          double qv[kUnroll], ro[kUnroll];
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            const int i = i0 + u * kThreads;
+            if (i < R.r1) {
+              qv[u] = load_q(S, i, p1);
+              ro[u] = S.r[i];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            const int i = i0 + u * kThreads;
+            if (i < R.r1) {
+              const double ri = fma(-alpha, qv[u], ro[u]);
+              S.r[i] = ri;
+              rr = fma(ri, ri, rr);
+              sigma_term(ri, p2, p4, sg);
+            }
+          }
         }
         rr = cta_sum(rr, sm.red);
-        const double sp = cta_sum(sd, sm.red);
+        const double sp = cta_dot(sg, sm.red);
         write_partial(L, 0, rr);
         write_partial(L, 1, sp);
         if (!team_step(L, T, st, sm, [&] {
@@ -766,26 +855,33 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
       }
       const int mode = sm.bc.mode;
       if (mode == M_CONT) {
-        // ---- phase C: x += alpha p; p = z + beta p; p in the next product's format ----
+        // ---- phase C: x += alpha p; p = z + beta p (fp64); p in the next product's format ----
         const double alpha = sm.bc.alpha, beta = sm.bc.beta;
-        // bc.fmt holds the next action; z = fl_p2(r) uses the finished iteration's p2.
-        const int p1n = sm.bc.fmt[0];
-        const int p2 = sm.bc.zfmt;
-        for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
-          const double pi = S.p[i];
-          S.x[i] = fma(alpha, pi, S.x[i]);
-          const double pn = fma(beta, pi, round_fmt(S.r[i], p2));
-          S.p[i] = pn;
-          if (p1n != F64) store_fmt(S.plow, i, pn, p1n);
+        const int p1n = sm.bc.fmt[0];  // next action's product format
+        const int p2 = sm.bc.zfmt;     // z = fl_p2(r) of the finished iteration
+        for (int i0 = R.r0 + threadIdx.x; i0 < R.r1; i0 += kUnroll * kThreads) {
+          double pv[kUnroll], xv[kUnroll], rv[kUnroll];
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            const int i = i0 + u * kThreads;
+            if (i < R.r1) {
+              pv[u] = S.p[i];
+              xv[u] = S.x[i];
+              rv[u] = S.r[i];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            const int i = i0 + u * kThreads;
+            if (i < R.r1) {
+              S.x[i] = fma(alpha, pv[u], xv[u]);
+              const double pn = fma(beta, pv[u], z_of(rv[u], p2));
+              S.p[i] = pn;
+              if (p1n != F64) store_low(S.plow, i, pn, p1n);
+            }
+          }
         }
-        if (!team_step(L, T, st, sm, [&] {
-              if (threadIdx.x == 0) {
-                const unsigned d = stamp(st);
-                const int kd = st->k - 1;
-                if (S.hist && kd >= 0 && kd < S.hist_cap) S.hist[kd].ns_c = d;
-              }
-            }))
-          return false;
+        if (!team_step(L, T, st, sm, [&] { stamp_c(S, st); })) return false;
         if (sm.bc.k >= S.max_iter) break;
         continue;
       }
@@ -800,10 +896,11 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
       // ---- phase T: r = b - A x (fp64), ||r||^2, sigma partials ----
       {
         const int p2 = sm.bc.fmt[1], p4 = sm.bc.fmt[3];
-        double rr = 0.0, sd = 0.0;
-        true_res_rows(S, R, p2, p4, false, rr, sd);
+        double rr = 0.0;
+        DotAcc sg{0.0, 0.f, 0.f};
+        true_res_rows(S, R, p2, p4, false, rr, sg);
         rr = cta_sum(rr, sm.red);
-        const double sp = cta_sum(sd, sm.red);
+        const double sp = cta_dot(sg, sm.red);
         write_partial(L, 0, rr);
         write_partial(L, 1, sp);
         if (!team_step(L, T, st, sm, [&] {
@@ -818,9 +915,9 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
         const int p1n = sm.bc.fmt[0];
         const int p2 = sm.bc.zfmt;
         for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
-          const double pn = round_fmt(S.r[i], p2);
+          const double pn = z_of(S.r[i], p2);
           S.p[i] = pn;
-          if (p1n != F64) store_fmt(S.plow, i, pn, p1n);
+          if (p1n != F64) store_low(S.plow, i, pn, p1n);
         }
         if (!team_step(L, T, st, sm, [] {})) return false;
         if (sm.bc.k >= S.max_iter) break;
@@ -832,11 +929,12 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
 
   // ---- final: ||b - A x|| in fp64 unless already known ----
   {
-    double rr = 0.0, sd = 0.0;
+    double rr = 0.0;
+    DotAcc unused{0.0, 0.f, 0.f};
     int known = 0;
     if (threadIdx.x == 0) known = *(volatile int*)&st->true_known;
     known = __syncthreads_or(known);
-    if (!known) true_res_rows(S, R, -1, -1, false, rr, sd);
+    if (!known) true_res_rows(S, R, -1, -1, false, rr, unused);
     rr = cta_sum(rr, sm.red);
     write_partial(L, 0, rr);
     if (!team_step(L, T, st, sm, [&] { step_final(L, S, st, sid, team_sum(L, T, 0, sm.red)); })) return false;
@@ -846,6 +944,18 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
 
 __global__ void __launch_bounds__(kThreads) cg_persistent(const Launch L) {
   __shared__ Smem sm;
+  extern __shared__ __align__(128) unsigned char dyn[];
+  StreamCtx scx{dyn, sm.mbar, &sm.mbar_phase, L.err, L.stream_stage};
+  if (L.stream_stage > 0) {
+    if (threadIdx.x == 0) {
+      mbar_init(sm.mbar + 0, 1);
+      mbar_init(sm.mbar + 1, 1);
+      mbar_fence_init();
+      sm.mbar_phase = 0;
+    }
+    __syncthreads();
+  }
+  const StreamCtx* sc = L.stream_stage > 0 ? &scx : nullptr;
   TeamCtx T;
   T.team = L.cta_team[blockIdx.x];
   T.rank = L.cta_rank[blockIdx.x];
@@ -853,7 +963,7 @@ __global__ void __launch_bounds__(kThreads) cg_persistent(const Launch L) {
   T.first = L.team_first[T.team];
   T.bar = L.bars + (long long)T.team * kBarStride;
   for (int i = L.team_sys_off[T.team]; i < L.team_sys_off[T.team + 1]; ++i) {
-    if (!solve_system(L, T, L.team_sys[i], sm)) return;
+    if (!solve_system(L, T, L.team_sys[i], sm, sc)) return;
   }
 }
 
@@ -866,6 +976,10 @@ cudaError_t launch_cg(const Launch& L, int grid, size_t smem, cudaStream_t s) {
 
 cudaError_t cg_occupancy(int* blocks_per_sm, size_t smem) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, cg_persistent, kThreads, smem);
+}
+
+cudaError_t cg_set_smem_limit(size_t bytes) {
+  return cudaFuncSetAttribute(cg_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 size_t cg_static_smem() { return sizeof(Smem); }

@@ -131,6 +131,129 @@ __device__ __forceinline__ void store_fmt(void* p, long long i, double v, int f)
   }
 }
 
+// ---- fp32-domain conversions (no fp64 instruction on the common path) ---------------
+// GB300 executes fp64 arithmetic and fp64 conversions at a small fraction of the fp32 rate,
+// so the per-row work converts between fp32 and fp64 by assembling bit patterns and rounds
+// fp64 values onto the 16-bit formats through fp32.
+
+// Exact fp32 -> fp64.
+__device__ __forceinline__ double f2d(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned a = u & 0x7fffffffu;
+  if (a - 0x00800000u < 0x7f000000u) {  // normal
+    const unsigned hi = (u & 0x80000000u) | ((a >> 3) + (896u << 20));
+    return __hiloint2double((int)hi, (int)(a << 29));
+  }
+  if (a == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  return (double)v;  // subnormal, infinite or NaN
+}
+
+// x * 2^e for an fp64 x whose result stays in the normal range (exponent-field add);
+// otherwise a multiplication.
+__device__ __forceinline__ double scale2(double x, int e) {
+  const int hi = __double2hiint(x);
+  const int ex = (hi >> 20) & 0x7ff;
+  if (e == 0 || x == 0.0) return x;
+  if (ex > 0 && ex < 0x7ff && ex + e > 0 && ex + e < 0x7ff) return __hiloint2double(hi + (e << 20), __double2loint(x));
+  return x * __longlong_as_double((long long)((unsigned long long)(e + 1023) << 52));
+}
+
+// Truncation of x onto fp32 with the last bit set when bits were dropped ("round to odd").
+// Valid when |x| lies in the fp32 normal range or x = 0; returns false otherwise. Rounding
+// the result to nearest onto a format with at most 22 significand digits gives the correctly
+// rounded value of x (Boldo and Melquiond, "Emulation of FMA and correctly rounded sums:
+// proved algorithms using rounding to odd", IEEE Trans. Computers 57(4), 2008).
+__device__ __forceinline__ bool d2f_odd(double x, float& out) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned ex = (hi >> 20) & 0x7ffu;
+  if (ex >= 897u && ex <= 1150u) {  // 2^-126 <= |x| < 2^128
+    unsigned f = (hi & 0x80000000u) | ((ex - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    f |= (lo & 0x1fffffffu) ? 1u : 0u;
+    out = __uint_as_float(f);
+    return true;
+  }
+  if ((hi & 0x7fffffffu) == 0u && lo == 0u) {
+    out = __uint_as_float(hi);
+    return true;
+  }
+  return false;
+}
+
+// fl_fp32(x), round to nearest even, for |x| in the fp32 normal range (false otherwise).
+__device__ __forceinline__ bool d2f_rn(double x, float& out) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned ex = (hi >> 20) & 0x7ffu;
+  if (ex >= 897u && ex <= 1150u) {
+    unsigned f = (hi & 0x80000000u) | ((ex - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1fffffffu;  // dropped bits; half = 0x10000000
+    if (rest > 0x10000000u || (rest == 0x10000000u && (f & 1u))) ++f;  // carries into the exponent
+    out = __uint_as_float(f);
+    return true;
+  }
+  if ((hi & 0x7fffffffu) == 0u && lo == 0u) {
+    out = __uint_as_float(hi);
+    return true;
+  }
+  return false;
+}
+
+// fl_f(v) of an fp32 value (one rounding) for f in {fp16, bf16, tf32, fp32} (and the
+// row-scaled variants).
+__device__ __forceinline__ float round_f2f(float v, int f) {
+  switch (base_fmt(f)) {
+    case F16: return __half2float(__float2half_rn(v));
+    case BF16: return __bfloat162float(__float2bfloat16_rn(v));
+    case TF32: return round_tf32(v);
+    default: return v;
+  }
+}
+
+// fl_f(x) of an fp64 value, returned as fp32 (exact), for f other than fp64.
+__device__ __forceinline__ float round_d2f(double x, int f) {
+  float o;
+  if (base_fmt(f) == F32) {
+    if (d2f_rn(x, o)) return o;
+  } else if (d2f_odd(x, o)) {
+    return round_f2f(o, f);
+  }
+  return (float)round_fmt(x, f);  // outside the fp32 normal range: exact bit-level rounding
+}
+
+// Value set of format a contains that of format b (so rounding onto a is the identity on b).
+__host__ __device__ constexpr bool contains_fmt(int a, int b) {
+  return base_fmt(a) == F64 || base_fmt(a) == base_fmt(b) ||
+         (base_fmt(a) == F32 && base_fmt(b) != F64) ||
+         (base_fmt(a) == TF32 && (base_fmt(b) == F16 || base_fmt(b) == BF16));
+}
+
+// s + t = a + b exactly (Knuth's TwoSum), fp32, without contraction.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Rounds the exact value s + e of a compensated fp32 pair onto format f (fp32 result):
+// fp32 takes fl(s + e); the coarser formats round the round-to-odd value of s + e.
+__device__ __forceinline__ float round_pair(float s, float e, int f) {
+  float hi, lo;
+  two_sum(s, e, hi, lo);
+  if (base_fmt(f) == F32 || !isfinite(hi)) return hi;
+  unsigned b = __float_as_uint(hi);
+  if (lo != 0.f && !(b & 1u)) b += ((lo > 0.f) == (hi > 0.f)) ? 1u : 0xffffffffu;
+  return round_f2f(__uint_as_float(b), f);
+}
+
+// Compensated fp32 accumulation of the product a * b (exact for inputs of at most 12
+// significand digits; for fp32 inputs the FMA error of the product is carried too).
+__device__ __forceinline__ void acc2(float a, float b, bool exact_product, float& s, float& c) {
+  const float p = __fmul_rn(a, b);
+  float t;
+  two_sum(s, p, s, t);
+  if (!exact_product) t = __fadd_rn(t, __fmaf_rn(a, b, -p));
+  c = __fadd_rn(c, t);
+}
+
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as easy as 1, 2, 3",
 // SC'11): ten rounds of two 64x64->128-bit multiplications with a Weyl-sequence key schedule.
 struct U64x4 { unsigned long long v[4]; };

@@ -19,6 +19,7 @@ constexpr int kNSlot = 4;           // partial sums per CTA and phase
 constexpr int kNFeat = 16;          // MLP input features
 constexpr int kMaxHidden = 128;     // MLP hidden width bound
 constexpr int kBarStride = 32;      // uint32 words between team barriers (128 bytes)
+constexpr int kStageBytes = 54 * 1024;  // one stage of the stream schedule's shared-memory ring
 
 enum Sched : int { SCHED_VECTOR = 0, SCHED_STREAM = 1 };
 
@@ -39,8 +40,8 @@ struct DevMatrix {
   const short* rexp;        // e_i of the row scales s_i = 2^e_i of the row-scaled formats
   int sched[8];             // SpMV schedule per format
   int lanes[8];             // lanes per row per format
-  int tile_rows[8];         // stream schedule: rows per shared-memory tile
-  int tile_bytes[8];        // stream schedule: bytes of one tile buffer (values + columns)
+  int tile_rows[8];         // stream schedule: rows per shared-memory tile (kThreads / lanes)
+  int tile_bytes[8];        // stream schedule: bytes of a stage's value region (columns follow)
 };
 
 // One transition of an exploration episode (Algorithm 1), recorded for the end-of-round merge.
@@ -139,7 +140,7 @@ struct Launch {
   PolicyView pol;
   OptView opt;
   int train;                // 1: epsilon-greedy episode with online private updates
-  int pad;
+  int stream_stage;         // bytes of one stage of the stream ring (0: no stream schedule)
   unsigned long long episode;
   double eps;
   long long timeout_cycles;
@@ -160,7 +161,9 @@ cudaError_t launch_row_features(int n, const int* rp, const int* ci, const doubl
                                 cudaStream_t s);
 cudaError_t launch_to_format(const double* x, void* xlow, int n, int f, cudaStream_t s);
 cudaError_t launch_from_q(const void* q, const short* rexp, double* y, int n, int f, cudaStream_t s);
-cudaError_t launch_spmv_only(const DevSys& S, int fmt, int grid, cudaStream_t s);
+cudaError_t launch_spmv_only(const DevSys& S, int fmt, int grid, int stream_stage, unsigned* err, cudaStream_t s);
+cudaError_t spmv_occupancy(int* blocks_per_sm, size_t smem);
+cudaError_t set_smem_limits(size_t bytes);
 cudaError_t launch_qcopy(const double* Q, double* Qpriv, int nlanes, long long qsize, cudaStream_t s);
 cudaError_t launch_qmerge(double* Q, int* visits, const Transition* trans, const SysState* st, int nlanes, int cap,
                           int S, int nprec, double lr, double gamma, cudaStream_t s);

@@ -126,8 +126,14 @@ __global__ void row_features(int n, const int* __restrict__ rp, const int* __res
 
 // x (fp64) -> fl_f(x) stored in format f.
 __global__ void to_format(const double* __restrict__ x, void* xlow, int n, int f) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    store_fmt(xlow, i, x[i], f);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float r = round_d2f(x[i], f);
+    switch (store_of(f)) {
+      case ST_HALF: ((__half*)xlow)[i] = __float2half_rn(r); break;
+      case ST_BF16: ((__nv_bfloat16*)xlow)[i] = __float2bfloat16_rn(r); break;
+      default: ((float*)xlow)[i] = r; break;
+    }
+  }
 }
 
 // y = q (stored in format f) as fp64, times the row scale for the row-scaled formats.
@@ -140,15 +146,25 @@ __global__ void from_q(const void* q, const short* __restrict__ rexp, double* y,
 }
 
 // Standalone product with the same per-CTA row split and row code as the solver.
-__global__ void __launch_bounds__(kThreads) spmv_standalone(const DevSys S, int fmt) {
+__global__ void __launch_bounds__(kThreads) spmv_standalone(const DevSys S, int fmt, int stream_stage, unsigned* err) {
   __shared__ int r01[2];
+  __shared__ unsigned long long mbar[2];
+  __shared__ unsigned phase;
+  extern __shared__ __align__(128) unsigned char dyn[];
   if (threadIdx.x == 0) {
     r01[0] = part_row(S.A.rp, S.A.n, S.A.nnz, blockIdx.x, gridDim.x);
     r01[1] = part_row(S.A.rp, S.A.n, S.A.nnz, blockIdx.x + 1, gridDim.x);
+    if (stream_stage > 0) {
+      mbar_init(mbar + 0, 1);
+      mbar_init(mbar + 1, 1);
+      mbar_fence_init();
+      phase = 0;
+    }
   }
   __syncthreads();
-  double nd = 0.0;
-  spmv_rows(S, Rows{r01[0], r01[1]}, fmt, -1, nd);
+  StreamCtx scx{dyn, mbar, &phase, err, stream_stage};
+  DotAcc nu{0.0, 0.f, 0.f};
+  spmv_rows(S, Rows{r01[0], r01[1]}, fmt, -1, nu, stream_stage > 0 ? &scx : nullptr);
 }
 
 __global__ void qcopy_kernel(const double* __restrict__ Q, double* Qpriv, int nlanes, long long qsize) {
@@ -254,11 +270,23 @@ cudaError_t launch_from_q(const void* q, const short* rexp, double* y, int n, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_spmv_only(const DevSys& S, int fmt, int grid, cudaStream_t s) {
+cudaError_t launch_spmv_only(const DevSys& S, int fmt, int grid, int stream_stage, unsigned* err, cudaStream_t s) {
   if (S.A.n == 0) return cudaSuccess;
   cudaGetLastError();
-  spmv_standalone<<<grid, kThreads, 0, s>>>(S, fmt);
+  spmv_standalone<<<grid, kThreads, stream_stage > 0 ? 2 * (size_t)stream_stage : 0, s>>>(S, fmt, stream_stage, err);
   return cudaGetLastError();
+}
+
+cudaError_t spmv_occupancy(int* blocks_per_sm, size_t smem) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, spmv_standalone, kThreads, smem);
+}
+
+cudaError_t cg_set_smem_limit(size_t bytes);
+
+cudaError_t set_smem_limits(size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(spmv_standalone, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  return cg_set_smem_limit(bytes);
 }
 
 cudaError_t launch_qcopy(const double* Q, double* Qpriv, int nlanes, long long qsize, cudaStream_t s) {

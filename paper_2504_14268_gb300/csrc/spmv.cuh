@@ -28,10 +28,17 @@ __device__ __forceinline__ int part_row(const int* rp, int n, long long nnz, int
   return lo;
 }
 
-// nu term of row i: fl_p3(p_i) fl_p3(q_i), products of rounded inputs accumulated in fp64
-// (exact for every format of the set), the sum rounded to p3 by the caller.
-__device__ __forceinline__ void nu_term(double pi, double qi, int p3, double& nd) {
-  nd = fma(round_fmt(pi, p3), round_fmt(qi, p3), nd);
+// Accumulator of a dot product term by term: fp64 for the fp64 format, otherwise a
+// compensated fp32 pair of the products of rounded inputs (exact products for the 16-bit
+// formats and tf32, FMA-corrected for fp32), i.e. the "Dot2" scheme of Ogita, Rump and
+// Oishi (SIAM J. Sci. Comput. 26(6), 2005) carried out in fp32.
+struct DotAcc {
+  double d;
+  float s, c;
+};
+
+__device__ __forceinline__ void dot_low(DotAcc& a, float x, float y, int f) {
+  acc2(x, y, base_fmt(f) != F32, a.s, a.c);
 }
 
 // 2^e as fp64 (e in [-1022, 1023]).
@@ -39,103 +46,250 @@ __device__ __forceinline__ double pow2(int e) {
   return __longlong_as_double((long long)((unsigned long long)(e + 1023) << 52));
 }
 
-// Rounds the row sum onto the product's format p1 (one rounding), stores it in q and
-// returns the row's value of q (times 2^e_i for the row-scaled formats) as fp64.
-__device__ __forceinline__ double store_q(void* q, int i, double tot, int p1, double scale) {
-  const double r = round_fmt(tot, p1);
+// Row finished with a compensated fp32 pair (sp, ep): q_i = fl_p1(sp + ep) (one rounding of
+// the pair's exact value), stored in p1's storage; then the row's nu term fl_p3(p_i) fl_p3(q_i)
+// (q_i includes the row scale 2^e_i of the row-scaled formats).
+__device__ __forceinline__ void finish_row_low(const DevSys& S, int row, float sp, float ep, int p1, int nu_fmt,
+                                               DotAcc& nu) {
+  const float qf = round_pair(sp, ep, p1);
   switch (store_of(p1)) {
-    case ST_HALF: store_exact((__half*)q, i, r); break;
-    case ST_BF16: store_exact((__nv_bfloat16*)q, i, r); break;
-    case ST_FLOAT: store_exact((float*)q, i, r); break;
-    default: store_exact((double*)q, i, r); break;
+    case ST_HALF: ((__half*)S.q)[row] = __float2half_rn(qf); break;
+    case ST_BF16: ((__nv_bfloat16*)S.q)[row] = __float2bfloat16_rn(qf); break;
+    default: ((float*)S.q)[row] = qf; break;
   }
-  return r * scale;
+  if (nu_fmt < 0) return;
+  const double pi = S.p[row];
+  const bool scaled = row_scaled(p1);
+  if (nu_fmt == F64) {
+    double qd = f2d(qf);
+    if (scaled) qd = scale2(qd, __ldg(S.A.rexp + row));
+    nu.d = fma(pi, qd, nu.d);
+  } else {
+    float b;
+    if (scaled) b = round_d2f(scale2(f2d(qf), __ldg(S.A.rexp + row)), nu_fmt);
+    else b = contains_fmt(nu_fmt, p1) ? qf : round_f2f(qf, nu_fmt);
+    dot_low(nu, round_d2f(pi, nu_fmt), b, nu_fmt);
+  }
 }
 
-// s + t = a + b exactly (Knuth's TwoSum), fp32, without contraction.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+// Row finished with an fp64 sum (fp64 product).
+__device__ __forceinline__ void finish_row_64(const DevSys& S, int row, double tot, int nu_fmt, DotAcc& nu) {
+  ((double*)S.q)[row] = tot;
+  if (nu_fmt < 0) return;
+  const double pi = S.p[row];
+  if (nu_fmt == F64) nu.d = fma(pi, tot, nu.d);
+  else dot_low(nu, round_d2f(pi, nu_fmt), round_d2f(tot, nu_fmt), nu_fmt);
 }
 
-// Sub-warp vector CSR: K lanes per row, rows strided over the CTA.
-// fp64 values: fp64 accumulation. Lower formats: the products of the rounded inputs are
-// summed with a compensated fp32 accumulator (sum and error term, TwoSum; fp32 products
-// carry their FMA error term too), i.e. the dot product "Dot2" of Ogita, Rump and Oishi
-// (SIAM J. Sci. Comput. 2005) in fp32, so the row sum is accurate to about 2^-48 and its
-// single rounding onto p1 matches a wide-accumulator sum. The K lane results are combined
-// by an xor butterfly of (sum, error) pairs. With nu_fmt < 0 no nu partial is formed.
+// Products of one row slice accumulated by one lane. fp64: fp64 accumulation. Lower
+// formats: compensated fp32 pair (sum, error): the products of the rounded inputs are exact
+// for the 16-bit formats and tf32 and carry their FMA error for fp32, so the row sum is
+// accurate to about 2^-48 before its single rounding onto p1.
+template <typename VT>
+struct RowAcc {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(VT a, VT x) {
+    const float af = to_acc(a), xf = to_acc(x);
+    acc2(af, xf, sizeof(VT) == 2, s, c);
+  }
+  template <int K>
+  __device__ __forceinline__ void reduce(unsigned mask) {
+#pragma unroll
+    for (int o = K / 2; o > 0; o >>= 1) {
+      const float s2 = __shfl_xor_sync(mask, s, o), c2 = __shfl_xor_sync(mask, c, o);
+      float t;
+      two_sum(s, s2, s, t);
+      c = __fadd_rn(__fadd_rn(c, c2), t);
+    }
+  }
+  __device__ __forceinline__ void finish(const DevSys& S, int row, int p1, int nu_fmt, DotAcc& nu) const {
+    finish_row_low(S, row, s, isfinite(s) ? c : 0.f, p1, nu_fmt, nu);
+  }
+};
+
+template <>
+struct RowAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double x) { s = fma(a, x, s); }
+  template <int K>
+  __device__ __forceinline__ void reduce(unsigned mask) {
+#pragma unroll
+    for (int o = K / 2; o > 0; o >>= 1) s += __shfl_xor_sync(mask, s, o);
+  }
+  __device__ __forceinline__ void finish(const DevSys& S, int row, int, int nu_fmt, DotAcc& nu) const {
+    finish_row_64(S, row, s, nu_fmt, nu);
+  }
+};
+
+// ---- bulk copies into shared memory (cp.async.bulk + mbarrier) ------------------------
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// Global -> shared copy of `bytes` (multiple of 16, both addresses 16-byte aligned),
+// completing on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Shared-memory ring of the stream schedule: two stages of `stage_bytes`; in a stage the
+// value region comes first (DevMatrix::tile_bytes[format] bytes), then the column region.
+// `phase` (shared memory) holds the parity bit each stage's mbarrier waits for next; it
+// persists across calls.
+struct StreamCtx {
+  unsigned char* buf;
+  unsigned long long* bar;
+  unsigned* phase;
+  unsigned* err;
+  int stage_bytes;
+};
+
+// Bounded wait on a stage's mbarrier; on timeout the device status word is set.
+__device__ __forceinline__ void stage_wait(const StreamCtx& sc, int stage) {
+  const unsigned par = (*sc.phase >> stage) & 1u;
+  unsigned spins = 0;
+  while (!mbar_try_wait(sc.bar + stage, par)) {
+    if (++spins > (1u << 26)) {
+      if (sc.err) atomicCAS(sc.err, 0u, 1u);
+      break;
+    }
+  }
+}
+
+// Sub-warp vector CSR: K lanes per row, rows strided over the CTA, operands read from
+// global memory. The K lane accumulators are combined by an xor butterfly. With nu_fmt < 0
+// no nu partial is formed.
 template <typename VT, int K>
 __device__ void spmv_vec(const DevSys& S, const VT* __restrict__ vals, const VT* xin, Rows R, int p1,
-                         int nu_fmt, double& nd) {
+                         int nu_fmt, DotAcc& nu) {
   constexpr int NG = kThreads / K;
   const int lane = threadIdx.x & (K - 1);
   const int grp = threadIdx.x / K;
   const unsigned mask = (K == 32) ? kFull : (((1u << K) - 1u) << ((threadIdx.x & 31) & ~(K - 1)));
   const int* __restrict__ rp = S.A.rp;
   const int* __restrict__ ci = S.A.ci;
-  const bool scaled = row_scaled(p1);
-  const short* __restrict__ rexp = S.A.rexp;
   for (int row = R.r0 + grp; row < R.r1; row += NG) {
     const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
-    double tot;
-    if constexpr (sizeof(VT) == 8) {
-      double acc = 0.0;
-      for (int e = e0 + lane; e < e1; e += K) acc = fma(__ldg(vals + e), xin[__ldg(ci + e)], acc);
-#pragma unroll
-      for (int o = K / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(mask, acc, o);
-      tot = acc;
-    } else {
-      float sum = 0.f, err = 0.f;
-      for (int e = e0 + lane; e < e1; e += K) {
-        const float a = to_acc(__ldg(vals + e)), xv = to_acc(xin[__ldg(ci + e)]);
-        const float pr = __fmul_rn(a, xv);
-        float t;
-        two_sum(sum, pr, sum, t);
-        if constexpr (sizeof(VT) == 4) t = __fadd_rn(t, __fmaf_rn(a, xv, -pr));
-        err = __fadd_rn(err, t);
-      }
-#pragma unroll
-      for (int o = K / 2; o > 0; o >>= 1) {
-        const float s2 = __shfl_xor_sync(mask, sum, o), e2 = __shfl_xor_sync(mask, err, o);
-        float t;
-        two_sum(sum, s2, sum, t);
-        err = __fadd_rn(__fadd_rn(err, e2), t);
-      }
-      // an infinite or NaN partial (format overflow) makes the error term meaningless
-      tot = isfinite(sum) ? (double)sum + (double)err : (double)sum;
+    RowAcc<VT> acc;
+    for (int e = e0 + lane; e < e1; e += K) acc.add(__ldg(vals + e), xin[__ldg(ci + e)]);
+    acc.template reduce<K>(mask);
+    if (lane == 0) acc.finish(S, row, p1, nu_fmt, nu);
+  }
+}
+
+// Staged stream CSR: the CTA's rows are cut into tiles of kThreads / K rows; the tile's
+// contiguous value and column ranges are fetched into a two-stage shared-memory ring with
+// bulk copies (16-byte aligned by rounding the byte ranges out; the matrix arrays are
+// padded so the rounded ranges stay in bounds) while the previous tile is processed. K lanes
+// per row read the row from shared memory (strided, conflict-free) and gather x.
+template <typename VT, int K>
+__device__ void spmv_stream(const DevSys& S, const VT* __restrict__ vals, const VT* xin, Rows R, int p1,
+                            int nu_fmt, DotAcc& nu, const StreamCtx& sc) {
+  constexpr int TR = kThreads / K;
+  const int nrows = R.r1 - R.r0;
+  const int ntiles = nrows > 0 ? (nrows + TR - 1) / TR : 0;
+  if (ntiles == 0) return;
+  const int lane = threadIdx.x & (K - 1);
+  const int grp = threadIdx.x / K;
+  const unsigned mask = (K == 32) ? kFull : (((1u << K) - 1u) << ((threadIdx.x & 31) & ~(K - 1)));
+  const int* __restrict__ rp = S.A.rp;
+  const int* __restrict__ ci = S.A.ci;
+  const int vreg = S.A.tile_bytes[p1];
+  auto issue = [&](int t, int stage) {
+    const int ra = R.r0 + t * TR;
+    const int rb = min(ra + TR, R.r1);
+    const long long e0 = __ldg(rp + ra), e1 = __ldg(rp + rb);
+    const long long vlo = (e0 * (long long)sizeof(VT)) & ~15ll, vhi = (e1 * (long long)sizeof(VT) + 15) & ~15ll;
+    const long long clo = (e0 * 4) & ~15ll, chi = (e1 * 4 + 15) & ~15ll;
+    unsigned char* base = sc.buf + (size_t)stage * sc.stage_bytes;
+    fence_proxy_async();
+    mbar_expect_tx(sc.bar + stage, (unsigned)((vhi - vlo) + (chi - clo)));
+    bulk_g2s(base, (const char*)vals + vlo, (unsigned)(vhi - vlo), sc.bar + stage);
+    bulk_g2s(base + vreg, (const char*)ci + clo, (unsigned)(chi - clo), sc.bar + stage);
+  };
+  if (threadIdx.x == 0) {
+    issue(0, 0);
+    if (ntiles > 1) issue(1, 1);
+  }
+  for (int t = 0; t < ntiles; ++t) {
+    const int stage = t & 1;
+    stage_wait(sc, stage);
+    const int ra = R.r0 + t * TR;
+    const int rb = min(ra + TR, R.r1);
+    const int e0 = __ldg(rp + ra);
+    const unsigned char* base = sc.buf + (size_t)stage * sc.stage_bytes;
+    const int ev0 = (int)(((long long)e0 * (long long)sizeof(VT)) & ~15ll) / (int)sizeof(VT);
+    const int ec0 = e0 & ~3;
+    const VT* sv = (const VT*)base - ev0;
+    const int* scol = (const int*)(base + vreg) - ec0;
+    const int row = ra + grp;
+    if (row < rb) {
+      const int rs = __ldg(rp + row), re = __ldg(rp + row + 1);
+      RowAcc<VT> acc;
+      for (int e = rs + lane; e < re; e += K) acc.add(sv[e], xin[scol[e]]);
+      acc.template reduce<K>(mask);
+      if (lane == 0) acc.finish(S, row, p1, nu_fmt, nu);
     }
-    if (lane == 0) {
-      const double qv = store_q(S.q, row, tot, p1, scaled ? pow2(__ldg(rexp + row)) : 1.0);
-      if (nu_fmt >= 0) nu_term(S.p[row], qv, nu_fmt, nd);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      *sc.phase ^= (1u << stage);
+      if (t + 2 < ntiles) issue(t + 2, stage);
     }
+    __syncthreads();
   }
 }
 
 template <typename VT>
 __device__ void spmv_dispatch_k(const DevSys& S, const VT* vals, const VT* xin, Rows R, int p1, int nu_fmt,
-                                double& nd) {
+                                DotAcc& nu, const StreamCtx* sc) {
+  if (sc && S.A.sched[p1] == SCHED_STREAM) {
+    switch (S.A.lanes[p1]) {
+      case 1: spmv_stream<VT, 1>(S, vals, xin, R, p1, nu_fmt, nu, *sc); return;
+      case 2: spmv_stream<VT, 2>(S, vals, xin, R, p1, nu_fmt, nu, *sc); return;
+      case 4: spmv_stream<VT, 4>(S, vals, xin, R, p1, nu_fmt, nu, *sc); return;
+      default: spmv_stream<VT, 8>(S, vals, xin, R, p1, nu_fmt, nu, *sc); return;
+    }
+  }
   switch (S.A.lanes[p1]) {
-    case 1: spmv_vec<VT, 1>(S, vals, xin, R, p1, nu_fmt, nd); break;
-    case 2: spmv_vec<VT, 2>(S, vals, xin, R, p1, nu_fmt, nd); break;
-    case 4: spmv_vec<VT, 4>(S, vals, xin, R, p1, nu_fmt, nd); break;
-    case 8: spmv_vec<VT, 8>(S, vals, xin, R, p1, nu_fmt, nd); break;
-    case 16: spmv_vec<VT, 16>(S, vals, xin, R, p1, nu_fmt, nd); break;
-    default: spmv_vec<VT, 32>(S, vals, xin, R, p1, nu_fmt, nd); break;
+    case 1: spmv_vec<VT, 1>(S, vals, xin, R, p1, nu_fmt, nu); break;
+    case 2: spmv_vec<VT, 2>(S, vals, xin, R, p1, nu_fmt, nu); break;
+    case 4: spmv_vec<VT, 4>(S, vals, xin, R, p1, nu_fmt, nu); break;
+    case 8: spmv_vec<VT, 8>(S, vals, xin, R, p1, nu_fmt, nu); break;
+    case 16: spmv_vec<VT, 16>(S, vals, xin, R, p1, nu_fmt, nu); break;
+    default: spmv_vec<VT, 32>(S, vals, xin, R, p1, nu_fmt, nu); break;
   }
 }
 
-// Phase A: q = fl_p1(A fl_p1(p)) for the CTA's rows, plus nu partials.
-__device__ void spmv_rows(const DevSys& S, Rows R, int p1, int nu_fmt, double& nd) {
+// Phase A: q = fl_p1(A fl_p1(p)) for the CTA's rows, plus nu partials. `sc` is the
+// shared-memory ring of the stream schedule (nullptr when the launch has none).
+__device__ void spmv_rows(const DevSys& S, Rows R, int p1, int nu_fmt, DotAcc& nu, const StreamCtx* sc) {
   switch (p1) {
-    case F64: spmv_dispatch_k<double>(S, S.A.v64, S.p, R, p1, nu_fmt, nd); break;
-    case F32: spmv_dispatch_k<float>(S, S.A.v32, (const float*)S.plow, R, p1, nu_fmt, nd); break;
-    case TF32: spmv_dispatch_k<float>(S, S.A.vtf, (const float*)S.plow, R, p1, nu_fmt, nd); break;
-    case F16: spmv_dispatch_k<__half>(S, S.A.v16, (const __half*)S.plow, R, p1, nu_fmt, nd); break;
-    case BF16: spmv_dispatch_k<__nv_bfloat16>(S, S.A.vbf, (const __nv_bfloat16*)S.plow, R, p1, nu_fmt, nd); break;
-    case F16R: spmv_dispatch_k<__half>(S, S.A.v16r, (const __half*)S.plow, R, p1, nu_fmt, nd); break;
-    default: spmv_dispatch_k<__nv_bfloat16>(S, S.A.vbfr, (const __nv_bfloat16*)S.plow, R, p1, nu_fmt, nd); break;
+    case F64: spmv_dispatch_k<double>(S, S.A.v64, S.p, R, p1, nu_fmt, nu, sc); break;
+    case F32: spmv_dispatch_k<float>(S, S.A.v32, (const float*)S.plow, R, p1, nu_fmt, nu, sc); break;
+    case TF32: spmv_dispatch_k<float>(S, S.A.vtf, (const float*)S.plow, R, p1, nu_fmt, nu, sc); break;
+    case F16: spmv_dispatch_k<__half>(S, S.A.v16, (const __half*)S.plow, R, p1, nu_fmt, nu, sc); break;
+    case BF16: spmv_dispatch_k<__nv_bfloat16>(S, S.A.vbf, (const __nv_bfloat16*)S.plow, R, p1, nu_fmt, nu, sc); break;
+    case F16R: spmv_dispatch_k<__half>(S, S.A.v16r, (const __half*)S.plow, R, p1, nu_fmt, nu, sc); break;
+    default: spmv_dispatch_k<__nv_bfloat16>(S, S.A.vbfr, (const __nv_bfloat16*)S.plow, R, p1, nu_fmt, nu, sc); break;
   }
 }
 
