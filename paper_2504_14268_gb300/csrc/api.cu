@@ -146,9 +146,10 @@ int lanes_index(int lanes) { return lanes == 1 ? 0 : lanes == 2 ? 1 : lanes == 4
 int stream_vreg(const mpcg_matrix_s* M, int fmt, int lanes) {
   const int li = lanes_index(lanes);
   if (li < 0) return -1;
+  // a tile's byte range is rounded out to 16-byte boundaries at both ends (up to 30 extra bytes)
   const long long w = M->win[li];
-  const long long vreg = (w * bytes_of(fmt) + 16 + 15) / 16 * 16;
-  const long long creg = (w * 4 + 16 + 15) / 16 * 16;
+  const long long vreg = (w * bytes_of(fmt) + 32 + 15) / 16 * 16;
+  const long long creg = (w * 4 + 32 + 15) / 16 * 16;
   return vreg + creg <= kStageBytes ? (int)vreg : -1;
 }
 
