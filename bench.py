@@ -143,7 +143,7 @@ def cpu_sample(A, b, Q, visits, gpu_iters: int, budget_s: float = 15.0):
     (solves/s extrapolated to the GPU's iteration count, iterations sampled, seconds)."""
     import oracle as O
 
-    o = O.Options(true_res_at_conv=1)
+    o = O.Options(true_res_at_conv=1, on_breakdown=1)
     qt = O.QTable(Q.copy(), visits.copy())
     t0 = time.time()
     O.solve(o, A, b, TAU, 1, qtable=qt)
@@ -230,7 +230,7 @@ def main():
     Z = len(val)
     t_gen = time.time() - t_gen
     Q, visits = load_policy()
-    ctx = M.Context(local, M.Options(true_res_at_conv=1))
+    ctx = M.Context(local, M.Options(true_res_at_conv=1, on_breakdown=1))
     t0 = time.time()
     mat = ctx.matrix((n, torch.as_tensor(rp).cuda(), torch.as_tensor(ci).cuda(), torch.as_tensor(val).cuda()))
     torch.cuda.synchronize()

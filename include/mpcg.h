@@ -108,6 +108,9 @@ typedef struct {
   int32_t true_res_every;  /* >0: replace r by b - A x (fp64) every this many iterations */
   int32_t true_res_at_conv;/* 1: confirm a claimed convergence with b - A x (fp64)      */
   int32_t warm_start;      /* 1: x holds x_0 on entry; 0: x_0 = 0 (Algorithms 1 and 2)  */
+  int32_t on_breakdown;    /* 0: a breakdown ends the solve (paper); 1: inference solves
+                              recompute r = b - A x in fp64, restart with p = r and finish
+                              with every operation in fp64 (at most once per solve)     */
   int32_t mlp_hidden;      /* hidden width of the MLP policy (64)                       */
 } mpcg_options;
 
@@ -118,13 +121,14 @@ typedef struct {
   double rel_res_rec;      /* ||r|| / ||b|| of the recursive residual at the end        */
   double rel_res_true;     /* ||b - A x|| / ||b|| computed in fp64 at the end           */
   int32_t n_true_checks;   /* residual recomputations during the solve                  */
-  int32_t pad;
+  int32_t n_restarts;      /* fp64 restarts after a breakdown (option on_breakdown)      */
   int64_t action_hist[MPCG_NUM_OPS][MPCG_MAX_PREC]; /* iterations per (op, format)       */
 } mpcg_result;
 
 /* One record per iteration k (80 bytes). rho is rho_{k+1} after the iteration (the true
  * relative residual when r was replaced). flags: bit0 converged here, bit1 breakdown here,
- * bit2 r replaced by b - A x, bit3 an operation explored (training). ns_a / ns_b / ns_c:
+ * bit2 r replaced by b - A x, bit3 an operation explored (training), bit4 restarted in fp64
+ * after the breakdown. ns_a / ns_b / ns_c:
  * device time (globaltimer, ns) from the previous team barrier to the barriers that close
  * phase A (product and nu), phase B (residual update, norms) and phase C (x and p update)
  * of the iteration, including the barrier itself. */

@@ -55,7 +55,7 @@ class Opts(C.Structure):
         ("w1", C.c_double), ("w2", C.c_double), ("w3", C.c_double), ("lr", C.c_double),
         ("gamma", C.c_double), ("eps0", C.c_double), ("eps_floor", C.c_double), ("seed", C.c_uint64),
         ("unvisited_fallback", C.c_int), ("true_res_every", C.c_int), ("true_res_at_conv", C.c_int),
-        ("mlp_hidden", C.c_int),
+        ("on_breakdown", C.c_int), ("mlp_hidden", C.c_int),
     ]
 
 
@@ -159,13 +159,14 @@ class Options:
     unvisited_fallback: int = FP64
     true_res_every: int = 0
     true_res_at_conv: int = 0
+    on_breakdown: int = 0
     mlp_hidden: int = 64
 
     def c(self) -> Opts:
         o = Opts()
         for name in ("b_bins", "r_bins", "t_bin", "min_k", "eps_min", "w1", "w2", "w3", "lr", "gamma",
                      "eps0", "eps_floor", "seed", "unvisited_fallback", "true_res_every",
-                     "true_res_at_conv", "mlp_hidden"):
+                     "true_res_at_conv", "on_breakdown", "mlp_hidden"):
             setattr(o, name, getattr(self, name))
         o.nprec = len(self.precs)
         for a, f in enumerate(self.precs):

@@ -143,6 +143,8 @@ typedef struct {
                              -1 keeps the plain first-index argmax                    */
   int true_res_every;     /* >0: replace r by b - A x every this many iterations      */
   int true_res_at_conv;   /* 1: confirm a claimed convergence with b - A x            */
+  int on_breakdown;       /* 1: an inference solve that breaks down restarts once from
+                             r = b - A x, p = r (fp64) and finishes in fp64            */
   int mlp_hidden;         /* MLP hidden width (64)                                     */
 } orc_opts;
 
@@ -570,6 +572,7 @@ int orc_run(const orc_opts* o, int n, const int32_t* rp, const int32_t* ci, cons
     max_iter = 0;
   }
   fs.rho_hist[0] = rho;
+  int locked = 0, restarts = 0; /* fp64 restart after a breakdown (option on_breakdown) */
   double fstat[5] = {0, 0, 0, 0, 0};
   if (pol->feat_static) memcpy(fstat, pol->feat_static, sizeof(fstat));
 
@@ -581,7 +584,9 @@ int orc_run(const orc_opts* o, int n, const int32_t* rp, const int32_t* ci, cons
     for (int j = 0; j < 5; ++j) f[j] = fstat[j];
     orc_dynamic_features(o, k, &fs, f);
     if (feat_out) memcpy(feat_out + (int64_t)k * ORC_NFEAT, f, sizeof(f));
-    if (pol->kind == ORC_POL_FIXED) {
+    if (locked) {
+      for (int j = 0; j < 4; ++j) fmt[j] = ORC_FP64;
+    } else if (pol->kind == ORC_POL_FIXED) {
       for (int j = 0; j < 4; ++j) fmt[j] = pol->fixed[j];
     } else if (pol->kind == ORC_POL_SCHEDULE) {
       int row = k < pol->sched_len ? k : pol->sched_len - 1;
@@ -610,7 +615,7 @@ int orc_run(const orc_opts* o, int n, const int32_t* rp, const int32_t* ci, cons
         fmt[j] = o->precs[act[j]];
       }
     }
-    if (pol->kind == ORC_POL_FIXED || pol->kind == ORC_POL_SCHEDULE)
+    if (locked || pol->kind == ORC_POL_FIXED || pol->kind == ORC_POL_SCHEDULE)
       for (int j = 0; j < 4; ++j) act[j] = index_of(o, fmt[j]);
     int learn = mode == ORC_MODE_TRAIN && act[0] >= 0 && act[1] >= 0 && act[2] >= 0 && act[3] >= 0;
 
@@ -714,6 +719,32 @@ int orc_run(const orc_opts* o, int n, const int32_t* rp, const int32_t* ci, cons
           for (int j = 0; j < 4; ++j) fs.prev_act[j] = act[j] >= 0 ? act[j] : 0;
           rho = rho_new;
         }
+      }
+    }
+    if (stop && outcome == ORC_BREAKDOWN && mode == ORC_MODE_INFER && o->on_breakdown && !locked) {
+      /* READING (extension): restart from the current x (x_k after a curvature breakdown,
+       * x_{k+1} after a later one) with r = b - A x, p = r, sigma = r^T r, every operation
+       * in fp64 from here on; iteration k counts as done. */
+      double nt = orc_true_residual(n, rp, ci, val, b, x, r);
+      for (int i = 0; i < n; ++i) p[i] = r[i];
+      sigma = nt;
+      rho = sqrt(nt) / bnorm;
+      locked = 1;
+      restarts += 1;
+      rec.flags |= 16;
+      for (int h = 8; h > 0; --h) fs.rho_hist[h] = fs.rho_hist[h - 1];
+      fs.rho_hist[0] = rho;
+      stop = 0;
+      outcome = ORC_MAX_ITER;
+      iters = max_iter;
+      if (!isfinite(rho)) {
+        outcome = ORC_BREAKDOWN;
+        iters = k + 1;
+        stop = 1;
+      } else if (rho < tau && k >= o->min_k) {
+        outcome = ORC_CONVERGED;
+        iters = k + 1;
+        stop = 1;
       }
     }
     rec.reward = t.reward;

@@ -201,6 +201,7 @@ mpcg_status build_optview(mpcg_ctx_t ctx, const mpcg_options& o, OptView& v) {
   v.true_every = o.true_res_every;
   v.true_at_conv = o.true_res_at_conv;
   v.warm_start = o.warm_start;
+  v.on_breakdown = o.on_breakdown;
   return MPCG_OK;
 }
 
@@ -506,6 +507,7 @@ void mpcg_options_default(mpcg_options* o) {
   o->true_res_every = 0;
   o->true_res_at_conv = 0;
   o->warm_start = 0;
+  o->on_breakdown = 0;
   o->mlp_hidden = 64;
 }
 

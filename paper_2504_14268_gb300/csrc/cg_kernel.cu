@@ -23,7 +23,8 @@ namespace mpcg {
 
 namespace {
 
-enum Mode : int { M_CONT = 0, M_DONE = 1, M_X_THEN_DONE = 2, M_TCHK = 3, M_RESTART = 4 };
+enum Mode : int { M_CONT = 0, M_DONE = 1, M_X_THEN_DONE = 2, M_TCHK = 3, M_RESTART = 4, M_RESTART64 = 5,
+                  M_X_THEN_RESTART64 = 6 };
 
 struct TeamCtx {
   int team, rank, size, first;
@@ -304,7 +305,9 @@ __device__ void choose_action(const Launch& L, const DevSys& S, SysState* st, in
     int expl = 0;
     for (int j = 0; j < 4; ++j) {
       int fmt, act = -1;
-      if (P.kind == 0) {
+      if (st->fp64_lock) {
+        fmt = F64;
+      } else if (P.kind == 0) {
         fmt = P.fixed[j];
       } else if (P.kind == 1) {
         const int row = k < P.sched_len ? k : P.sched_len - 1;
@@ -505,6 +508,11 @@ __device__ void adopt_action(SysState* st, const Smem& sm) {
   st->s_cur = sm.a_state;
 }
 
+// A breakdown of an inference solve restarts in fp64 when the option asks for it (once).
+__device__ __forceinline__ bool restart_ok(const Launch& L, const SysState* st) {
+  return !L.train && L.opt.on_breakdown && !st->fp64_lock;
+}
+
 // After the initial phase: ||b||, rho_0, sigma_0 = r_0^T r_0, action of iteration 0.
 __device__ void step_init(const Launch& L, const DevSys& S, SysState* st, double bb, double rr, Smem& sm) {
   if (threadIdx.x == 0) {
@@ -527,6 +535,8 @@ __device__ void step_init(const Launch& L, const DevSys& S, SysState* st, double
     st->explored = 0;
     st->s_cur = 0;
     st->zfmt = F64;
+    st->fp64_lock = 0;
+    st->n_restart = 0;
     st->ns_a = st->ns_b = 0;
     st->t_last = gtime();
     for (int j = 0; j < 4; ++j) {
@@ -575,6 +585,10 @@ __device__ void step_A(const Launch& L, const DevSys& S, SysState* st, double nu
       const double R = !L.train ? 0.0 : reward_of(L.opt, st->rho, st->act, S.tol, false);
       write_record(S, st, 1, st->rho, 0.0, 0.0, L.train ? R : 0.0);
       push_transition(L, S, st, st->s_cur, R, 1);
+    } else if (restart_ok(L, st)) {
+      write_record(S, st, 2 | 16, st->rho, 0.0, 0.0, 0.0);
+      st->mode = M_RESTART64;
+      return;
     } else {
       st->outcome = MPCG_BREAKDOWN;
       const double R = !L.train ? 0.0 : reward_of(L.opt, st->rho, st->act, S.tol, true);
@@ -599,7 +613,10 @@ __device__ void continue_step(const Launch& L, const DevSys& S, SysState* st, do
     const double beta = replaced ? 0.0 : sigma_new / st->sigma;
     const int k = st->k;
     const int flags = replaced ? 4 : 0;
-    if (!isfinite(sigma_new) || !isfinite(beta)) {
+    if ((!isfinite(sigma_new) || !isfinite(beta)) && restart_ok(L, st)) {
+      write_record(S, st, flags | 2 | 16, rho_new, sigma_new, beta, 0.0);
+      st->mode = replaced ? M_RESTART64 : M_X_THEN_RESTART64;
+    } else if (!isfinite(sigma_new) || !isfinite(beta)) {
       st->outcome = MPCG_BREAKDOWN;
       st->iters = k + 1;
       const double R = !L.train ? 0.0 : reward_of(L.opt, rho_new, st->act, S.tol, true);
@@ -653,6 +670,9 @@ __device__ void step_B(const Launch& L, const DevSys& S, SysState* st, double rr
     if (check && isfinite(rho_rec)) {
       st->rho_true = rho_rec;  // recursive value, kept for the gap feature
       st->mode = M_TCHK;
+    } else if (!isfinite(rho_rec) && restart_ok(L, st)) {
+      write_record(S, st, 2 | 16, rho_rec, 0.0, 0.0, 0.0);
+      st->mode = M_X_THEN_RESTART64;
     } else if (!isfinite(rho_rec)) {
       st->outcome = MPCG_BREAKDOWN;
       st->iters = k + 1;
@@ -686,7 +706,10 @@ __device__ void step_T(const Launch& L, const DevSys& S, SysState* st, double rr
     st->gap_log = (rho_t > 0.0 && rho_rec > 0.0) ? log10(rho_t / rho_rec) : 0.0;
     const int k = st->k;
     sm.flag = 0;
-    if (!isfinite(rho_t)) {
+    if (!isfinite(rho_t) && restart_ok(L, st)) {
+      write_record(S, st, 4 | 2 | 16, rho_t, 0.0, 0.0, 0.0);
+      st->mode = M_RESTART64;
+    } else if (!isfinite(rho_t)) {
       st->outcome = MPCG_BREAKDOWN;
       st->iters = k + 1;
       const double R = !L.train ? 0.0 : reward_of(L.opt, rho_t, st->act, S.tol, true);
@@ -714,6 +737,51 @@ __device__ void step_T(const Launch& L, const DevSys& S, SysState* st, double rr
   if (sm.flag) continue_step(L, S, st, sqrt(rr) / st->bnorm, sig_sum, 1, sm);
 }
 
+// After the fp64 restart's residual recomputation (r = b - A x, p = r): iteration k counts
+// as done; sigma = ||r||^2, every later operation in fp64; stop test as after any iteration.
+__device__ void step_restart(const Launch& L, const DevSys& S, SysState* st, double rr, Smem& sm) {
+  if (threadIdx.x == 0) {
+    sm.need_action = 0;
+    const double rho = sqrt(rr) / st->bnorm;
+    const int k = st->k;
+    st->fp64_lock = 1;
+    st->n_restart += 1;
+    st->n_true += 1;
+    st->sigma = rr;
+    st->beta = 0.0;
+    st->rho = rho;
+    for (int h = 8; h > 0; --h) st->rho_hist[h] = st->rho_hist[h - 1];
+    st->rho_hist[0] = rho;
+    st->zfmt = F64;
+    st->k = k + 1;
+    if (!isfinite(rho)) {
+      st->outcome = MPCG_BREAKDOWN;
+      st->iters = k + 1;
+      st->rho_true = rho;
+      st->true_known = 1;
+      st->mode = M_DONE;
+    } else if (rho < S.tol && k >= L.opt.min_k) {
+      st->outcome = MPCG_CONVERGED;
+      st->iters = k + 1;
+      st->rho_true = rho;
+      st->true_known = 1;
+      st->mode = M_DONE;
+    } else if (k + 1 >= S.max_iter) {
+      st->outcome = MPCG_MAX_ITER;
+      st->iters = S.max_iter;
+      st->mode = M_DONE;
+    } else {
+      st->mode = M_CONT;
+      sm.need_action = 1;
+    }
+  }
+  __syncthreads();
+  if (sm.need_action) {
+    choose_action(L, S, st, st->k, st->rho, sm);
+    if (threadIdx.x == 0) adopt_action(st, sm);
+  }
+}
+
 __device__ void step_final(const Launch& L, const DevSys& S, SysState* st, int sid, double rr) {
   if (threadIdx.x != 0) return;
   if (!st->true_known) st->rho_true = st->bnorm > 0.0 ? sqrt(rr) / st->bnorm : 0.0;
@@ -723,7 +791,7 @@ __device__ void step_final(const Launch& L, const DevSys& S, SysState* st, int s
   res.rel_res_rec = st->rho;
   res.rel_res_true = st->rho_true;
   res.n_true_checks = st->n_true;
-  res.pad = st->ntrans;
+  res.n_restarts = st->n_restart;
   for (int j = 0; j < 4; ++j)
     for (int f = 0; f < 8; ++f) res.action_hist[j][f] = st->counts[j][f];
   L.res[sid] = res;
@@ -758,6 +826,16 @@ __device__ __forceinline__ void stamp_c(const DevSys& S, SysState* st) {
 }
 
 constexpr int kUnroll = 4;  // rows per thread in flight in the vector phases
+
+// fp64 restart after a breakdown: r = b - A x and p = r in fp64, then step_restart.
+__device__ bool restart64(const Launch& L, const TeamCtx& T, const DevSys& S, SysState* st, Rows R, Smem& sm) {
+  double rr = 0.0;
+  DotAcc unused{0.0, 0.f, 0.f};
+  true_res_rows(S, R, -1, -1, true, rr, unused);
+  rr = cta_sum(rr, sm.red);
+  write_partial(L, 0, rr);
+  return team_step(L, T, st, sm, [&] { step_restart(L, S, st, team_sum(L, T, 0, sm.red), sm); });
+}
 
 __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& sm, const StreamCtx* sc) {
   const DevSys& S = L.sys[sid];
@@ -813,6 +891,11 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
         spmv_rows(S, R, p1, p3, nu, sc);
         write_partial(L, 0, cta_dot(nu, sm.red));
         if (!team_step(L, T, st, sm, [&] { step_A(L, S, st, team_sum(L, T, 0, sm.red)); })) return false;
+        if (sm.bc.mode == M_RESTART64) {
+          if (!restart64(L, T, S, st, R, sm)) return false;
+          if (sm.bc.mode != M_CONT) break;
+          continue;
+        }
         if (sm.bc.mode != M_CONT) break;
       }
       // ---- phase B: r -= alpha q (fp64), ||r||^2 (fp64), sigma partials ----
@@ -893,6 +976,11 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
         if (!team_step(L, T, st, sm, [] {})) return false;
       }
       if (mode == M_X_THEN_DONE) break;
+      if (mode == M_X_THEN_RESTART64) {
+        if (!restart64(L, T, S, st, R, sm)) return false;
+        if (sm.bc.mode != M_CONT) break;
+        continue;
+      }
       // ---- phase T: r = b - A x (fp64), ||r||^2, sigma partials ----
       {
         const int p2 = sm.bc.fmt[1], p4 = sm.bc.fmt[3];
@@ -909,6 +997,11 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
               step_T(L, S, st, trr, tsg, sm);
             }))
           return false;
+      }
+      if (sm.bc.mode == M_RESTART64) {
+        if (!restart64(L, T, S, st, R, sm)) return false;
+        if (sm.bc.mode != M_CONT) break;
+        continue;
       }
       if (sm.bc.mode == M_RESTART) {
         // p = z (beta = 0) after the replacement; x is already up to date.
@@ -942,7 +1035,7 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
   return true;
 }
 
-__global__ void __launch_bounds__(kThreads) cg_persistent(const Launch L) {
+__global__ void __launch_bounds__(kThreads, 4) cg_persistent(const Launch L) {
   __shared__ Smem sm;
   extern __shared__ __align__(128) unsigned char dyn[];
   StreamCtx scx{dyn, sm.mbar, &sm.mbar_phase, L.err, L.stream_stage};

@@ -89,6 +89,7 @@ struct SysState {
   int have_prev, n_true, ntrans, true_known;
   int explored, s_cur;      // exploration flag and state index of the current iteration
   int zfmt, pad;            // p2 of the iteration whose direction update is pending
+  int fp64_lock, n_restart;   // after a breakdown restart every operation runs in fp64
   unsigned long long t_last;  // globaltimer at the previous team barrier
   unsigned ns_a, ns_b;        // phase times of the current iteration
   long long counts[4][8];
@@ -119,6 +120,7 @@ struct OptView {
   int fallback_fmt;         // unvisited-row action (format code), -1 = argmax
   int fallback_idx;         // its index in precs (-1 if absent)
   int true_every, true_at_conv, warm_start, t_bin;
+  int on_breakdown, pad;
 };
 
 // Arguments of one launch of the persistent kernel.

@@ -46,12 +46,9 @@ __device__ __forceinline__ double pow2(int e) {
   return __longlong_as_double((long long)((unsigned long long)(e + 1023) << 52));
 }
 
-// Row finished with a compensated fp32 pair (sp, ep): q_i = fl_p1(sp + ep) (one rounding of
-// the pair's exact value), stored in p1's storage; then the row's nu term fl_p3(p_i) fl_p3(q_i)
-// (q_i includes the row scale 2^e_i of the row-scaled formats).
-__device__ __forceinline__ void finish_row_low(const DevSys& S, int row, float sp, float ep, int p1, int nu_fmt,
-                                               DotAcc& nu) {
-  const float qf = round_pair(sp, ep, p1);
+// Row finished with q_i = qf already rounded onto p1: stored in p1's storage; then the row's
+// nu term fl_p3(p_i) fl_p3(q_i) (q_i includes the row scale 2^e_i of the row-scaled formats).
+__device__ __forceinline__ void finish_row_low(const DevSys& S, int row, float qf, int p1, int nu_fmt, DotAcc& nu) {
   switch (store_of(p1)) {
     case ST_HALF: ((__half*)S.q)[row] = __float2half_rn(qf); break;
     case ST_BF16: ((__nv_bfloat16*)S.q)[row] = __float2bfloat16_rn(qf); break;
@@ -81,29 +78,59 @@ __device__ __forceinline__ void finish_row_64(const DevSys& S, int row, double t
   else dot_low(nu, round_d2f(pi, nu_fmt), round_d2f(tot, nu_fmt), nu_fmt);
 }
 
-// Products of one row slice accumulated by one lane. fp64: fp64 accumulation. Lower
-// formats: compensated fp32 pair (sum, error): the products of the rounded inputs are exact
-// for the 16-bit formats and tf32 and carry their FMA error for fp32, so the row sum is
-// accurate to about 2^-48 before its single rounding onto p1.
+// Half the distance from fl_f(v) = r to its neighbours in format f, below and above
+// (conservative at binade edges), as fp32; f is fp16, bf16 or tf32.
+__device__ __forceinline__ void half_gaps(float r, int f, float& below, float& above) {
+  const int t = base_fmt(f) == BF16 ? 8 : 11;
+  const int emin = base_fmt(f) == F16 ? -14 : -126;
+  int e = (int)((__float_as_uint(r) >> 23) & 0xff) - 127;
+  if (r == 0.f || e < emin) e = emin;
+  const float ulp = __uint_as_float((unsigned)(e - t + 1 + 127) << 23);
+  const float low = (fabsf(r) == __uint_as_float((unsigned)(e + 127) << 23) && e > emin) ? 0.5f * ulp : ulp;
+  // moving toward zero from a power of two the spacing halves
+  above = 0.5f * (r >= 0.f ? ulp : low);
+  below = 0.5f * (r >= 0.f ? low : ulp);
+}
+
+// Products of one row slice accumulated by one lane.
+// fp64 values: fp64 accumulation. fp32: fp32 accumulation (the output format is fp32, so
+// the accumulation error stays at its last place). fp16, bf16, tf32 (and the row-scaled
+// formats): the products are exact in fp32 and the fp32 sum s carries the bound
+// m = sum |a_ij x_j|; the recursive-summation bound |s - exact| <= gamma_n m (Higham,
+// "Accuracy and Stability of Numerical Algorithms", Section 4.2) tells whether s rounds to
+// the same value of the output format as the exact sum. When the error interval reaches
+// a rounding midpoint (a small fraction of rows), lane 0 sums the row again in fp64 and
+// rounds that sum, so every row of q is the correctly rounded value of its sum.
 template <typename VT>
 struct RowAcc {
-  float s = 0.f, c = 0.f;
+  float s = 0.f, m = 0.f;
   __device__ __forceinline__ void add(VT a, VT x) {
     const float af = to_acc(a), xf = to_acc(x);
-    acc2(af, xf, sizeof(VT) == 2, s, c);
+    s = fmaf(af, xf, s);
+    if constexpr (sizeof(VT) == 2) m = fmaf(fabsf(af), fabsf(xf), m);
+    else m = fmaf(fabsf(af), fabsf(xf), m);
   }
   template <int K>
   __device__ __forceinline__ void reduce(unsigned mask) {
 #pragma unroll
     for (int o = K / 2; o > 0; o >>= 1) {
-      const float s2 = __shfl_xor_sync(mask, s, o), c2 = __shfl_xor_sync(mask, c, o);
-      float t;
-      two_sum(s, s2, s, t);
-      c = __fadd_rn(__fadd_rn(c, c2), t);
+      s += __shfl_xor_sync(mask, s, o);
+      m += __shfl_xor_sync(mask, m, o);
     }
   }
-  __device__ __forceinline__ void finish(const DevSys& S, int row, int p1, int nu_fmt, DotAcc& nu) const {
-    finish_row_low(S, row, s, isfinite(s) ? c : 0.f, p1, nu_fmt, nu);
+  // Row sum rounded onto p1 (fp32 result). `exact` recomputes the row in fp64 when needed.
+  template <class Exact>
+  __device__ __forceinline__ float rounded(int p1, int len, Exact&& exact) const {
+    if (base_fmt(p1) == F32 || !isfinite(s)) return s;
+    const float r = round_f2f(s, p1);
+    if (!isfinite(r)) return r;
+    float below, above;
+    half_gaps(r, p1, below, above);
+    // gamma_n m with n = len additions, inflated for the rounding of m itself
+    const float err = m * (float)(len + 2) * 6.0e-8f;
+    const float d = s - r;
+    if (d + err < above && -d + err < below) return r;
+    return round_d2f(exact(), p1);
   }
 };
 
@@ -116,10 +143,27 @@ struct RowAcc<double> {
 #pragma unroll
     for (int o = K / 2; o > 0; o >>= 1) s += __shfl_xor_sync(mask, s, o);
   }
-  __device__ __forceinline__ void finish(const DevSys& S, int row, int, int nu_fmt, DotAcc& nu) const {
-    finish_row_64(S, row, s, nu_fmt, nu);
-  }
 };
+
+// fp64 sum of a row from value and column accessors (the exact fallback).
+template <typename VT, class V, class Cf>
+__device__ __forceinline__ double row_sum64(int rs, int re, V&& val, Cf&& col, const VT* xin) {
+  double acc = 0.0;
+  for (int e = rs; e < re; ++e) acc = fma(f2d(to_acc(val(e))), f2d(to_acc(xin[col(e)])), acc);
+  return acc;
+}
+
+// Finishes a row of the product from its accumulator (lane 0 of the row's lanes).
+template <typename VT, class V, class Cf>
+__device__ __forceinline__ void finish_row(const DevSys& S, int row, int rs, int re, const RowAcc<VT>& acc, int p1,
+                                           int nu_fmt, DotAcc& nu, V&& val, Cf&& col, const VT* xin) {
+  if constexpr (sizeof(VT) == 8) {
+    finish_row_64(S, row, acc.s, nu_fmt, nu);
+  } else {
+    const float qf = acc.rounded(p1, re - rs, [&] { return row_sum64<VT>(rs, re, val, col, xin); });
+    finish_row_low(S, row, qf, p1, nu_fmt, nu);
+  }
+}
 
 // ---- bulk copies into shared memory (cp.async.bulk + mbarrier) ------------------------
 
@@ -194,7 +238,9 @@ __device__ void spmv_vec(const DevSys& S, const VT* __restrict__ vals, const VT*
     RowAcc<VT> acc;
     for (int e = e0 + lane; e < e1; e += K) acc.add(__ldg(vals + e), xin[__ldg(ci + e)]);
     acc.template reduce<K>(mask);
-    if (lane == 0) acc.finish(S, row, p1, nu_fmt, nu);
+    if (lane == 0)
+      finish_row<VT>(S, row, e0, e1, acc, p1, nu_fmt, nu, [&](int e) { return __ldg(vals + e); },
+                     [&](int e) { return __ldg(ci + e); }, xin);
   }
 }
 
@@ -239,8 +285,9 @@ __device__ void spmv_stream(const DevSys& S, const VT* __restrict__ vals, const 
     const int rb = min(ra + TR, R.r1);
     const int e0 = __ldg(rp + ra);
     const unsigned char* base = sc.buf + (size_t)stage * sc.stage_bytes;
-    const int ev0 = (int)(((long long)e0 * (long long)sizeof(VT)) & ~15ll) / (int)sizeof(VT);
-    const int ec0 = e0 & ~3;
+    // element index of the first copied value (64-bit: e0 * 8 exceeds 2^31 for large matrices)
+    const long long ev0 = (((long long)e0 * (long long)sizeof(VT)) & ~15ll) / (long long)sizeof(VT);
+    const long long ec0 = (long long)(e0 & ~3);
     const VT* sv = (const VT*)base - ev0;
     const int* scol = (const int*)(base + vreg) - ec0;
     const int row = ra + grp;
@@ -249,7 +296,9 @@ __device__ void spmv_stream(const DevSys& S, const VT* __restrict__ vals, const 
       RowAcc<VT> acc;
       for (int e = rs + lane; e < re; e += K) acc.add(sv[e], xin[scol[e]]);
       acc.template reduce<K>(mask);
-      if (lane == 0) acc.finish(S, row, p1, nu_fmt, nu);
+      if (lane == 0)
+        finish_row<VT>(S, row, rs, re, acc, p1, nu_fmt, nu, [&](int e) { return sv[e]; }, [&](int e) { return scol[e]; },
+                       xin);
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -42,13 +42,13 @@ class COptions(C.Structure):
         ("w1", C.c_double), ("w2", C.c_double), ("w3", C.c_double), ("lr", C.c_double), ("gamma", C.c_double),
         ("eps0", C.c_double), ("eps_floor", C.c_double), ("seed", C.c_uint64),
         ("unvisited_fallback", C.c_int32), ("true_res_every", C.c_int32), ("true_res_at_conv", C.c_int32),
-        ("warm_start", C.c_int32), ("mlp_hidden", C.c_int32),
+        ("warm_start", C.c_int32), ("on_breakdown", C.c_int32), ("mlp_hidden", C.c_int32),
     ]
 
 
 class CResult(C.Structure):
     _fields_ = [("outcome", C.c_int32), ("iters", C.c_int32), ("rel_res_rec", C.c_double),
-                ("rel_res_true", C.c_double), ("n_true_checks", C.c_int32), ("pad", C.c_int32),
+                ("rel_res_true", C.c_double), ("n_true_checks", C.c_int32), ("n_restarts", C.c_int32),
                 ("action_hist", (C.c_int64 * 8) * 4)]
 
 
@@ -177,6 +177,7 @@ class Options:
     true_res_every: int = 0
     true_res_at_conv: int = 0
     warm_start: int = 0
+    on_breakdown: int = 0
     mlp_hidden: int = 64
 
     def c(self) -> COptions:
@@ -200,7 +201,7 @@ class Options:
 
 def result_dict(r: CResult) -> dict:
     return dict(outcome=r.outcome, iters=r.iters, rel_res_rec=r.rel_res_rec, rel_res_true=r.rel_res_true,
-                n_true_checks=r.n_true_checks, action_hist=np.array([list(row) for row in r.action_hist]))
+                n_true_checks=r.n_true_checks, n_restarts=r.n_restarts, action_hist=np.array([list(row) for row in r.action_hist]))
 
 
 class Context:
