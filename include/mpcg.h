@@ -203,7 +203,14 @@ mpcg_status mpcg_policy_schedule(mpcg_ctx_t ctx, const int32_t* fmts, int32_t le
 mpcg_status mpcg_policy_qtable(mpcg_ctx_t ctx, const double* Q, const int32_t* visits, mpcg_policy_t* out);
 /* MLP Q-function 16 -> H -> H -> 4*nprec (ReLU), fp32 parameters in the layout W1[H][16],
  * b1[H], W2[H][H], b2[H], W3[4*nprec][H], b3[4*nprec] (host array of mpcg_mlp_nparams
- * floats), H = options.mlp_hidden. */
+ * floats), H = options.mlp_hidden. Greedy: per operation, the first-index argmax over its
+ * nprec outputs. Features of iteration k (an extension; the paper's state is the pair of
+ * bins): f0 = log10(n)/8, f1 = mean nnz per row / 64, f2 = log10(max a_ii / min a_ii)/16,
+ * f3 = log10(max_i sum_j |a_ij| / a_ii)/16, f4 = fraction of |a_ij| outside the fp16 normal
+ * range, f5 = k / t_bin, f6 = -log10(max(rho_k, eps_min))/16, f7 = log10(rho_k / rho_{k-1}),
+ * f8 = log10(rho_k / rho_{k-8}) / 8, f9 = log10|alpha_{k-1}| / 8, f10 = log10|beta_{k-1}| / 8,
+ * f11 = log10(true / recursive residual) at the last recomputation, f12..f15 = previous
+ * action indices / (nprec - 1); unavailable history terms are 0. */
 mpcg_status mpcg_policy_mlp(mpcg_ctx_t ctx, const float* params, mpcg_policy_t* out);
 int64_t mpcg_mlp_nparams(int32_t hidden, int32_t nprec);
 /* Copies a QTABLE policy's tables back to host arrays (either may be NULL). */
@@ -263,6 +270,42 @@ mpcg_status mpcg_graph_destroy(mpcg_graph_t g);
 mpcg_status mpcg_train_qtable(mpcg_ctx_t ctx, int32_t nsys, const mpcg_matrix_t* A,
                               const double* const* b, double tol, int32_t t_max, int32_t episodes,
                               mpcg_policy_t inout, int32_t* iters_out, void* stream);
+
+/* ---- learned policy (MLP Q-function; an extension, not in the paper) ----------------- */
+
+/* One transition of the MLP's training data (152 bytes). */
+typedef struct {
+  float f[16];      /* features of state s_k (see mpcg_policy_mlp for their definition)   */
+  float f_next[16]; /* features of state s_{k+1} (unused when done = 1)                   */
+  int32_t act[4];   /* action of each operation as an index into options.precs            */
+  float reward;     /* reward of Section 4.1                                              */
+  int32_t done;     /* 1 when the episode ended with this transition                      */
+} mpcg_transition;
+
+/* Runs one epsilon-greedy episode (at most max_iter iterations, x_0 = 0) per system with
+ * the behaviour policy (QTABLE: its tables are copied and updated privately as in
+ * Algorithm 1, the policy itself is unchanged; MLP: greedy on its Q-values) and exploration
+ * rate eps, episode counter `episode` for the draws. The transitions of all systems are
+ * written to the host array out (system order, then iteration order), at most cap of them;
+ * *count receives the number written. b[i]: device pointers. */
+mpcg_status mpcg_collect(mpcg_ctx_t ctx, int32_t nsys, const mpcg_matrix_t* A, const double* const* b, double tol,
+                         int32_t max_iter, mpcg_policy_t behavior, double eps, uint64_t episode,
+                         mpcg_transition* out, int64_t cap, int64_t* count, void* stream);
+
+/* Loss (1/(4B)) sum_b sum_j 1/2 (Q(f_b)[j, a_bj] - y_bj)^2 of the MLP with parameters
+ * `params` (host, mpcg_mlp_nparams floats) on B samples (host arrays feats[B][16],
+ * acts[B][4], y[B][4]) and its gradient (host array, same layout as params). */
+mpcg_status mpcg_mlp_loss_grad(mpcg_ctx_t ctx, const float* params, int64_t B, const float* feats,
+                               const int32_t* acts, const float* y, float* grad, double* loss, void* stream);
+
+/* Fitted-Q training of an MLP policy in place: `steps` Adam steps (lr, betas 0.9 / 0.999,
+ * eps 1e-8) on minibatches of `batch` transitions drawn from data[count] (host array) with
+ * Philox4x64-10 (key seed), targets r + gamma (1 - done) max_p Q_target(f_next)[j, p] from a
+ * target network copied from the trained one every target_sync steps. loss_out (optional,
+ * host [steps]) receives each step's loss. */
+mpcg_status mpcg_mlp_train(mpcg_ctx_t ctx, mpcg_policy_t mlp, const mpcg_transition* data, int64_t count,
+                           int32_t steps, int32_t batch, float lr, int32_t target_sync, uint64_t seed,
+                           float* loss_out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -1,6 +1,6 @@
 """Builds the CUDA library libmpcg.so in-tree for sm_103a (nvcc, no cmake).
 
-The three translation units compile in parallel; the shared library lands in
+The translation units compile in parallel; the shared library lands in
 paper_2504_14268_gb300/_lib/. Rebuilds only when a source or header is newer than it.
 """
 from __future__ import annotations
@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 OBJ_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libmpcg.so")
-SOURCES = ["cg_kernel.cu", "setup_kernels.cu", "api.cu"]
+SOURCES = ["cg_kernel.cu", "setup_kernels.cu", "mlp_kernels.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

@@ -64,7 +64,7 @@ struct Plan {
   int grid = 0, nsys = 0, nteams = 0;
   DevBuf sys, st, res, cta_team, cta_rank, team_size, team_first, team_sys_off, team_sys, bars, partials, err;
   DevBuf work, bstage, xstage, hstage;
-  DevBuf qpriv, trans;
+  DevBuf qpriv, trans, feats;
   std::vector<DevSys> hsys;
   std::vector<mpcg_result> hres;
   Launch L;
@@ -316,7 +316,7 @@ mpcg_status fill_policy(mpcg_ctx_t ctx, mpcg_policy_t P, PolicyView& pv) {
 
 // Builds the device tables of a launch for `in` systems into `pl` and fills pl.L.
 mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, mpcg_policy_t policy, int train,
-                       int trans_cap, int force_team, cudaStream_t s) {
+                       int trans_cap, int force_team, cudaStream_t s, int feat_cap = 0) {
   const int nsys = (int)in.size();
   bool stream_shape = false;
   for (int i = 0; i < nsys; ++i) stream_shape = stream_shape || uses_stream(in[i].A->dm);
@@ -360,6 +360,7 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
     CK(ctx, pl.qpriv.ensure(sizeof(double) * qsize * nsys));
     CK(ctx, pl.trans.ensure(sizeof(Transition) * (size_t)trans_cap * nsys));
   }
+  if (feat_cap > 0) CK(ctx, pl.feats.ensure(sizeof(float) * kNFeat * (size_t)feat_cap * nsys));
   pl.hsys.resize(nsys);
   char* wp = pl.work.as<char>();
   auto take = [&](size_t bytes) {
@@ -389,6 +390,10 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
       d.trans_cap = trans_cap;
     }
     for (int j = 0; j < 5; ++j) d.feat_static[j] = in[i].A->feat[j];
+    if (feat_cap > 0) {
+      d.feat_log = pl.feats.as<float>() + (size_t)kNFeat * feat_cap * i;
+      d.feat_cap = feat_cap;
+    }
   }
   CK(ctx, pl.sys.ensure(sizeof(DevSys) * std::max(nsys, 1)));
   CK(ctx, pl.st.ensure(sizeof(SysState) * std::max(nsys, 1)));
@@ -535,6 +540,7 @@ mpcg_status mpcg_create(mpcg_ctx_t* out, int device, const mpcg_options* opt) {
   if (cg_occupancy(&c->occ_s, 2 * (size_t)kStageBytes) != cudaSuccess || c->occ_s < 1) return MPCG_ERR_CUDA;
   if (spmv_occupancy(&c->socc, 0) != cudaSuccess || spmv_occupancy(&c->socc_s, 2 * (size_t)kStageBytes) != cudaSuccess)
     return MPCG_ERR_CUDA;
+  if (mlp_set_smem_limit(mlp_grad_smem(kMaxHidden, MPCG_MAX_PREC)) != cudaSuccess) return MPCG_ERR_CUDA;
   c->socc = std::min(c->socc, c->occ);
   c->socc_s = std::min(c->socc_s, c->occ_s);
   *out = c.release();
@@ -1214,6 +1220,171 @@ mpcg_status mpcg_train_qtable(mpcg_ctx_t ctx, int32_t nsys, const mpcg_matrix_t*
         for (int i = 0; i < nsys; ++i) iters_out[(size_t)(e - 1) * nsys + i] = rr[i].iters;
     }
   }
+  return MPCG_OK;
+}
+
+// ---- learned policy ----------------------------------------------------------------------
+
+mpcg_status mpcg_collect(mpcg_ctx_t ctx, int32_t nsys, const mpcg_matrix_t* A, const double* const* b, double tol,
+                         int32_t max_iter, mpcg_policy_t behavior, double eps, uint64_t episode, mpcg_transition* out,
+                         int64_t cap, int64_t* count, void* stream) {
+  if (!ctx || !behavior || nsys < 1 || !A || !b || max_iter < 1 || !out || !count || cap < 0)
+    return fail(ctx, MPCG_ERR_INVALID_ARG, "bad collection arguments");
+  if (behavior->kind != 2 && behavior->kind != 3)
+    return fail(ctx, MPCG_ERR_BAD_POLICY, "collection needs a QTABLE or MLP behaviour policy");
+  ctx->err.clear();
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t xbytes = 0;
+  for (int i = 0; i < nsys; ++i) xbytes += 8 * (size_t)A[i]->dm.n + 256;
+  DevBuf xs;
+  CK(ctx, xs.ensure(xbytes));
+  std::vector<double*> xp(nsys);
+  std::vector<double> tols(nsys, tol);
+  std::vector<int32_t> caps(nsys, max_iter);
+  char* w = xs.as<char>();
+  for (int i = 0; i < nsys; ++i) {
+    xp[i] = (double*)w;
+    w += (8 * (size_t)A[i]->dm.n + 255) / 256 * 256;
+  }
+  std::vector<SysIn> in;
+  mpcg_status st = collect_batch(ctx, nsys, A, b, xp.data(), tols.data(), caps.data(), in);
+  if (st != MPCG_OK) return st;
+  Plan& pl = ctx->plan;
+  st = build_plan(ctx, pl, in, behavior, 1, max_iter, 0, s, max_iter + 1);
+  if (st != MPCG_OK) return st;
+  const mpcg_options& o = ctx->opt;
+  const long long qsize = 4LL * o.b_bins * o.r_bins * o.nprec;
+  if (behavior->kind == 2) CK(ctx, launch_qcopy(behavior->Q.as<double>(), pl.qpriv.as<double>(), nsys, qsize, s));
+  pl.L.episode = (unsigned long long)episode;
+  pl.L.eps = eps;
+  st = enqueue_plan(ctx, pl, s);
+  if (st != MPCG_OK) return st;
+  std::vector<mpcg_result> rr(nsys);
+  st = finish_plan(ctx, pl, rr.data(), s);
+  if (st != MPCG_OK) return st;
+  std::vector<SysState> hst(nsys);
+  std::vector<Transition> htr((size_t)max_iter * nsys);
+  std::vector<float> hf((size_t)kNFeat * (max_iter + 1) * nsys);
+  CK(ctx, cudaMemcpy(hst.data(), pl.st.p, sizeof(SysState) * nsys, cudaMemcpyDeviceToHost));
+  CK(ctx, cudaMemcpy(htr.data(), pl.trans.p, sizeof(Transition) * htr.size(), cudaMemcpyDeviceToHost));
+  CK(ctx, cudaMemcpy(hf.data(), pl.feats.p, sizeof(float) * hf.size(), cudaMemcpyDeviceToHost));
+  int64_t c = 0;
+  for (int l = 0; l < nsys && c < cap; ++l) {
+    const int nt = std::min(hst[l].ntrans, max_iter);
+    const float* fl = hf.data() + (size_t)kNFeat * (max_iter + 1) * l;
+    for (int t = 0; t < nt && c < cap; ++t, ++c) {
+      const Transition& tr = htr[(size_t)max_iter * l + t];
+      mpcg_transition& d = out[c];
+      memcpy(d.f, fl + (size_t)kNFeat * t, sizeof(d.f));
+      memcpy(d.f_next, fl + (size_t)kNFeat * (t + 1), sizeof(d.f_next));
+      for (int j = 0; j < 4; ++j) d.act[j] = tr.act[j];
+      d.reward = (float)tr.reward;
+      d.done = tr.terminal;
+    }
+  }
+  *count = c;
+  return MPCG_OK;
+}
+
+mpcg_status mpcg_mlp_loss_grad(mpcg_ctx_t ctx, const float* params, int64_t B, const float* feats, const int32_t* acts,
+                               const float* y, float* grad, double* loss, void* stream) {
+  if (!ctx || !params || B < 1 || !feats || !acts || !y || !grad) return fail(ctx, MPCG_ERR_INVALID_ARG, "NULL argument");
+  const mpcg_options& o = ctx->opt;
+  for (int64_t i = 0; i < 4 * B; ++i)
+    if (acts[i] < 0 || acts[i] >= o.nprec) return fail(ctx, MPCG_ERR_INVALID_ARG, "action %d out of range", acts[i]);
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long np = mlp_nparams_dev(o.mlp_hidden, o.nprec);
+  const int chunk = 32;
+  const int nparts = (int)((B + chunk - 1) / chunk);
+  DevBuf dw, df, da, dy, dpart, dl, dg, dloss;
+  CK(ctx, dw.ensure(sizeof(float) * np));
+  CK(ctx, df.ensure(sizeof(float) * kNFeat * B));
+  CK(ctx, da.ensure(sizeof(int) * 4 * B));
+  CK(ctx, dy.ensure(sizeof(float) * 4 * B));
+  CK(ctx, dpart.ensure(sizeof(float) * np * nparts));
+  CK(ctx, dl.ensure(sizeof(double) * nparts));
+  CK(ctx, dg.ensure(sizeof(float) * np));
+  CK(ctx, dloss.ensure(sizeof(double)));
+  CK(ctx, cudaMemcpyAsync(dw.p, params, sizeof(float) * np, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(df.p, feats, sizeof(float) * kNFeat * B, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(da.p, acts, sizeof(int) * 4 * B, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(dy.p, y, sizeof(float) * 4 * B, cudaMemcpyHostToDevice, s));
+  CK(ctx, launch_mlp_grad(dw.as<float>(), nullptr, o.mlp_hidden, o.nprec, df.as<float>(), nullptr, da.as<int>(), nullptr,
+                          nullptr, dy.as<float>(), nullptr, (int)B, chunk, (float)o.gamma, dpart.as<float>(),
+                          dl.as<double>(), s));
+  CK(ctx, launch_mlp_reduce_adam(dpart.as<float>(), nparts, np, dg.as<float>(), nullptr, nullptr, nullptr, 0, 0.f,
+                                 dl.as<double>(), dloss.as<double>(), s));
+  CK(ctx, cudaMemcpyAsync(grad, dg.p, sizeof(float) * np, cudaMemcpyDeviceToHost, s));
+  double hl = 0.0;
+  CK(ctx, cudaMemcpyAsync(&hl, dloss.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  if (loss) *loss = hl;
+  return MPCG_OK;
+}
+
+mpcg_status mpcg_mlp_train(mpcg_ctx_t ctx, mpcg_policy_t P, const mpcg_transition* data, int64_t count, int32_t steps,
+                           int32_t batch, float lr, int32_t target_sync, uint64_t seed, float* loss_out, void* stream) {
+  if (!ctx || !P || !data || count < 1 || steps < 1 || batch < 1 || target_sync < 1)
+    return fail(ctx, MPCG_ERR_INVALID_ARG, "bad MLP training arguments");
+  if (P->kind != 3) return fail(ctx, MPCG_ERR_BAD_POLICY, "mpcg_mlp_train needs an MLP policy");
+  const mpcg_options& o = ctx->opt;
+  if (P->H != o.mlp_hidden || P->nprec != o.nprec) return fail(ctx, MPCG_ERR_BAD_POLICY, "MLP shape differs from the options");
+  for (int64_t i = 0; i < count; ++i)
+    for (int j = 0; j < 4; ++j)
+      if (data[i].act[j] < 0 || data[i].act[j] >= o.nprec)
+        return fail(ctx, MPCG_ERR_INVALID_ARG, "transition %lld: action out of range", (long long)i);
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long np = mlp_nparams_dev(o.mlp_hidden, o.nprec);
+  const int chunk = 32;
+  const int nparts = (batch + chunk - 1) / chunk;
+  std::vector<float> hF((size_t)kNFeat * count), hFn((size_t)kNFeat * count), hR(count);
+  std::vector<int> hA((size_t)4 * count), hD(count);
+  for (int64_t i = 0; i < count; ++i) {
+    memcpy(&hF[(size_t)kNFeat * i], data[i].f, sizeof(float) * kNFeat);
+    memcpy(&hFn[(size_t)kNFeat * i], data[i].f_next, sizeof(float) * kNFeat);
+    for (int j = 0; j < 4; ++j) hA[(size_t)4 * i + j] = data[i].act[j];
+    hR[i] = data[i].reward;
+    hD[i] = data[i].done;
+  }
+  DevBuf dF, dFn, dA, dR, dD, dwt, dm, dv, didx, dpart, dl, dloss;
+  CK(ctx, dF.ensure(sizeof(float) * hF.size()));
+  CK(ctx, dFn.ensure(sizeof(float) * hFn.size()));
+  CK(ctx, dA.ensure(sizeof(int) * hA.size()));
+  CK(ctx, dR.ensure(sizeof(float) * hR.size()));
+  CK(ctx, dD.ensure(sizeof(int) * hD.size()));
+  CK(ctx, dwt.ensure(sizeof(float) * np));
+  CK(ctx, dm.ensure(sizeof(float) * np));
+  CK(ctx, dv.ensure(sizeof(float) * np));
+  CK(ctx, didx.ensure(sizeof(long long) * batch));
+  CK(ctx, dpart.ensure(sizeof(float) * np * nparts));
+  CK(ctx, dl.ensure(sizeof(double) * nparts));
+  CK(ctx, dloss.ensure(sizeof(double) * steps));
+  CK(ctx, cudaMemcpyAsync(dF.p, hF.data(), sizeof(float) * hF.size(), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(dFn.p, hFn.data(), sizeof(float) * hFn.size(), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(dA.p, hA.data(), sizeof(int) * hA.size(), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(dR.p, hR.data(), sizeof(float) * hR.size(), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(dD.p, hD.data(), sizeof(int) * hD.size(), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemsetAsync(dm.p, 0, sizeof(float) * np, s));
+  CK(ctx, cudaMemsetAsync(dv.p, 0, sizeof(float) * np, s));
+  CK(ctx, cudaMemcpyAsync(dwt.p, P->mlp.p, sizeof(float) * np, cudaMemcpyDeviceToDevice, s));
+  for (int t = 1; t <= steps; ++t) {
+    CK(ctx, launch_mlp_sample(didx.as<long long>(), batch, count, seed, (unsigned long long)t, s));
+    CK(ctx, launch_mlp_grad(P->mlp.as<float>(), dwt.as<float>(), o.mlp_hidden, o.nprec, dF.as<float>(), dFn.as<float>(),
+                            dA.as<int>(), dR.as<float>(), dD.as<int>(), nullptr, didx.as<long long>(), batch, chunk,
+                            (float)o.gamma, dpart.as<float>(), dl.as<double>(), s));
+    CK(ctx, launch_mlp_reduce_adam(dpart.as<float>(), nparts, np, nullptr, P->mlp.as<float>(), dm.as<float>(),
+                                   dv.as<float>(), t, lr, dl.as<double>(), dloss.as<double>() + (t - 1), s));
+    if (t % target_sync == 0)
+      CK(ctx, cudaMemcpyAsync(dwt.p, P->mlp.p, sizeof(float) * np, cudaMemcpyDeviceToDevice, s));
+  }
+  std::vector<double> hl(steps);
+  CK(ctx, cudaMemcpyAsync(hl.data(), dloss.p, sizeof(double) * steps, cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  if (loss_out)
+    for (int t = 0; t < steps; ++t) loss_out[t] = (float)hl[t];
   return MPCG_OK;
 }
 

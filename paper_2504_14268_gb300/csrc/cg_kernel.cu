@@ -296,10 +296,14 @@ __device__ void choose_action(const Launch& L, const DevSys& S, SysState* st, in
   const OptView& o = L.opt;
   const PolicyView& P = L.pol;
   const int s = state_of(o, k, rho);
-  if (P.kind == 3) {
-    if (threadIdx.x == 0) mlp_features(L, S, st, k, sm);
+  if (P.kind == 3 || S.feat_log) {
+    if (threadIdx.x == 0) {
+      mlp_features(L, S, st, k, sm);
+      if (S.feat_log && k < S.feat_cap)
+        for (int j = 0; j < kNFeat; ++j) S.feat_log[(long long)k * kNFeat + j] = sm.feat[j];
+    }
     __syncthreads();
-    mlp_forward(P.mlp, P.H, 4 * o.nprec, sm);
+    if (P.kind == 3 && !st->fp64_lock) mlp_forward(P.mlp, P.H, 4 * o.nprec, sm);
   }
   if (threadIdx.x == 0) {
     int expl = 0;
@@ -644,6 +648,10 @@ __device__ void continue_step(const Launch& L, const DevSys& S, SysState* st, do
       if (k + 1 >= S.max_iter) {
         st->outcome = MPCG_MAX_ITER;
         st->iters = S.max_iter;
+        if (S.feat_log && k + 1 < S.feat_cap) {  // the bootstrap state of the last transition
+          mlp_features(L, S, st, k + 1, sm);
+          for (int j = 0; j < kNFeat; ++j) S.feat_log[(long long)(k + 1) * kNFeat + j] = sm.feat[j];
+        }
       } else {
         sm.need_action = 1;
       }

@@ -72,7 +72,8 @@ struct DevSys {
   int trans_cap;
   int pad2;
   float feat_static[5];     // MLP static features of the matrix
-  int pad3;
+  int feat_cap;             // capacity of feat_log in feature vectors
+  float* feat_log;          // when set: the 16 features of every visited state, [k][16]
 };
 
 // Per-system state that persists across phases; written only by the CTA that arrives
@@ -159,6 +160,17 @@ cudaError_t launch_validate(int n, long long nnz, const int* rp, const int* ci, 
                             unsigned* flags, int* bad_row, cudaStream_t s);
 cudaError_t launch_convert(const DevMatrix& A, float* v32, float* vtf, __half* v16, __nv_bfloat16* vbf,
                            __half* v16r, __nv_bfloat16* vbfr, short* rexp, cudaStream_t s);
+long long mlp_nparams_dev(int H, int nprec);
+size_t mlp_grad_smem(int H, int nprec);
+cudaError_t mlp_set_smem_limit(size_t bytes);
+cudaError_t launch_mlp_grad(const float* w, const float* wt, int H, int nprec, const float* feats,
+                            const float* feats_next, const int* acts, const float* rew, const int* done, const float* y,
+                            const long long* idx, int B, int chunk, float gamma, float* part, double* lpart,
+                            cudaStream_t s);
+cudaError_t launch_mlp_reduce_adam(const float* part, int nparts, long long np, float* grad, float* w, float* m,
+                                   float* v, int t, float lr, const double* lpart, double* loss, cudaStream_t s);
+cudaError_t launch_mlp_sample(long long* idx, int B, long long count, unsigned long long seed, unsigned long long t,
+                              cudaStream_t s);
 cudaError_t launch_row_features(int n, const int* rp, const int* ci, const double* v, unsigned long long* out,
                                 cudaStream_t s);
 cudaError_t launch_to_format(const double* x, void* xlow, int n, int f, cudaStream_t s);

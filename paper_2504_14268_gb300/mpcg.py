@@ -58,6 +58,12 @@ class CStats(C.Structure):
                 ("device_bytes", C.c_int64), ("static_features", C.c_double * 5)]
 
 
+TRANS_DTYPE = np.dtype([
+    ("f", np.float32, 16), ("f_next", np.float32, 16), ("act", np.int32, 4), ("reward", np.float32),
+    ("done", np.int32),
+])
+assert TRANS_DTYPE.itemsize == 152
+
 REC_DTYPE = np.dtype([
     ("k", np.int32), ("state", np.int32), ("fmt", np.int8, 4), ("act", np.int8, 4),
     ("rho", np.float64), ("nu", np.float64), ("alpha", np.float64), ("sigma", np.float64),
@@ -98,6 +104,9 @@ SIGNATURES = {
     "mpcg_graph_results": (_st, [_vp, _vp, _vp]),
     "mpcg_graph_destroy": (_st, [_vp]),
     "mpcg_train_qtable": (_st, [_vp, _i32, _vp, _vp, _d, _i32, _i32, _vp, _vp, _vp]),
+    "mpcg_collect": (_st, [_vp, _i32, _vp, _vp, _d, _i32, _vp, _d, C.c_uint64, _vp, _i64, C.POINTER(_i64), _vp]),
+    "mpcg_mlp_loss_grad": (_st, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, C.POINTER(_d), _vp]),
+    "mpcg_mlp_train": (_st, [_vp, _vp, _vp, _i64, _i32, _i32, C.c_float, _i32, C.c_uint64, _vp, _vp]),
 }
 
 _LIB = None
@@ -329,6 +338,38 @@ class Context:
         self._check(lib().mpcg_train_qtable(self.handle, nsys, A, B, float(tol), int(t_max), int(episodes),
                                             policy.handle, _ptr(it), _stream(stream)))
         return it
+
+    def collect(self, mats, bs, tol: float, max_iter: int, behavior: "Policy", eps: float, episode: int,
+                cap: int | None = None, stream=None) -> np.ndarray:
+        """mpcg_collect: one epsilon-greedy episode per system; returns TRANS_DTYPE records."""
+        nsys = len(mats)
+        cap = cap if cap is not None else nsys * max_iter
+        out = np.zeros(cap, dtype=TRANS_DTYPE)
+        A = (C.c_void_p * nsys)(*[m.handle.value for m in mats])
+        B = (C.c_void_p * nsys)(*[_ptr(b).value for b in bs])
+        cnt = C.c_int64()
+        self._check(lib().mpcg_collect(self.handle, nsys, A, B, float(tol), int(max_iter), behavior.handle, float(eps),
+                                       int(episode), _ptr(out), int(cap), C.byref(cnt), _stream(stream)))
+        return out[: cnt.value]
+
+    def mlp_loss_grad(self, params, feats, acts, y, stream=None):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        f = np.ascontiguousarray(feats, dtype=np.float32)
+        a = np.ascontiguousarray(acts, dtype=np.int32)
+        yy = np.ascontiguousarray(y, dtype=np.float32)
+        g = np.zeros_like(p)
+        loss = C.c_double()
+        self._check(lib().mpcg_mlp_loss_grad(self.handle, _ptr(p), f.shape[0], _ptr(f), _ptr(a), _ptr(yy), _ptr(g),
+                                             C.byref(loss), _stream(stream)))
+        return loss.value, g
+
+    def mlp_train(self, policy: "Policy", data, steps: int, batch: int = 4096, lr: float = 1e-3,
+                  target_sync: int = 200, seed: int = 0, stream=None) -> np.ndarray:
+        d = np.ascontiguousarray(data, dtype=TRANS_DTYPE)
+        losses = np.zeros(steps, dtype=np.float32)
+        self._check(lib().mpcg_mlp_train(self.handle, policy.handle, _ptr(d), d.shape[0], int(steps), int(batch),
+                                         float(lr), int(target_sync), int(seed), _ptr(losses), _stream(stream)))
+        return losses
 
     def spmv(self, A: "Matrix", fmt: int, x, y, reps: int = 1, stream=None) -> float:
         ms = C.c_double()
