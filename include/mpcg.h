@@ -108,6 +108,10 @@ typedef struct {
   int32_t true_res_every;  /* >0: replace r by b - A x (fp64) every this many iterations */
   int32_t true_res_at_conv;/* 1: confirm a claimed convergence with b - A x (fp64)      */
   int32_t warm_start;      /* 1: x holds x_0 on entry; 0: x_0 = 0 (Algorithms 1 and 2)  */
+  int32_t op_mask[4];      /* per operation, bitmask of the entries of precs the policy may
+                              choose (bit a = precs[a]); 0 allows all. Section 5 notes the
+                              precision set can be customised; a mask customises it per
+                              operation (greedy, exploration and fallback respect it)    */
   int32_t on_breakdown;    /* 0: a breakdown ends the solve (paper); 1: inference solves
                               recompute r = b - A x in fp64, restart with p = r and finish
                               with every operation in fp64 (at most once per solve)     */

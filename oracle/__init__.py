@@ -55,7 +55,7 @@ class Opts(C.Structure):
         ("w1", C.c_double), ("w2", C.c_double), ("w3", C.c_double), ("lr", C.c_double),
         ("gamma", C.c_double), ("eps0", C.c_double), ("eps_floor", C.c_double), ("seed", C.c_uint64),
         ("unvisited_fallback", C.c_int), ("true_res_every", C.c_int), ("true_res_at_conv", C.c_int),
-        ("on_breakdown", C.c_int), ("mlp_hidden", C.c_int),
+        ("op_mask", C.c_int * 4), ("on_breakdown", C.c_int), ("mlp_hidden", C.c_int),
     ]
 
 
@@ -159,6 +159,7 @@ class Options:
     unvisited_fallback: int = FP64
     true_res_every: int = 0
     true_res_at_conv: int = 0
+    op_mask: tuple = (0, 0, 0, 0)
     on_breakdown: int = 0
     mlp_hidden: int = 64
 
@@ -168,6 +169,8 @@ class Options:
                      "eps0", "eps_floor", "seed", "unvisited_fallback", "true_res_every",
                      "true_res_at_conv", "on_breakdown", "mlp_hidden"):
             setattr(o, name, getattr(self, name))
+        for j in range(4):
+            o.op_mask[j] = int(self.op_mask[j])
         o.nprec = len(self.precs)
         for a, f in enumerate(self.precs):
             o.precs[a] = f

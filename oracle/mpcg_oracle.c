@@ -143,6 +143,8 @@ typedef struct {
                              -1 keeps the plain first-index argmax                    */
   int true_res_every;     /* >0: replace r by b - A x every this many iterations      */
   int true_res_at_conv;   /* 1: confirm a claimed convergence with b - A x            */
+  int op_mask[4];         /* per operation, bitmask of allowed entries of precs (0 = all);
+                             READING (extension): Section 5 allows customising P         */
   int on_breakdown;       /* 1: an inference solve that breaks down restarts once from
                              r = b - A x, p = r (fp64) and finishes in fp64            */
   int mlp_hidden;         /* MLP hidden width (64)                                     */
@@ -219,12 +221,27 @@ double orc_reward_breakdown(const orc_opts* o, const int act[4]) {
   return r;
 }
 
-/* First-index argmax over the nprec entries of a Q row (ties -> lowest index). */
-static int argmax_row(const double* row, int nprec) {
-  int best = 0;
-  for (int a = 1; a < nprec; ++a)
-    if (row[a] > row[best]) best = a;
+/* Allowed actions of operation j: bit a of op_mask[j], all when the mask is 0. */
+static int allowed(const orc_opts* o, int j, int a) {
+  return o->op_mask[j] == 0 || ((o->op_mask[j] >> a) & 1);
+}
+
+/* First-index argmax over the allowed entries of a Q row. */
+static int argmax_allowed(const orc_opts* o, int j, const double* row) {
+  int best = -1;
+  for (int a = 0; a < o->nprec; ++a)
+    if (allowed(o, j, a) && (best < 0 || row[a] > row[best])) best = a;
   return best;
+}
+
+/* The random action of an exploring operation: the (pick mod #allowed)-th allowed entry. */
+static int random_allowed(const orc_opts* o, int j, uint32_t pick) {
+  int cnt = 0;
+  for (int a = 0; a < o->nprec; ++a) cnt += allowed(o, j, a);
+  int k = (int)(pick % (uint32_t)cnt);
+  for (int a = 0; a < o->nprec; ++a)
+    if (allowed(o, j, a) && k-- == 0) return a;
+  return 0;
 }
 
 static double max_row(const double* row, int nprec) {
@@ -495,15 +512,15 @@ static int select_qtable(const orc_opts* o, const orc_policy* pol, int mode, int
     orc_draw(o->seed, ep, lane, (uint64_t)k, (uint64_t)j, &u, &pick);
     if (u < eps) {
       *explored = 1;
-      return (int)(pick % (uint32_t)o->nprec);
+      return random_allowed(o, j, pick);
     }
-    return argmax_row(row, o->nprec);
+    return argmax_allowed(o, j, row);
   }
   if (o->unvisited_fallback >= 0 && pol->visits[(int64_t)j * S + s] == 0) {
     int a = index_of(o, o->unvisited_fallback);
-    return a >= 0 ? a : argmax_row(row, o->nprec);
+    return (a >= 0 && allowed(o, j, a)) ? a : argmax_allowed(o, j, row);
   }
-  return argmax_row(row, o->nprec);
+  return argmax_allowed(o, j, row);
 }
 
 /* Q_j(s, a_j) += lr (R + gamma max_p Q_j(s', p) - Q_j(s, a_j))   (Section 4.1, Alg. 1 non-terminal)
@@ -602,13 +619,13 @@ int orc_run(const orc_opts* o, int n, const int32_t* rp, const int32_t* ci, cons
       /* Learned policy: greedy per operation on the MLP's Q-values (same tie rule). */
       orc_mlp_forward(pol->mlp, H, nout, f, h1, h2, qout);
       for (int j = 0; j < 4; ++j) {
-        act[j] = argmax_row(qout + j * o->nprec, o->nprec);
+        act[j] = argmax_allowed(o, j, qout + j * o->nprec);
         if (mode == ORC_MODE_TRAIN) {
           double u;
           uint32_t pick;
           orc_draw(o->seed, ep, lane, (uint64_t)k, (uint64_t)j, &u, &pick);
           if (u < eps) {
-            act[j] = (int)(pick % (uint32_t)o->nprec);
+            act[j] = random_allowed(o, j, pick);
             explored = 1;
           }
         }

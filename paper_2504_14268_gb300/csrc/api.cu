@@ -202,6 +202,12 @@ mpcg_status build_optview(mpcg_ctx_t ctx, const mpcg_options& o, OptView& v) {
   v.true_at_conv = o.true_res_at_conv;
   v.warm_start = o.warm_start;
   v.on_breakdown = o.on_breakdown;
+  for (int j = 0; j < 4; ++j) {
+    const unsigned all = (1u << o.nprec) - 1u;
+    const unsigned m = o.op_mask[j] ? ((unsigned)o.op_mask[j] & all) : all;
+    if (!m) return fail(ctx, MPCG_ERR_INVALID_ARG, "op_mask[%d] allows no entry of precs", j);
+    v.op_mask[j] = (int)m;
+  }
   return MPCG_OK;
 }
 

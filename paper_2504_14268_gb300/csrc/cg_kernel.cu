@@ -221,11 +221,23 @@ __device__ __forceinline__ double row_max(const double* row, int n) {
   return m;
 }
 
-__device__ __forceinline__ int row_argmax(const double* row, int n) {
-  int b = 0;
-  for (int a = 1; a < n; ++a)
-    if (row[a] > row[b]) b = a;
+// First-index argmax over the allowed entries (bit a of mask).
+__device__ __forceinline__ int row_argmax(const double* row, int n, unsigned mask) {
+  int b = -1;
+  for (int a = 0; a < n; ++a)
+    if ((mask >> a) & 1u)
+      if (b < 0 || row[a] > row[b]) b = a;
   return b;
+}
+
+// The k-th allowed index (k < popcount(mask)).
+__device__ __forceinline__ int kth_allowed(unsigned mask, int k) {
+  for (int a = 0; a < 32; ++a)
+    if ((mask >> a) & 1u) {
+      if (k == 0) return a;
+      --k;
+    }
+  return 0;
 }
 
 // Q_j(s, a_j) += lr (R + gamma max_p Q_j(s', p) - Q_j(s, a_j)), terminal without the max term.
@@ -317,17 +329,19 @@ __device__ void choose_action(const Launch& L, const DevSys& S, SysState* st, in
         const int row = k < P.sched_len ? k : P.sched_len - 1;
         fmt = P.sched[row * 4 + j];
       } else {
+        const unsigned mask = (unsigned)o.op_mask[j];
         if (P.kind == 2) {
           const double* Qsrc = L.train ? S.Qpriv : P.Q;
           const double* row = Qsrc + ((long long)j * (o.b_bins * o.r_bins) + s) * o.nprec;
-          act = row_argmax(row, o.nprec);
-          if (!L.train && P.visits && o.fallback_fmt >= 0 && o.fallback_idx >= 0 &&
+          act = row_argmax(row, o.nprec, mask);
+          if (!L.train && P.visits && o.fallback_fmt >= 0 && o.fallback_idx >= 0 && ((mask >> o.fallback_idx) & 1u) &&
               P.visits[j * (o.b_bins * o.r_bins) + s] == 0)
             act = o.fallback_idx;
         } else {
-          int b = 0;
-          for (int a = 1; a < o.nprec; ++a)
-            if (sm.out[j * o.nprec + a] > sm.out[j * o.nprec + b]) b = a;
+          int b = -1;
+          for (int a = 0; a < o.nprec; ++a)
+            if ((mask >> a) & 1u)
+              if (b < 0 || sm.out[j * o.nprec + a] > sm.out[j * o.nprec + b]) b = a;
           act = b;
         }
         if (L.train) {
@@ -339,7 +353,7 @@ __device__ void choose_action(const Launch& L, const DevSys& S, SysState* st, in
           const U64x4 w = philox4x64_10(c, o.seed, 0x6d706367ull);
           const double u = (double)(w.v[0] >> 11) * 0x1.0p-53;
           if (u < L.eps) {
-            act = (int)((unsigned)(w.v[1] & 0xffffffffull) % (unsigned)o.nprec);
+            act = kth_allowed(mask, (int)((unsigned)(w.v[1] & 0xffffffffull) % (unsigned)__popc(mask)));
             expl = 1;
           }
         }

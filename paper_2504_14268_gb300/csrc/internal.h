@@ -122,6 +122,7 @@ struct OptView {
   int fallback_idx;         // its index in precs (-1 if absent)
   int true_every, true_at_conv, warm_start, t_bin;
   int on_breakdown, pad;
+  int op_mask[4];           // allowed action indices per operation (all bits set = no restriction)
 };
 
 // Arguments of one launch of the persistent kernel.

@@ -42,7 +42,8 @@ class COptions(C.Structure):
         ("w1", C.c_double), ("w2", C.c_double), ("w3", C.c_double), ("lr", C.c_double), ("gamma", C.c_double),
         ("eps0", C.c_double), ("eps_floor", C.c_double), ("seed", C.c_uint64),
         ("unvisited_fallback", C.c_int32), ("true_res_every", C.c_int32), ("true_res_at_conv", C.c_int32),
-        ("warm_start", C.c_int32), ("on_breakdown", C.c_int32), ("mlp_hidden", C.c_int32),
+        ("warm_start", C.c_int32), ("op_mask", C.c_int32 * 4), ("on_breakdown", C.c_int32),
+        ("mlp_hidden", C.c_int32),
     ]
 
 
@@ -186,17 +187,20 @@ class Options:
     true_res_every: int = 0
     true_res_at_conv: int = 0
     warm_start: int = 0
+    op_mask: tuple = (0, 0, 0, 0)
     on_breakdown: int = 0
     mlp_hidden: int = 64
 
     def c(self) -> COptions:
         o = COptions()
         for f in fields(self):
-            if f.name in ("precs", "cost"):
+            if f.name in ("precs", "cost", "op_mask"):
                 continue
             setattr(o, f.name, getattr(self, f.name))
         if len(self.precs) != len(self.cost):
             raise ValueError("precs and cost must have the same length")
+        for j in range(4):
+            o.op_mask[j] = int(self.op_mask[j])
         o.nprec = len(self.precs)
         for a, (p, c) in enumerate(zip(self.precs, self.cost)):
             o.precs[a] = p

@@ -175,3 +175,30 @@ def test_training_learns_cheap_safe_schedule_on_easy_problem():
     assert out.outcome == O.CONVERGED
     cost = sum(o.cost[int(f)] for f in out.hist["fmt"].ravel()) / len(out.hist)
     assert cost < 4 * o.cost[O.FP64]
+
+
+def test_operation_masks_restrict_greedy_and_exploration():
+    """op_mask: op 0 may use only fp32/fp64 (indices 3, 4). The one-step episode of the closed
+    form test then updates Q_0(s_0, fp32) (first allowed index), the other operations keep
+    fp16; exploration draws stay uniform over the allowed entries."""
+    A = _scaled_identity()
+    b = np.arange(1.0, 9.0)
+    o = O.Options(min_k=0, eps0=0.0, eps_floor=0.0, op_mask=(0b11000, 0, 0, 0))
+    qt = O.QTable.zeros(o)
+    m = 10
+    O.train_sequential(o, A, b, 1e-6, 50, m, qt)
+    s0 = O.state(o, 0, 1.0)
+    R = 16 - 0.1 * (1.0 + 0.8 * 3) + 10  # fp32 for op 0, fp16 for the others
+    assert qt.Q[0, s0, 3] == pytest.approx((1 - 0.9 ** m) * R, rel=1e-12)
+    assert qt.Q[0, s0, 0] == 0.0
+    for j in (1, 2, 3):
+        assert qt.Q[j, s0, 0] == pytest.approx((1 - 0.9 ** m) * R, rel=1e-12)
+    # exploration with epsilon = 1 picks only allowed entries, uniformly
+    A2, b2, _ = I.cfg_poisson32()
+    o2 = O.Options(min_k=0, seed=4, op_mask=(0b10110, 0, 0, 0))
+    out = O.solve(o2, A2, b2, 1e-30, 600, qtable=O.QTable.zeros(o2), train=True, episode=1, eps=1.0)
+    picks = out.hist["act"][:, 0]
+    assert set(np.unique(picks)) <= {1, 2, 4}
+    cnt = np.array([np.sum(picks == a) for a in (1, 2, 4)])
+    exp = len(picks) / 3
+    assert np.sum((cnt - exp) ** 2 / exp) < 13.8  # chi-square, 2 dof, p ~ 0.001
