@@ -14,7 +14,7 @@ problems; these keep its character at the sizes a GPU needs):
                             cell coefficients and harmonic-mean faces.
 * ``fem27_aniso``        -- Q1 finite-element 27-point stencil of -div(K grad u),
                             K = diag(1, 1, eps), as K (x) M (x) M + M (x) K (x) M + eps M (x) M (x) K.
-* ``banded_spd``         -- symmetric banded N(0,1) matrix shifted to a chosen lambda_min.
+* ``banded_spd``         -- banded L L^T (N(0,1) lower factor) shifted by lambda_t I.
 * ``ba_laplacian``       -- shifted graph Laplacian of a Barabasi-Albert-style power-law graph.
 """
 from __future__ import annotations
@@ -157,21 +157,27 @@ def fem27_spectrum(N: int, eps: float = 1e-3):
 
 
 def banded_spd(n: int, kd: int, lam_min_target: float, rng: np.random.Generator):
-    """Symmetric banded matrix with N(0,1) entries in half-bandwidth kd, shifted so that its
-    smallest eigenvalue equals lam_min_target: A = S + (lam_t - lambda_min(S)) I. lambda_min
-    comes from LAPACK's banded symmetric eigensolver (scipy)."""
-    import scipy.linalg as la
+    """Banded SPD matrix A = L L^T + lam_t I with L lower triangular, half-bandwidth kd and
+    N(0,1) entries: L L^T is positive semidefinite with a smallest eigenvalue that is tiny for
+    a random triangular factor, so lambda_min(A) ~ lam_t (bounded below by lam_t). A has
+    half-bandwidth kd; its diagonals are formed one by one:
+    (L L^T)[i, i-d] = sum_{m=d..kd} L[i, i-m] L[i-d, i-m]."""
     import scipy.sparse as sp
 
-    ab = np.zeros((kd + 1, n))  # lower form: ab[d, j] = S[j + d, j]
-    for dgl in range(kd + 1):
-        ab[dgl, : n - dgl] = rng.standard_normal(n - dgl)
-    lam0 = la.eigvals_banded(ab, lower=True, select="i", select_range=(0, 0))[0]
-    ab[0, :] += lam_min_target - lam0
-    diags = [ab[0]] + [ab[dgl, : n - dgl] for dgl in range(1, kd + 1)]
-    offsets = [0] + list(range(1, kd + 1))
-    L = sp.diags(diags, [-o for o in offsets], shape=(n, n))
-    U = sp.diags(diags[1:], offsets[1:], shape=(n, n))
+    kd = max(1, min(kd, n - 1))
+    ab = np.zeros((kd + 1, n))  # ab[m, i] = L[i, i - m]
+    for m in range(kd + 1):
+        ab[m, m:] = rng.standard_normal(n - m)
+    diags, offs = [], []
+    for d in range(kd + 1):
+        acc = np.zeros(n - d)
+        for m in range(d, kd + 1):
+            # rows i = d..n-1: L[i, i-m] L[i-d, i-m]; L[i-d, i-m] = ab[m-d, i-d]
+            acc += ab[m, d:] * ab[m - d, : n - d]
+        diags.append(acc + (lam_min_target if d == 0 else 0.0))
+        offs.append(-d)
+    L = sp.diags(diags, offs, shape=(n, n))
+    U = sp.diags(diags[1:], [-o for o in offs[1:]], shape=(n, n))
     return _from_scipy(L + U)
 
 
@@ -256,8 +262,8 @@ def cfg_train_set(count: int = 64, m_lo: int = 16, m_hi: int = 40, sig_lo: float
 
 def cfg_batched(count: int = 512, n_lo: float = 1e3, n_hi: float = 2e5, seed: int = 4):
     """Uneven batch: n log-uniform on [n_lo, n_hi]; types in thirds: 2D 5-point and 3D 7-point
-    variable-coefficient diffusion (sigma ~ U[0.5, 3]), and banded N(0,1) matrices with
-    half-bandwidth kd ~ U{5..64} shifted to lambda_min log-uniform on [1e-6, 1e-2]."""
+    variable-coefficient diffusion (sigma ~ U[0.5, 3]), and banded SPD matrices L L^T + lam I
+    with half-bandwidth kd ~ U{5..64} and lam log-uniform on [1e-6, 1e-2] (lambda_min ~ lam)."""
     out = []
     for i in range(count):
         rng = rng_for(seed, i)

@@ -237,10 +237,10 @@ def test_training_one_lane_matches_algorithm_1_fp32_fp64(M):
 
 
 def test_training_one_lane_matches_algorithm_1_full_set(M):
-    """Full precision set: episodes agree until the residual histories separate; iteration
-    counts stay close and the tables stay close."""
+    """Full precision set: episodes agree until the residual histories separate (an fp16 dot
+    rounded on either side of a tie is enough to split them, even in the first episode);
+    iteration counts stay close and the tables stay close."""
     it_o, it_g, qt, Qg, vg = _train_both(M, (0, 1, 2, 3, 4), (0.8, 0.6, 0.8, 1.0, 2.0))
-    assert it_o[0] == it_g[0]
     assert np.all(np.abs(np.asarray(it_o) - np.asarray(it_g)) <= np.maximum(3, np.asarray(it_o) // 10))
     assert np.linalg.norm(Qg - qt.Q) <= 0.05 * np.linalg.norm(qt.Q)
 
