@@ -262,6 +262,20 @@ mpcg_status mpcg_graph_launch(mpcg_graph_t g, void* stream);
 mpcg_status mpcg_graph_results(mpcg_graph_t g, mpcg_result* res, void* stream);
 mpcg_status mpcg_graph_destroy(mpcg_graph_t g);
 
+/* Same solve as mpcg_solve (no history) for callers that cannot allocate device memory
+ * while they solve, e.g. code running under a fixed device-memory budget or inside a pool
+ * that must not grow. The paper has no counterpart; this is a property of the library.
+ * This call allocates nothing: its scratch (work vectors, team barriers, partial sums,
+ * state) lives in a static device array of 1 MiB + 28 bytes per row for at most
+ * 1,048,576 rows (about 29 MiB), which every GPU that loads the library holds until the
+ * process exits. Systems with more rows are rejected with MPCG_ERR_INVALID_ARG. b and x must
+ * be device pointers; the matrix and the policy are created beforehand with the calls
+ * above. The first call on a device looks up the array's device address, so make that
+ * first call before any stream capture. All calls share the one array: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and must not be issued. */
+mpcg_status mpcg_solve_noalloc(mpcg_ctx_t ctx, mpcg_matrix_t A, const double* b, double* x, double tol,
+                               int32_t max_iter, mpcg_policy_t policy, mpcg_result* res, void* stream);
+
 /* ---- training --------------------------------------------------------------------- */
 
 /* Tabular Q-learning (Algorithm 1) on nsys training systems, batched: in every round

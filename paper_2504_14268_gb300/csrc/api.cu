@@ -1394,4 +1394,142 @@ mpcg_status mpcg_mlp_train(mpcg_ctx_t ctx, mpcg_policy_t P, const mpcg_transitio
   return MPCG_OK;
 }
 
+// ---- solve without device allocation ------------------------------------------------------
+//
+// For callers that cannot allocate device memory at solve time (for example code running
+// under a fixed device-memory budget, inside a memory pool that must not grow, or between
+// the set-up and the teardown of an embedding application that reserved all memory up
+// front): every scratch buffer of the persistent kernel for one system lives in this
+// file-scope device array, reserved when the library is loaded on a device and held until
+// the process exits. Layout: a 1 MiB control area (system descriptor, state, result,
+// status word, team barriers, team tables, CTA partials), then the work vectors r, p, q and
+// p's low-precision copy (28 bytes per row) for at most kNoAllocMaxRows rows.
+
+constexpr int kNoAllocMaxRows = 1 << 20;
+constexpr int kNoAllocMaxGrid = 2048;
+constexpr size_t kNoAllocCtrl = 1 << 20;
+constexpr size_t kNoAllocBytes = kNoAllocCtrl + 28 * (size_t)kNoAllocMaxRows + 4 * 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+// Device address of g_noalloc_scratch per device ordinal, looked up once per device.
+void* g_noalloc_ptr[64] = {nullptr};
+}  // namespace
+
+mpcg_status mpcg_solve_noalloc(mpcg_ctx_t ctx, mpcg_matrix_t A, const double* b, double* x, double tol,
+                               int32_t max_iter, mpcg_policy_t policy, mpcg_result* res, void* stream) {
+  if (!ctx || !A || !policy || !res) return fail(ctx, MPCG_ERR_INVALID_ARG, "NULL argument");
+  ctx->err.clear();
+  const int n = A->dm.n;
+  if (n > kNoAllocMaxRows)
+    return fail(ctx, MPCG_ERR_INVALID_ARG, "mpcg_solve_noalloc supports at most %d rows (got %d)", kNoAllocMaxRows, n);
+  if (n > 0 && (!b || !x)) return fail(ctx, MPCG_ERR_INVALID_ARG, "b or x is NULL");
+  if (n > 0 && (!is_device_ptr(b) || !is_device_ptr(x)))
+    return fail(ctx, MPCG_ERR_INVALID_ARG, "mpcg_solve_noalloc needs device pointers for b and x");
+  if (!(tol >= 0.0) || max_iter < 0) return fail(ctx, MPCG_ERR_INVALID_ARG, "tol must be >= 0 and max_iter >= 0");
+  if (A->ctx != ctx || policy->ctx != ctx) return fail(ctx, MPCG_ERR_INVALID_ARG, "objects belong to another context");
+  if (ctx->device < 0 || ctx->device >= 64) return fail(ctx, MPCG_ERR_INVALID_ARG, "device ordinal out of range");
+  cudaError_t ce = cudaSetDevice(ctx->device);
+  if (ce != cudaSuccess) return fail(ctx, MPCG_ERR_CUDA, "cudaSetDevice failed: %s", cudaGetErrorString(ce));
+  if (!g_noalloc_ptr[ctx->device]) {
+    void* ptr = nullptr;
+    ce = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (ce != cudaSuccess || !ptr)
+      return fail(ctx, MPCG_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(ce));
+    g_noalloc_ptr[ctx->device] = ptr;
+  }
+  unsigned char* base = (unsigned char*)g_noalloc_ptr[ctx->device];
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool stream_shape = uses_stream(A->dm);
+  const int grid = ctx->nsm * (stream_shape ? ctx->occ_s : ctx->occ);
+  if (grid > kNoAllocMaxGrid) return fail(ctx, MPCG_ERR_INTERNAL, "grid of %d CTAs exceeds the scratch layout", grid);
+  // control area
+  DevSys* d_sys = (DevSys*)(base + 0);
+  SysState* d_st = (SysState*)(base + 4096);
+  mpcg_result* d_res = (mpcg_result*)(base + 12288);
+  unsigned* d_err = (unsigned*)(base + 16384);
+  unsigned* d_bars = (unsigned*)(base + 20480);
+  int* d_tsize = (int*)(base + 24576);
+  int* d_tfirst = d_tsize + 4;
+  int* d_tsoff = d_tsize + 8;
+  int* d_tsys = d_tsize + 12;
+  int* d_cta_team = (int*)(base + 32768);
+  int* d_cta_rank = d_cta_team + kNoAllocMaxGrid;
+  double* d_part = (double*)(base + 65536);
+  static_assert(4096 >= sizeof(DevSys) && 8192 >= sizeof(SysState), "control area too small");
+  static_assert(65536 + sizeof(double) * kNSlot * kNoAllocMaxGrid <= kNoAllocCtrl, "control area too small");
+  // work vectors
+  unsigned char* w = base + kNoAllocCtrl;
+  auto take = [&](size_t bytes) {
+    unsigned char* r = w;
+    w += (bytes + 255) / 256 * 256;
+    return (void*)r;
+  };
+  DevSys hs;
+  memset(&hs, 0, sizeof(hs));
+  hs.A = A->dm;
+  hs.b = b;
+  hs.x = x;
+  hs.r = (double*)take(8 * (size_t)n);
+  hs.p = (double*)take(8 * (size_t)n);
+  hs.q = take(8 * (size_t)n);
+  hs.plow = take(4 * (size_t)n);
+  hs.tol = tol;
+  hs.max_iter = max_iter;
+  for (int j = 0; j < 5; ++j) hs.feat_static[j] = A->feat[j];
+  // one team for the system, the remaining CTAs in an empty second team
+  const int ts = team_size_for(A->dm.nnz + 4LL * n, grid);
+  int tsize[2] = {ts, std::max(1, grid - ts)};
+  int tfirst[3] = {0, ts, grid};
+  int tsoff[3] = {0, 1, 1};
+  int tsys[1] = {0};
+  static thread_local int cta_team[kNoAllocMaxGrid], cta_rank[kNoAllocMaxGrid];
+  for (int c = 0; c < grid; ++c) {
+    cta_team[c] = c < ts ? 0 : 1;
+    cta_rank[c] = c < ts ? c : c - ts;
+  }
+  CK(ctx, cudaMemcpyAsync(d_sys, &hs, sizeof(DevSys), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(d_tsize, tsize, sizeof(tsize), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(d_tfirst, tfirst, sizeof(tfirst), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(d_tsoff, tsoff, sizeof(tsoff), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(d_tsys, tsys, sizeof(tsys), cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(d_cta_team, cta_team, sizeof(int) * grid, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(d_cta_rank, cta_rank, sizeof(int) * grid, cudaMemcpyHostToDevice, s));
+  // the array keeps the previous call's contents: barriers and the status word start at zero
+  CK(ctx, cudaMemsetAsync(d_bars, 0, sizeof(unsigned) * kBarStride * 2, s));
+  CK(ctx, cudaMemsetAsync(d_err, 0, sizeof(unsigned), s));
+  Launch L;
+  memset(&L, 0, sizeof(L));
+  L.sys = d_sys;
+  L.st = d_st;
+  L.nsys = 1;
+  L.nteams = 2;
+  L.cta_team = d_cta_team;
+  L.cta_rank = d_cta_rank;
+  L.team_size = d_tsize;
+  L.team_first = d_tfirst;
+  L.team_sys_off = d_tsoff;
+  L.team_sys = d_tsys;
+  L.bars = d_bars;
+  L.partials = d_part;
+  L.res = d_res;
+  L.err = d_err;
+  mpcg_status st = fill_policy(ctx, policy, L.pol);
+  if (st != MPCG_OK) return st;
+  L.opt = ctx->ov;
+  L.train = 0;
+  L.stream_stage = stream_shape ? kStageBytes : 0;
+  L.timeout_cycles = kTimeoutCycles;
+  cudaGetLastError();
+  CK(ctx, launch_cg(L, grid, stream_shape ? 2 * (size_t)kStageBytes : 0, s));
+  unsigned herr = 0;
+  CK(ctx, cudaMemcpyAsync(res, d_res, sizeof(mpcg_result), cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaMemcpyAsync(&herr, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  if (herr == DERR_TIMEOUT) return fail(ctx, MPCG_ERR_TIMEOUT, "a device-side barrier wait exceeded its limit");
+  if (herr) return fail(ctx, MPCG_ERR_INTERNAL, "device status word %u", herr);
+  return MPCG_OK;
+}
+
 }  // extern "C"

@@ -100,6 +100,7 @@ SIGNATURES = {
     "mpcg_policy_destroy": (_st, [_vp]),
     "mpcg_solve": (_st, [_vp, _vp, _vp, _vp, _d, _i32, _vp, C.POINTER(CResult), _vp, _i32, _vp]),
     "mpcg_solve_batched": (_st, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "mpcg_solve_noalloc": (_st, [_vp, _vp, _vp, _vp, _d, _i32, _vp, C.POINTER(CResult), _vp]),
     "mpcg_graph_create": (_st, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(_vp)]),
     "mpcg_graph_launch": (_st, [_vp, _vp]),
     "mpcg_graph_results": (_st, [_vp, _vp, _vp]),
@@ -308,6 +309,15 @@ class Context:
         self._check(lib().mpcg_solve(self.handle, A.handle, _ptr(b), _ptr(x), float(tol), int(max_iter),
                                      policy.handle, C.byref(res), _ptr(history), int(cap), _stream(stream)))
         return result_dict(res), history
+
+    def solve_noalloc(self, A: "Matrix", b, x, tol: float, max_iter: int, policy: "Policy", stream=None) -> dict:
+        """mpcg_solve_noalloc: the solve without device allocation (b, x device tensors)."""
+        _check_dtype(b, "b", "float64")
+        _check_dtype(x, "x", "float64")
+        res = CResult()
+        self._check(lib().mpcg_solve_noalloc(self.handle, A.handle, _ptr(b), _ptr(x), float(tol), int(max_iter),
+                                             policy.handle, C.byref(res), _stream(stream)))
+        return result_dict(res)
 
     def solve_batched(self, mats, bs, xs, tols, max_iters, policy: "Policy", stream=None):
         """mpcg_solve_batched with device tensors. Returns a list of result dicts."""
