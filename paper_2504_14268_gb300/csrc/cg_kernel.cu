@@ -924,6 +924,8 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
       {
         const double alpha = sm.bc.alpha;
         const int p1 = sm.bc.fmt[0], p2 = sm.bc.fmt[1], p4 = sm.bc.fmt[3];
+        // with z = r and an fp64 dot, sigma is ||r||^2 itself: one DFMA per row saved
+        const bool sig_rr = (p2 == F64 && p4 == F64);
         double rr = 0.0;
         DotAcc sg{0.0, 0.f, 0.f};
         for (int i0 = R.r0 + threadIdx.x; i0 < R.r1; i0 += kUnroll * kThreads) {
@@ -943,12 +945,12 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
               const double ri = fma(-alpha, qv[u], ro[u]);
               S.r[i] = ri;
               rr = fma(ri, ri, rr);
-              sigma_term(ri, p2, p4, sg);
+              if (!sig_rr) sigma_term(ri, p2, p4, sg);
             }
           }
         }
         rr = cta_sum(rr, sm.red);
-        const double sp = cta_dot(sg, sm.red);
+        const double sp = sig_rr ? rr : cta_dot(sg, sm.red);
         write_partial(L, 0, rr);
         write_partial(L, 1, sp);
         if (!team_step(L, T, st, sm, [&] {

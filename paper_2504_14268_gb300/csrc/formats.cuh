@@ -136,6 +136,13 @@ __device__ __forceinline__ void store_fmt(void* p, long long i, double v, int f)
 // so the per-row work converts between fp32 and fp64 by assembling bit patterns and rounds
 // fp64 values onto the 16-bit formats through fp32.
 
+// The rare cases of the conversions below go through out-of-line functions, so that the
+// common path never issues (even predicated off) an instruction of the fp64 pipe.
+static __device__ __noinline__ double f2d_slow(float v) { return (double)v; }
+static __device__ __noinline__ double mul_pow2_slow(double x, int e) {
+  return x * __longlong_as_double((long long)((unsigned long long)(e + 1023) << 52));
+}
+
 // Exact fp32 -> fp64.
 __device__ __forceinline__ double f2d(float v) {
   const unsigned u = __float_as_uint(v);
@@ -145,7 +152,7 @@ __device__ __forceinline__ double f2d(float v) {
     return __hiloint2double((int)hi, (int)(a << 29));
   }
   if (a == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
-  return (double)v;  // subnormal, infinite or NaN
+  return f2d_slow(v);  // subnormal, infinite or NaN
 }
 
 // x * 2^e for an fp64 x whose result stays in the normal range (exponent-field add);
@@ -155,7 +162,7 @@ __device__ __forceinline__ double scale2(double x, int e) {
   const int ex = (hi >> 20) & 0x7ff;
   if (e == 0 || x == 0.0) return x;
   if (ex > 0 && ex < 0x7ff && ex + e > 0 && ex + e < 0x7ff) return __hiloint2double(hi + (e << 20), __double2loint(x));
-  return x * __longlong_as_double((long long)((unsigned long long)(e + 1023) << 52));
+  return mul_pow2_slow(x, e);
 }
 
 // Truncation of x onto fp32 with the last bit set when bits were dropped ("round to odd").
@@ -208,6 +215,8 @@ __device__ __forceinline__ float round_f2f(float v, int f) {
   }
 }
 
+static __device__ __noinline__ float round_d2f_slow(double x, int f) { return (float)round_fmt(x, f); }
+
 // fl_f(x) of an fp64 value, returned as fp32 (exact), for f other than fp64.
 __device__ __forceinline__ float round_d2f(double x, int f) {
   float o;
@@ -216,7 +225,7 @@ __device__ __forceinline__ float round_d2f(double x, int f) {
   } else if (d2f_odd(x, o)) {
     return round_f2f(o, f);
   }
-  return (float)round_fmt(x, f);  // outside the fp32 normal range: exact bit-level rounding
+  return round_d2f_slow(x, f);  // outside the fp32 normal range: exact bit-level rounding
 }
 
 // Value set of format a contains that of format b (so rounding onto a is the identity on b).

@@ -19,7 +19,7 @@ constexpr int kNSlot = 4;           // partial sums per CTA and phase
 constexpr int kNFeat = 16;          // MLP input features
 constexpr int kMaxHidden = 128;     // MLP hidden width bound
 constexpr int kBarStride = 32;      // uint32 words between team barriers (128 bytes)
-constexpr int kStageBytes = 54 * 1024;  // one stage of the stream schedule's shared-memory ring
+constexpr int kStageBytes = 24 * 1024;  // one stage of the stream schedule's shared-memory ring
 
 enum Sched : int { SCHED_VECTOR = 0, SCHED_STREAM = 1 };
 

@@ -93,49 +93,76 @@ __device__ __forceinline__ void half_gaps(float r, int f, float& below, float& a
 }
 
 // Products of one row slice accumulated by one lane.
-// fp64 values: fp64 accumulation. fp32: fp32 accumulation (the output format is fp32, so
-// the accumulation error stays at its last place). fp16, bf16, tf32 (and the row-scaled
-// formats): the products are exact in fp32 and the fp32 sum s carries the bound
-// m = sum |a_ij x_j|; the recursive-summation bound |s - exact| <= gamma_n m (Higham,
-// "Accuracy and Stability of Numerical Algorithms", Section 4.2) tells whether s rounds to
-// the same value of the output format as the exact sum. When the error interval reaches
-// a rounding midpoint (a small fraction of rows), lane 0 sums the row again in fp64 and
-// rounds that sum, so every row of q is the correctly rounded value of its sum.
-template <typename VT>
+// fp64 values: fp64 accumulation. fp32 (COMP = false): fp32 accumulation (the output format
+// is fp32, so the accumulation error stays at its last place). fp16, bf16, tf32 and the
+// row-scaled formats (COMP = true): the products are exact in fp32 and are summed with
+// Knuth's TwoSum, so s + (the exact sum of the rounding errors t_i) equals the exact row sum;
+// c accumulates the t_i in fp32 and a the |t_i|, which bounds the error of c by
+// gamma_n a (Higham, "Accuracy and Stability of Numerical Algorithms", Sections 4.2 and 4.3).
+// The pair (s, c) is rounded once onto the output format; only when the residual error
+// bound reaches a rounding midpoint (about n u^2 sum |a_ij x_j| away, essentially never) is
+// the row summed again in fp64 by lane 0.
+template <typename VT, bool COMP>
 struct RowAcc {
-  float s = 0.f, m = 0.f;
-  __device__ __forceinline__ void add(VT a, VT x) {
-    const float af = to_acc(a), xf = to_acc(x);
-    s = fmaf(af, xf, s);
-    if constexpr (sizeof(VT) == 2) m = fmaf(fabsf(af), fabsf(xf), m);
-    else m = fmaf(fabsf(af), fabsf(xf), m);
+  float s = 0.f, c = 0.f, a = 0.f;
+  __device__ __forceinline__ void add(VT av, VT xv) {
+    const float af = to_acc(av), xf = to_acc(xv);
+    if constexpr (COMP) {
+      const float p = __fmul_rn(af, xf);
+      float t;
+      two_sum(s, p, s, t);
+      c = __fadd_rn(c, t);
+      a = __fadd_rn(a, fabsf(t));
+    } else {
+      s = fmaf(af, xf, s);
+    }
   }
   template <int K>
   __device__ __forceinline__ void reduce(unsigned mask) {
 #pragma unroll
     for (int o = K / 2; o > 0; o >>= 1) {
-      s += __shfl_xor_sync(mask, s, o);
-      m += __shfl_xor_sync(mask, m, o);
+      const float so = __shfl_xor_sync(mask, s, o);
+      if constexpr (COMP) {
+        const float co = __shfl_xor_sync(mask, c, o), ao = __shfl_xor_sync(mask, a, o);
+        float t;
+        two_sum(s, so, s, t);
+        c = __fadd_rn(__fadd_rn(c, co), t);
+        a = __fadd_rn(__fadd_rn(a, ao), fabsf(t));
+      } else {
+        s += so;
+      }
     }
   }
   // Row sum rounded onto p1 (fp32 result). `exact` recomputes the row in fp64 when needed.
   template <class Exact>
   __device__ __forceinline__ float rounded(int p1, int len, Exact&& exact) const {
-    if (base_fmt(p1) == F32 || !isfinite(s)) return s;
-    const float r = round_f2f(s, p1);
-    if (!isfinite(r)) return r;
-    float below, above;
-    half_gaps(r, p1, below, above);
-    // gamma_n m with n = len additions, inflated for the rounding of m itself
-    const float err = m * (float)(len + 2) * 6.0e-8f;
-    const float d = s - r;
-    if (d + err < above && -d + err < below) return r;
-    return round_d2f(exact(), p1);
+    if constexpr (!COMP) {
+      return s;
+    } else {
+      // s is the plain fp32 sum: an infinite or NaN product leaves it infinite or NaN as the
+      // fp64 sum would be (c, formed from infinite differences, is NaN then)
+      if (!isfinite(s)) return s;
+      float hi, lo;
+      two_sum(s, c, hi, lo);  // hi + lo = s + c exactly
+      if (!isfinite(hi)) return hi;
+      const float r = round_pair(hi, lo, p1);
+      if (!isfinite(r)) return r;
+      float below, above;
+      half_gaps(r, p1, below, above);
+      // |exact - (s + c)| <= gamma_m a with m <= len + 2 log2(K) + 2 additions into c, inflated
+      // for the roundings of a and d
+      const float err = __fmul_rn(a, (float)(len + 16) * 1.2e-7f);
+      const float d = __fadd_rn(__fsub_rn(hi, r), lo);
+      const float slack = fabsf(d) * 1.2e-7f;
+      if (d + err + slack < above && -d + err + slack < below) return r;
+      return slow_round(p1, exact());
+    }
   }
+  __device__ static __noinline__ float slow_round(int p1, double v) { return round_d2f(v, p1); }
 };
 
 template <>
-struct RowAcc<double> {
+struct RowAcc<double, false> {
   double s = 0.0;
   __device__ __forceinline__ void add(double a, double x) { s = fma(a, x, s); }
   template <int K>
@@ -154,8 +181,8 @@ __device__ __forceinline__ double row_sum64(int rs, int re, V&& val, Cf&& col, c
 }
 
 // Finishes a row of the product from its accumulator (lane 0 of the row's lanes).
-template <typename VT, class V, class Cf>
-__device__ __forceinline__ void finish_row(const DevSys& S, int row, int rs, int re, const RowAcc<VT>& acc, int p1,
+template <typename VT, bool COMP, class V, class Cf>
+__device__ __forceinline__ void finish_row(const DevSys& S, int row, int rs, int re, const RowAcc<VT, COMP>& acc, int p1,
                                            int nu_fmt, DotAcc& nu, V&& val, Cf&& col, const VT* xin) {
   if constexpr (sizeof(VT) == 8) {
     finish_row_64(S, row, acc.s, nu_fmt, nu);
@@ -224,7 +251,7 @@ __device__ __forceinline__ void stage_wait(const StreamCtx& sc, int stage) {
 // Sub-warp vector CSR: K lanes per row, rows strided over the CTA, operands read from
 // global memory. The K lane accumulators are combined by an xor butterfly. With nu_fmt < 0
 // no nu partial is formed.
-template <typename VT, int K>
+template <typename VT, bool COMP, int K>
 __device__ void spmv_vec(const DevSys& S, const VT* __restrict__ vals, const VT* xin, Rows R, int p1,
                          int nu_fmt, DotAcc& nu) {
   constexpr int NG = kThreads / K;
@@ -235,11 +262,11 @@ __device__ void spmv_vec(const DevSys& S, const VT* __restrict__ vals, const VT*
   const int* __restrict__ ci = S.A.ci;
   for (int row = R.r0 + grp; row < R.r1; row += NG) {
     const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
-    RowAcc<VT> acc;
+    RowAcc<VT, COMP> acc;
     for (int e = e0 + lane; e < e1; e += K) acc.add(__ldg(vals + e), xin[__ldg(ci + e)]);
     acc.template reduce<K>(mask);
     if (lane == 0)
-      finish_row<VT>(S, row, e0, e1, acc, p1, nu_fmt, nu, [&](int e) { return __ldg(vals + e); },
+      finish_row<VT, COMP>(S, row, e0, e1, acc, p1, nu_fmt, nu, [&](int e) { return __ldg(vals + e); },
                      [&](int e) { return __ldg(ci + e); }, xin);
   }
 }
@@ -249,7 +276,7 @@ __device__ void spmv_vec(const DevSys& S, const VT* __restrict__ vals, const VT*
 // bulk copies (16-byte aligned by rounding the byte ranges out; the matrix arrays are
 // padded so the rounded ranges stay in bounds) while the previous tile is processed. K lanes
 // per row read the row from shared memory (strided, conflict-free) and gather x.
-template <typename VT, int K>
+template <typename VT, bool COMP, int K>
 __device__ void spmv_stream(const DevSys& S, const VT* __restrict__ vals, const VT* xin, Rows R, int p1,
                             int nu_fmt, DotAcc& nu, const StreamCtx& sc) {
   constexpr int TR = kThreads / K;
@@ -293,11 +320,11 @@ __device__ void spmv_stream(const DevSys& S, const VT* __restrict__ vals, const 
     const int row = ra + grp;
     if (row < rb) {
       const int rs = __ldg(rp + row), re = __ldg(rp + row + 1);
-      RowAcc<VT> acc;
+      RowAcc<VT, COMP> acc;
       for (int e = rs + lane; e < re; e += K) acc.add(sv[e], xin[scol[e]]);
       acc.template reduce<K>(mask);
       if (lane == 0)
-        finish_row<VT>(S, row, rs, re, acc, p1, nu_fmt, nu, [&](int e) { return sv[e]; }, [&](int e) { return scol[e]; },
+        finish_row<VT, COMP>(S, row, rs, re, acc, p1, nu_fmt, nu, [&](int e) { return sv[e]; }, [&](int e) { return scol[e]; },
                        xin);
     }
     __syncthreads();
@@ -309,24 +336,24 @@ __device__ void spmv_stream(const DevSys& S, const VT* __restrict__ vals, const 
   }
 }
 
-template <typename VT>
+template <typename VT, bool COMP>
 __device__ void spmv_dispatch_k(const DevSys& S, const VT* vals, const VT* xin, Rows R, int p1, int nu_fmt,
                                 DotAcc& nu, const StreamCtx* sc) {
   if (sc && S.A.sched[p1] == SCHED_STREAM) {
     switch (S.A.lanes[p1]) {
-      case 1: spmv_stream<VT, 1>(S, vals, xin, R, p1, nu_fmt, nu, *sc); return;
-      case 2: spmv_stream<VT, 2>(S, vals, xin, R, p1, nu_fmt, nu, *sc); return;
-      case 4: spmv_stream<VT, 4>(S, vals, xin, R, p1, nu_fmt, nu, *sc); return;
-      default: spmv_stream<VT, 8>(S, vals, xin, R, p1, nu_fmt, nu, *sc); return;
+      case 1: spmv_stream<VT, COMP, 1>(S, vals, xin, R, p1, nu_fmt, nu, *sc); return;
+      case 2: spmv_stream<VT, COMP, 2>(S, vals, xin, R, p1, nu_fmt, nu, *sc); return;
+      case 4: spmv_stream<VT, COMP, 4>(S, vals, xin, R, p1, nu_fmt, nu, *sc); return;
+      default: spmv_stream<VT, COMP, 8>(S, vals, xin, R, p1, nu_fmt, nu, *sc); return;
     }
   }
   switch (S.A.lanes[p1]) {
-    case 1: spmv_vec<VT, 1>(S, vals, xin, R, p1, nu_fmt, nu); break;
-    case 2: spmv_vec<VT, 2>(S, vals, xin, R, p1, nu_fmt, nu); break;
-    case 4: spmv_vec<VT, 4>(S, vals, xin, R, p1, nu_fmt, nu); break;
-    case 8: spmv_vec<VT, 8>(S, vals, xin, R, p1, nu_fmt, nu); break;
-    case 16: spmv_vec<VT, 16>(S, vals, xin, R, p1, nu_fmt, nu); break;
-    default: spmv_vec<VT, 32>(S, vals, xin, R, p1, nu_fmt, nu); break;
+    case 1: spmv_vec<VT, COMP, 1>(S, vals, xin, R, p1, nu_fmt, nu); break;
+    case 2: spmv_vec<VT, COMP, 2>(S, vals, xin, R, p1, nu_fmt, nu); break;
+    case 4: spmv_vec<VT, COMP, 4>(S, vals, xin, R, p1, nu_fmt, nu); break;
+    case 8: spmv_vec<VT, COMP, 8>(S, vals, xin, R, p1, nu_fmt, nu); break;
+    case 16: spmv_vec<VT, COMP, 16>(S, vals, xin, R, p1, nu_fmt, nu); break;
+    default: spmv_vec<VT, COMP, 32>(S, vals, xin, R, p1, nu_fmt, nu); break;
   }
 }
 
@@ -334,13 +361,15 @@ __device__ void spmv_dispatch_k(const DevSys& S, const VT* vals, const VT* xin, 
 // shared-memory ring of the stream schedule (nullptr when the launch has none).
 __device__ void spmv_rows(const DevSys& S, Rows R, int p1, int nu_fmt, DotAcc& nu, const StreamCtx* sc) {
   switch (p1) {
-    case F64: spmv_dispatch_k<double>(S, S.A.v64, S.p, R, p1, nu_fmt, nu, sc); break;
-    case F32: spmv_dispatch_k<float>(S, S.A.v32, (const float*)S.plow, R, p1, nu_fmt, nu, sc); break;
-    case TF32: spmv_dispatch_k<float>(S, S.A.vtf, (const float*)S.plow, R, p1, nu_fmt, nu, sc); break;
-    case F16: spmv_dispatch_k<__half>(S, S.A.v16, (const __half*)S.plow, R, p1, nu_fmt, nu, sc); break;
-    case BF16: spmv_dispatch_k<__nv_bfloat16>(S, S.A.vbf, (const __nv_bfloat16*)S.plow, R, p1, nu_fmt, nu, sc); break;
-    case F16R: spmv_dispatch_k<__half>(S, S.A.v16r, (const __half*)S.plow, R, p1, nu_fmt, nu, sc); break;
-    default: spmv_dispatch_k<__nv_bfloat16>(S, S.A.vbfr, (const __nv_bfloat16*)S.plow, R, p1, nu_fmt, nu, sc); break;
+    case F64: spmv_dispatch_k<double, false>(S, S.A.v64, S.p, R, p1, nu_fmt, nu, sc); break;
+    case F32: spmv_dispatch_k<float, false>(S, S.A.v32, (const float*)S.plow, R, p1, nu_fmt, nu, sc); break;
+    case TF32: spmv_dispatch_k<float, true>(S, S.A.vtf, (const float*)S.plow, R, p1, nu_fmt, nu, sc); break;
+    case F16: spmv_dispatch_k<__half, true>(S, S.A.v16, (const __half*)S.plow, R, p1, nu_fmt, nu, sc); break;
+    case BF16: spmv_dispatch_k<__nv_bfloat16, true>(S, S.A.vbf, (const __nv_bfloat16*)S.plow, R, p1, nu_fmt, nu, sc);
+      break;
+    case F16R: spmv_dispatch_k<__half, true>(S, S.A.v16r, (const __half*)S.plow, R, p1, nu_fmt, nu, sc); break;
+    default: spmv_dispatch_k<__nv_bfloat16, true>(S, S.A.vbfr, (const __nv_bfloat16*)S.plow, R, p1, nu_fmt, nu, sc);
+      break;
   }
 }
 
