@@ -849,6 +849,109 @@ __device__ __forceinline__ void stamp_c(const DevSys& S, SysState* st) {
 
 constexpr int kUnroll = 4;  // rows per thread in flight in the vector phases
 
+// Storage types of q (phase B) and of p's low copy (phase C), one instantiation each, so that
+// the loads of a thread's kUnroll rows are issued together before any use.
+template <typename T>
+__device__ __forceinline__ double stored_as_double(T v) {
+  if constexpr (sizeof(T) == 8) return v;
+  else return f2d(to_acc(v));
+}
+template <typename T>
+__device__ __forceinline__ T to_storage(float v);
+template <>
+__device__ __forceinline__ float to_storage<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __half to_storage<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_storage<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// Phase B rows: r -= alpha q (fp64), ||r||^2 (fp64) and, unless sigma is ||r||^2 itself,
+// the sigma terms. QT: storage of q; SCALED: q carries the row scale 2^e_i.
+template <typename QT, bool SCALED>
+__device__ __forceinline__ void phase_b_rows(const DevSys& S, Rows R, double alpha, int p2, int p4, bool sig_rr,
+                                             double& rr, DotAcc& sg) {
+  const QT* __restrict__ q = (const QT*)S.q;
+  for (int i0 = R.r0 + threadIdx.x; i0 < R.r1; i0 += kUnroll * kThreads) {
+    QT qv[kUnroll];
+    double ro[kUnroll];
+    short ev[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int i = i0 + u * kThreads;
+      if (i < R.r1) {
+        qv[u] = q[i];
+        ro[u] = S.r[i];
+        if constexpr (SCALED) ev[u] = __ldg(S.A.rexp + i);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int i = i0 + u * kThreads;
+      if (i < R.r1) {
+        double qd = stored_as_double(qv[u]);
+        if constexpr (SCALED) qd = scale2(qd, ev[u]);
+        const double ri = fma(-alpha, qd, ro[u]);
+        S.r[i] = ri;
+        rr = fma(ri, ri, rr);
+        if (!sig_rr) sigma_term(ri, p2, p4, sg);
+      }
+    }
+  }
+}
+
+// Phase C rows: x += alpha p; p = z + beta p (fp64) with z = fl_p2(r); p's copy in the next
+// product's format p1n, stored as PT (PT = double: no copy, the next product is fp64).
+template <typename PT>
+__device__ __forceinline__ void phase_c_rows(const DevSys& S, Rows R, double alpha, double beta, int p2, int p1n) {
+  const bool zlow = p2 != F64;
+  for (int i0 = R.r0 + threadIdx.x; i0 < R.r1; i0 += kUnroll * kThreads) {
+    double pv[kUnroll], xv[kUnroll], rv[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int i = i0 + u * kThreads;
+      if (i < R.r1) {
+        pv[u] = S.p[i];
+        xv[u] = S.x[i];
+        rv[u] = S.r[i];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int i = i0 + u * kThreads;
+      if (i < R.r1) {
+        S.x[i] = fma(alpha, pv[u], xv[u]);
+        const double z = zlow ? f2d(round_d2f(rv[u], p2)) : rv[u];
+        const double pn = fma(beta, pv[u], z);
+        S.p[i] = pn;
+        if constexpr (sizeof(PT) != 8) ((PT*)S.plow)[i] = to_storage<PT>(round_d2f(pn, p1n));
+      }
+    }
+  }
+}
+
+// Row phases B and C, out of line (one register allocation each, as for the product).
+__device__ __noinline__ void phase_b(const DevSys& S, Rows R, double alpha, int p1, int p2, int p4, bool sig_rr,
+                                     double& rr, DotAcc& sg) {
+  switch (p1) {
+    case F64: phase_b_rows<double, false>(S, R, alpha, p2, p4, sig_rr, rr, sg); break;
+    case F32:
+    case TF32: phase_b_rows<float, false>(S, R, alpha, p2, p4, sig_rr, rr, sg); break;
+    case F16: phase_b_rows<__half, false>(S, R, alpha, p2, p4, sig_rr, rr, sg); break;
+    case BF16: phase_b_rows<__nv_bfloat16, false>(S, R, alpha, p2, p4, sig_rr, rr, sg); break;
+    case F16R: phase_b_rows<__half, true>(S, R, alpha, p2, p4, sig_rr, rr, sg); break;
+    default: phase_b_rows<__nv_bfloat16, true>(S, R, alpha, p2, p4, sig_rr, rr, sg); break;
+  }
+}
+
+__device__ __noinline__ void phase_c(const DevSys& S, Rows R, double alpha, double beta, int p2, int p1n) {
+  switch (store_of(p1n)) {
+    case ST_DOUBLE: phase_c_rows<double>(S, R, alpha, beta, p2, p1n); break;
+    case ST_FLOAT: phase_c_rows<float>(S, R, alpha, beta, p2, p1n); break;
+    case ST_HALF: phase_c_rows<__half>(S, R, alpha, beta, p2, p1n); break;
+    default: phase_c_rows<__nv_bfloat16>(S, R, alpha, beta, p2, p1n); break;
+  }
+}
+
 // fp64 restart after a breakdown: r = b - A x and p = r in fp64, then step_restart.
 __device__ bool restart64(const Launch& L, const TeamCtx& T, const DevSys& S, SysState* st, Rows R, Smem& sm) {
   double rr = 0.0;
@@ -859,7 +962,7 @@ __device__ bool restart64(const Launch& L, const TeamCtx& T, const DevSys& S, Sy
   return team_step(L, T, st, sm, [&] { step_restart(L, S, st, team_sum(L, T, 0, sm.red), sm); });
 }
 
-__device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& sm, const StreamCtx* sc) {
+__device__ __forceinline__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& sm, const StreamCtx* sc) {
   const DevSys& S = L.sys[sid];
   SysState* st = L.st + sid;
   const OptView& o = L.opt;
@@ -928,27 +1031,7 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
         const bool sig_rr = (p2 == F64 && p4 == F64);
         double rr = 0.0;
         DotAcc sg{0.0, 0.f, 0.f};
-        for (int i0 = R.r0 + threadIdx.x; i0 < R.r1; i0 += kUnroll * kThreads) {
-          double qv[kUnroll], ro[kUnroll];
-#pragma unroll
-          for (int u = 0; u < kUnroll; ++u) {
-            const int i = i0 + u * kThreads;
-            if (i < R.r1) {
-              qv[u] = load_q(S, i, p1);
-              ro[u] = S.r[i];
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < kUnroll; ++u) {
-            const int i = i0 + u * kThreads;
-            if (i < R.r1) {
-              const double ri = fma(-alpha, qv[u], ro[u]);
-              S.r[i] = ri;
-              rr = fma(ri, ri, rr);
-              if (!sig_rr) sigma_term(ri, p2, p4, sg);
-            }
-          }
-        }
+        phase_b(S, R, alpha, p1, p2, p4, sig_rr, rr, sg);
         rr = cta_sum(rr, sm.red);
         const double sp = sig_rr ? rr : cta_dot(sg, sm.red);
         write_partial(L, 0, rr);
@@ -966,28 +1049,7 @@ __device__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& s
         const double alpha = sm.bc.alpha, beta = sm.bc.beta;
         const int p1n = sm.bc.fmt[0];  // next action's product format
         const int p2 = sm.bc.zfmt;     // z = fl_p2(r) of the finished iteration
-        for (int i0 = R.r0 + threadIdx.x; i0 < R.r1; i0 += kUnroll * kThreads) {
-          double pv[kUnroll], xv[kUnroll], rv[kUnroll];
-#pragma unroll
-          for (int u = 0; u < kUnroll; ++u) {
-            const int i = i0 + u * kThreads;
-            if (i < R.r1) {
-              pv[u] = S.p[i];
-              xv[u] = S.x[i];
-              rv[u] = S.r[i];
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < kUnroll; ++u) {
-            const int i = i0 + u * kThreads;
-            if (i < R.r1) {
-              S.x[i] = fma(alpha, pv[u], xv[u]);
-              const double pn = fma(beta, pv[u], z_of(rv[u], p2));
-              S.p[i] = pn;
-              if (p1n != F64) store_low(S.plow, i, pn, p1n);
-            }
-          }
-        }
+        phase_c(S, R, alpha, beta, p2, p1n);
         if (!team_step(L, T, st, sm, [&] { stamp_c(S, st); })) return false;
         if (sm.bc.k >= S.max_iter) break;
         continue;
