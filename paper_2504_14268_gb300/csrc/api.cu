@@ -715,12 +715,15 @@ mpcg_status mpcg_matrix_set_schedule(mpcg_matrix_t A, int32_t fmt, int32_t sched
   if (!valid_fmt(fmt) || lanes < 1 || lanes > 32 || (lanes & (lanes - 1)))
     return fail(A->ctx, MPCG_ERR_INVALID_ARG, "unsupported schedule (fmt %d, sched %d, lanes %d)", fmt, sched, lanes);
   if (sched == SCHED_STREAM) {
+    if (lanes > 4) return fail(A->ctx, MPCG_ERR_INVALID_ARG, "the stream schedule takes 1, 2 or 4 lanes per row");
     const int vreg = stream_vreg(A, fmt, lanes);
     if (vreg < 0)
       return fail(A->ctx, MPCG_ERR_INVALID_ARG, "stream schedule with %d lanes does not fit a %d-byte stage", lanes,
                   kStageBytes);
     A->dm.tile_rows[fmt] = kThreads / lanes;
     A->dm.tile_bytes[fmt] = vreg;
+  } else if (sched == SCHED_VLOAD) {
+    if (lanes != 1) return fail(A->ctx, MPCG_ERR_INVALID_ARG, "the vector-load schedule takes one lane per row");
   } else if (sched != SCHED_VECTOR) {
     return fail(A->ctx, MPCG_ERR_INVALID_ARG, "unknown schedule %d", sched);
   }
@@ -793,16 +796,25 @@ mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, 
   // Configuration P: every format on the sub-warp vector schedule, no stream ring.
   int bestP[NFMT];
   double sumP = 0;
+  int schedP[NFMT];
   for (int f = 0; f < NFMT; ++f) A->dm.sched[f] = SCHED_VECTOR;
   for (int f = 0; f < NFMT; ++f) {
     double best = 1e30;
     bestP[f] = A->dm.lanes[f];
+    schedP[f] = SCHED_VECTOR;
     for (int lanes = 1; lanes <= 32; lanes *= 2) {
       double ms = 0;
       mpcg_status st = time_it(f, SCHED_VECTOR, lanes, ms);
       if (st != MPCG_OK) return st;
       if (ms < best) { best = ms; bestP[f] = lanes; }
     }
+    {
+      double ms = 0;
+      mpcg_status st = time_it(f, SCHED_VLOAD, 1, ms);
+      if (st != MPCG_OK) return st;
+      if (ms < best) { best = ms; bestP[f] = 1; schedP[f] = SCHED_VLOAD; }
+    }
+    A->dm.sched[f] = schedP[f];
     A->dm.lanes[f] = bestP[f];
     sumP += best;
   }
@@ -810,18 +822,19 @@ mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, 
   // stream schedule and the vector schedule measured in that shape.
   bool any = false;
   for (int f = 0; f < NFMT && !any; ++f)
-    for (int lanes = 1; lanes <= 8; lanes *= 2) any = any || stream_vreg(A, f, lanes) >= 0;
+    for (int lanes = 1; lanes <= 4; lanes *= 2) any = any || stream_vreg(A, f, lanes) >= 0;
   if (any) {
     int schedS[NFMT], lanesS[NFMT];
     double sumS = 0;
     A->force_stream_shape = true;
     for (int f = 0; f < NFMT; ++f) {
       double best = 1e30;
-      schedS[f] = SCHED_VECTOR;
+      schedS[f] = schedP[f];
       lanesS[f] = bestP[f];
       for (int lanes = 1; lanes <= 32; lanes *= 2) {
-        for (int sched = 0; sched < 2; ++sched) {
-          if (sched == SCHED_STREAM && stream_vreg(A, f, lanes) < 0) continue;
+        for (int sched = 0; sched < 3; ++sched) {
+          if (sched == SCHED_STREAM && (lanes > 4 || stream_vreg(A, f, lanes) < 0)) continue;
+          if (sched == SCHED_VLOAD && lanes != 1) continue;
           double ms = 0;
           mpcg_status st = time_it(f, sched, lanes, ms);
           if (st != MPCG_OK) {
@@ -842,7 +855,7 @@ mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, 
       return MPCG_OK;
     }
   }
-  for (int f = 0; f < NFMT; ++f) mpcg_matrix_set_schedule(A, f, SCHED_VECTOR, bestP[f]);
+  for (int f = 0; f < NFMT; ++f) mpcg_matrix_set_schedule(A, f, schedP[f], bestP[f]);
   return MPCG_OK;
 }
 

@@ -48,14 +48,15 @@ __device__ __forceinline__ double pow2(int e) {
 
 // Row finished with q_i = qf already rounded onto p1: stored in p1's storage; then the row's
 // nu term fl_p3(p_i) fl_p3(q_i) (q_i includes the row scale 2^e_i of the row-scaled formats).
-__device__ __forceinline__ void finish_row_low(const DevSys& S, int row, float qf, int p1, int nu_fmt, DotAcc& nu) {
+// `pi` = p_i in fp64 (read by the caller, ahead of the row when it can).
+__device__ __forceinline__ void finish_row_low(const DevSys& S, int row, float qf, int p1, int nu_fmt, double pi,
+                                               DotAcc& nu) {
   switch (store_of(p1)) {
     case ST_HALF: ((__half*)S.q)[row] = __float2half_rn(qf); break;
     case ST_BF16: ((__nv_bfloat16*)S.q)[row] = __float2bfloat16_rn(qf); break;
     default: ((float*)S.q)[row] = qf; break;
   }
   if (nu_fmt < 0) return;
-  const double pi = S.p[row];
   const bool scaled = row_scaled(p1);
   if (nu_fmt == F64) {
     double qd = f2d(qf);
@@ -70,10 +71,10 @@ __device__ __forceinline__ void finish_row_low(const DevSys& S, int row, float q
 }
 
 // Row finished with an fp64 sum (fp64 product).
-__device__ __forceinline__ void finish_row_64(const DevSys& S, int row, double tot, int nu_fmt, DotAcc& nu) {
+__device__ __forceinline__ void finish_row_64(const DevSys& S, int row, double tot, int nu_fmt, double pi,
+                                              DotAcc& nu) {
   ((double*)S.q)[row] = tot;
   if (nu_fmt < 0) return;
-  const double pi = S.p[row];
   if (nu_fmt == F64) nu.d = fma(pi, tot, nu.d);
   else dot_low(nu, round_d2f(pi, nu_fmt), round_d2f(tot, nu_fmt), nu_fmt);
 }
@@ -183,12 +184,12 @@ __device__ __forceinline__ double row_sum64(int rs, int re, V&& val, Cf&& col, c
 // Finishes a row of the product from its accumulator (lane 0 of the row's lanes).
 template <typename VT, bool COMP, class V, class Cf>
 __device__ __forceinline__ void finish_row(const DevSys& S, int row, int rs, int re, const RowAcc<VT, COMP>& acc, int p1,
-                                           int nu_fmt, DotAcc& nu, V&& val, Cf&& col, const VT* xin) {
+                                           int nu_fmt, double pi, DotAcc& nu, V&& val, Cf&& col, const VT* xin) {
   if constexpr (sizeof(VT) == 8) {
-    finish_row_64(S, row, acc.s, nu_fmt, nu);
+    finish_row_64(S, row, acc.s, nu_fmt, pi, nu);
   } else {
     const float qf = acc.rounded(p1, re - rs, [&] { return row_sum64<VT>(rs, re, val, col, xin); });
-    finish_row_low(S, row, qf, p1, nu_fmt, nu);
+    finish_row_low(S, row, qf, p1, nu_fmt, pi, nu);
   }
 }
 
@@ -266,8 +267,67 @@ __device__ void spmv_vec(const DevSys& S, const VT* __restrict__ vals, const VT*
     for (int e = e0 + lane; e < e1; e += K) acc.add(__ldg(vals + e), xin[__ldg(ci + e)]);
     acc.template reduce<K>(mask);
     if (lane == 0)
-      finish_row<VT, COMP>(S, row, e0, e1, acc, p1, nu_fmt, nu, [&](int e) { return __ldg(vals + e); },
-                     [&](int e) { return __ldg(ci + e); }, xin);
+      finish_row<VT, COMP>(S, row, e0, e1, acc, p1, nu_fmt, nu_fmt >= 0 ? S.p[row] : 0.0, nu,
+                           [&](int e) { return __ldg(vals + e); }, [&](int e) { return __ldg(ci + e); }, xin);
+  }
+}
+
+// One thread per row with 16-byte loads: the row's column indices and values are read in
+// aligned groups of G elements (G = 8 for 16-bit values, 4 otherwise; group starts rounded
+// down to a multiple of G, the arrays are padded so the last group stays in bounds), so a
+// thread issues one load per 4 columns and per 16 bytes of values instead of one per
+// element; elements of a group outside the row are skipped.
+template <typename VT, bool COMP>
+__device__ void spmv_vload(const DevSys& S, const VT* __restrict__ vals, const VT* xin, Rows R, int p1, int nu_fmt,
+                           DotAcc& nu) {
+  constexpr int G = sizeof(VT) == 2 ? 8 : 4;
+  constexpr int NV = G * (int)sizeof(VT) / 16;  // 16-byte value loads per group
+  const int* __restrict__ rp = S.A.rp;
+  const int* __restrict__ ci = S.A.ci;
+  // the row pointers and p_i of a thread's next row are loaded one row ahead
+  int row = R.r0 + threadIdx.x;
+  int ne0 = 0, ne1 = 0;
+  double npi = 0.0;
+  if (row < R.r1) {
+    ne0 = __ldg(rp + row);
+    ne1 = __ldg(rp + row + 1);
+    if (nu_fmt >= 0) npi = S.p[row];
+  }
+  for (; row < R.r1; row += kThreads) {
+    const int e0 = ne0, e1 = ne1;
+    const double pi = npi;
+    if (row + kThreads < R.r1) {
+      ne0 = __ldg(rp + row + kThreads);
+      ne1 = __ldg(rp + row + kThreads + 1);
+      if (nu_fmt >= 0) npi = S.p[row + kThreads];
+    }
+    RowAcc<VT, COMP> acc;
+    for (int g = e0 & ~(G - 1); g < e1; g += G) {
+      int c[G];
+      VT v[G];
+#pragma unroll
+      for (int h = 0; h < G / 4; ++h) {
+        const int4 cc = __ldg(reinterpret_cast<const int4*>(ci + g) + h);
+        c[4 * h] = cc.x;
+        c[4 * h + 1] = cc.y;
+        c[4 * h + 2] = cc.z;
+        c[4 * h + 3] = cc.w;
+      }
+#pragma unroll
+      for (int h = 0; h < NV; ++h) {
+        const int4 vv = __ldg(reinterpret_cast<const int4*>(vals + g) + h);
+        memcpy(v + h * (16 / sizeof(VT)), &vv, 16);
+      }
+      VT xv[G];
+#pragma unroll
+      for (int j = 0; j < G; ++j)
+        if (g + j >= e0 && g + j < e1) xv[j] = xin[c[j]];
+#pragma unroll
+      for (int j = 0; j < G; ++j)
+        if (g + j >= e0 && g + j < e1) acc.add(v[j], xv[j]);
+    }
+    finish_row<VT, COMP>(S, row, e0, e1, acc, p1, nu_fmt, pi, nu, [&](int e) { return __ldg(vals + e); },
+                         [&](int e) { return __ldg(ci + e); }, xin);
   }
 }
 
@@ -324,8 +384,8 @@ __device__ void spmv_stream(const DevSys& S, const VT* __restrict__ vals, const 
       for (int e = rs + lane; e < re; e += K) acc.add(sv[e], xin[scol[e]]);
       acc.template reduce<K>(mask);
       if (lane == 0)
-        finish_row<VT, COMP>(S, row, rs, re, acc, p1, nu_fmt, nu, [&](int e) { return sv[e]; }, [&](int e) { return scol[e]; },
-                       xin);
+        finish_row<VT, COMP>(S, row, rs, re, acc, p1, nu_fmt, nu_fmt >= 0 ? S.p[row] : 0.0, nu,
+                             [&](int e) { return sv[e]; }, [&](int e) { return scol[e]; }, xin);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -339,12 +399,15 @@ __device__ void spmv_stream(const DevSys& S, const VT* __restrict__ vals, const 
 template <typename VT, bool COMP>
 __device__ void spmv_dispatch_k(const DevSys& S, const VT* vals, const VT* xin, Rows R, int p1, int nu_fmt,
                                 DotAcc& nu, const StreamCtx* sc) {
+  if (S.A.sched[p1] == SCHED_VLOAD) {
+    spmv_vload<VT, COMP>(S, vals, xin, R, p1, nu_fmt, nu);
+    return;
+  }
   if (sc && S.A.sched[p1] == SCHED_STREAM) {
     switch (S.A.lanes[p1]) {
       case 1: spmv_stream<VT, COMP, 1>(S, vals, xin, R, p1, nu_fmt, nu, *sc); return;
       case 2: spmv_stream<VT, COMP, 2>(S, vals, xin, R, p1, nu_fmt, nu, *sc); return;
-      case 4: spmv_stream<VT, COMP, 4>(S, vals, xin, R, p1, nu_fmt, nu, *sc); return;
-      default: spmv_stream<VT, COMP, 8>(S, vals, xin, R, p1, nu_fmt, nu, *sc); return;
+      default: spmv_stream<VT, COMP, 4>(S, vals, xin, R, p1, nu_fmt, nu, *sc); return;
     }
   }
   switch (S.A.lanes[p1]) {
