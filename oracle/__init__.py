@@ -125,6 +125,7 @@ def lib():
             L.orc_mlp_forward.argtypes = [vp, i, i, vp, vp, vp, vp]
             L.orc_mlp_loss_grad.restype = d
             L.orc_mlp_loss_grad.argtypes = [vp, i, i, i, vp, vp, vp, vp]
+            L.orc_mlp_targets.argtypes = [vp, i, i, i, vp, vp, vp, d, vp, vp]
             L.orc_adam.argtypes = [vp, vp, vp, vp, i64, i, d, d, d, d]
             L.orc_static_features.argtypes = [i, vp, vp, vp, vp]
             _lib = L
@@ -414,6 +415,19 @@ def mlp_loss_grad(w, H: int, nprec: int, feats, acts, y):
     B = feats.shape[0]
     loss = lib().orc_mlp_loss_grad(_p(w), H, nprec, B, _p(feats), _p(acts), _p(y), _p(g))
     return loss, g
+
+
+def mlp_targets(wt, H: int, nprec: int, feats_next, rew, done, gamma: float, op_mask=(0, 0, 0, 0)):
+    """Fitted-Q targets y[B][4] = r + gamma (1 - done) max over allowed p of Q_target(f_next)[j, p]."""
+    wt = np.ascontiguousarray(wt, dtype=np.float64)
+    fn = np.ascontiguousarray(feats_next, dtype=np.float64)
+    rew = np.ascontiguousarray(rew, dtype=np.float64)
+    done = np.ascontiguousarray(done, dtype=np.int32)
+    mask = np.ascontiguousarray(op_mask, dtype=np.int32)
+    B = fn.shape[0]
+    y = np.zeros((B, 4))
+    lib().orc_mlp_targets(_p(wt), H, nprec, B, _p(fn), _p(rew), _p(done), float(gamma), _p(mask), _p(y))
+    return y
 
 
 def adam(w, m, v, g, t: int, lr: float = 1e-3, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):

@@ -376,6 +376,30 @@ double orc_mlp_loss_grad(const double* w, int H, int nprec, int B, const double*
   return loss;
 }
 
+/* Fitted-Q targets (the regression targets of the MLP Q-function): for each sample b and
+ * operation j, y_bj = r_b + gamma (1 - done_b) max over the entries p allowed by op_mask[j]
+ * (bit p; 0 = all) of Q_target(f_next_b)[j, p], with Q_target the network wt. This is the
+ * one-step Bellman backup of the Q-learning update of Section 4.1 with the table replaced
+ * by a function of the features. */
+void orc_mlp_targets(const double* wt, int H, int nprec, int B, const double* feats_next, const double* rew,
+                     const int32_t* done, double gamma, const int32_t* op_mask, double* y) {
+  int nout = 4 * nprec;
+  double* h1 = malloc(sizeof(double) * H);
+  double* h2 = malloc(sizeof(double) * H);
+  double* out = malloc(sizeof(double) * nout);
+  for (int b = 0; b < B; ++b) {
+    orc_mlp_forward(wt, H, nout, feats_next + (int64_t)b * ORC_NFEAT, h1, h2, out);
+    for (int j = 0; j < 4; ++j) {
+      unsigned mask = op_mask && op_mask[j] ? (unsigned)op_mask[j] : ~0u;
+      double m = -INFINITY;
+      for (int p = 0; p < nprec; ++p)
+        if ((mask >> p) & 1u) m = out[j * nprec + p] > m ? out[j * nprec + p] : m;
+      y[(int64_t)b * 4 + j] = rew[b] + (done[b] ? 0.0 : gamma * m);
+    }
+  }
+  free(h1); free(h2); free(out);
+}
+
 /* Adam (Kingma & Ba, ICLR 2015), step t >= 1:
  *   m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2
  *   w -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps) */

@@ -101,3 +101,45 @@ def test_static_features_poisson():
     A, b, _ = I.cfg_poisson32()
     f = O.static_features(A)
     assert f == pytest.approx([np.log10(1024) / 8, 4.875 / 64, 0.0, np.log10(2.0) / 16, 0.0])
+
+
+def test_fitted_q_targets_closed_form_and_masks():
+    """With W1 = W2 = W3 = 0 the network's output is its last bias b3 whatever the features,
+    so y_bj = r_b + gamma (1 - done_b) max over the allowed p of b3[j nprec + p]; a terminal
+    sample keeps its reward alone."""
+    H, nprec = 8, 5
+    nout = 4 * nprec
+    w = np.zeros(O.mlp_nparams(H, nout))
+    rng = np.random.default_rng(3)
+    b3 = rng.normal(size=nout)
+    w[-nout:] = b3
+    B = 6
+    fn = rng.normal(size=(B, 16))
+    rew = rng.normal(size=B)
+    done = np.array([0, 1, 0, 0, 1, 0], dtype=np.int32)
+    masks = (0, 0b11000, 0b00110, 0b10000)
+    y = O.mlp_targets(w, H, nprec, fn, rew, done, 0.9, masks)
+    for b in range(B):
+        for j in range(4):
+            allowed = [p for p in range(nprec) if masks[j] == 0 or (masks[j] >> p) & 1]
+            m = max(b3[j * nprec + p] for p in allowed)
+            assert y[b, j] == pytest.approx(rew[b] + (0.0 if done[b] else 0.9 * m), abs=1e-15)
+
+
+def test_fitted_q_targets_match_forward_pass():
+    """General weights: each target equals the reward plus gamma times the largest allowed
+    output of the forward pass on f_next (forward pass pinned separately)."""
+    H, nprec = 6, 3
+    nout = 4 * nprec
+    rng = np.random.default_rng(4)
+    w = rng.normal(size=O.mlp_nparams(H, nout)) * 0.5
+    fn = rng.normal(size=(3, 16))
+    rew = np.array([1.0, -2.0, 0.5])
+    done = np.array([0, 0, 1], dtype=np.int32)
+    y = O.mlp_targets(w, H, nprec, fn, rew, done, 0.5, (0b011, 0, 0b100, 0b101))
+    out0, _, _ = O.mlp_forward(w, H, nout, fn[0])
+    assert y[0, 0] == pytest.approx(1.0 + 0.5 * max(out0[0], out0[1]))
+    assert y[0, 1] == pytest.approx(1.0 + 0.5 * max(out0[3:6]))
+    assert y[0, 2] == pytest.approx(1.0 + 0.5 * out0[8])
+    assert y[0, 3] == pytest.approx(1.0 + 0.5 * max(out0[9], out0[11]))
+    assert np.all(y[2] == 0.5)
