@@ -320,12 +320,22 @@ mpcg_status mpcg_mlp_loss_grad(mpcg_ctx_t ctx, const float* params, int64_t B, c
 
 /* Fitted-Q training of an MLP policy in place: `steps` Adam steps (lr, betas 0.9 / 0.999,
  * eps 1e-8) on minibatches of `batch` transitions drawn from data[count] (host array) with
- * Philox4x64-10 (key seed), targets r + gamma (1 - done) max_p Q_target(f_next)[j, p] from a
- * target network copied from the trained one every target_sync steps. loss_out (optional,
- * host [steps]) receives each step's loss. */
+ * Philox4x64-10 (key seed), targets r + gamma (1 - done) max_p Q_target(f_next)[j, p] (p over
+ * the entries the options' op_mask[j] allows, as mpcg_mlp_targets) from a target network
+ * copied from the trained one every target_sync steps. loss_out (optional, host [steps])
+ * receives each step's loss. */
 mpcg_status mpcg_mlp_train(mpcg_ctx_t ctx, mpcg_policy_t mlp, const mpcg_transition* data, int64_t count,
                            int32_t steps, int32_t batch, float lr, int32_t target_sync, uint64_t seed,
                            float* loss_out, void* stream);
+
+/* The fitted-Q regression targets of the MLP Q-function (the one-step backup of the
+ * Section 4.1 update with the table replaced by the network): y[b][j] = rew[b] +
+ * gamma (1 - done[b]) max over the entries p of precs allowed by the options' op_mask[j] of
+ * Q_target(feats_next[b])[j, p], Q_target the network with parameters target_params (host,
+ * mpcg_mlp_nparams floats). Host arrays feats_next[B][16], rew[B], done[B], y[B][4]. Errors:
+ * INVALID_ARG (NULL, B < 1), CUDA, OOM. */
+mpcg_status mpcg_mlp_targets(mpcg_ctx_t ctx, const float* target_params, int64_t B, const float* feats_next,
+                             const float* rew, const int32_t* done, float* y, void* stream);
 
 #ifdef __cplusplus
 }

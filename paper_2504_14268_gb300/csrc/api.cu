@@ -1306,6 +1306,14 @@ mpcg_status mpcg_collect(mpcg_ctx_t ctx, int32_t nsys, const mpcg_matrix_t* A, c
   return MPCG_OK;
 }
 
+// The options' per-operation masks with 0 meaning every entry of precs.
+static OpMask op_masks(const mpcg_options& o) {
+  OpMask m;
+  const unsigned all = (1u << o.nprec) - 1u;
+  for (int j = 0; j < 4; ++j) m.m[j] = o.op_mask[j] ? ((unsigned)o.op_mask[j] & all) : all;
+  return m;
+}
+
 mpcg_status mpcg_mlp_loss_grad(mpcg_ctx_t ctx, const float* params, int64_t B, const float* feats, const int32_t* acts,
                                const float* y, float* grad, double* loss, void* stream) {
   if (!ctx || !params || B < 1 || !feats || !acts || !y || !grad) return fail(ctx, MPCG_ERR_INVALID_ARG, "NULL argument");
@@ -1331,8 +1339,8 @@ mpcg_status mpcg_mlp_loss_grad(mpcg_ctx_t ctx, const float* params, int64_t B, c
   CK(ctx, cudaMemcpyAsync(da.p, acts, sizeof(int) * 4 * B, cudaMemcpyHostToDevice, s));
   CK(ctx, cudaMemcpyAsync(dy.p, y, sizeof(float) * 4 * B, cudaMemcpyHostToDevice, s));
   CK(ctx, launch_mlp_grad(dw.as<float>(), nullptr, o.mlp_hidden, o.nprec, df.as<float>(), nullptr, da.as<int>(), nullptr,
-                          nullptr, dy.as<float>(), nullptr, (int)B, chunk, (float)o.gamma, dpart.as<float>(),
-                          dl.as<double>(), s));
+                          nullptr, dy.as<float>(), nullptr, (int)B, chunk, (float)o.gamma, op_masks(o),
+                          dpart.as<float>(), dl.as<double>(), s));
   CK(ctx, launch_mlp_reduce_adam(dpart.as<float>(), nparts, np, dg.as<float>(), nullptr, nullptr, nullptr, 0, 0.f,
                                  dl.as<double>(), dloss.as<double>(), s));
   CK(ctx, cudaMemcpyAsync(grad, dg.p, sizeof(float) * np, cudaMemcpyDeviceToHost, s));
@@ -1393,7 +1401,7 @@ mpcg_status mpcg_mlp_train(mpcg_ctx_t ctx, mpcg_policy_t P, const mpcg_transitio
     CK(ctx, launch_mlp_sample(didx.as<long long>(), batch, count, seed, (unsigned long long)t, s));
     CK(ctx, launch_mlp_grad(P->mlp.as<float>(), dwt.as<float>(), o.mlp_hidden, o.nprec, dF.as<float>(), dFn.as<float>(),
                             dA.as<int>(), dR.as<float>(), dD.as<int>(), nullptr, didx.as<long long>(), batch, chunk,
-                            (float)o.gamma, dpart.as<float>(), dl.as<double>(), s));
+                            (float)o.gamma, op_masks(o), dpart.as<float>(), dl.as<double>(), s));
     CK(ctx, launch_mlp_reduce_adam(dpart.as<float>(), nparts, np, nullptr, P->mlp.as<float>(), dm.as<float>(),
                                    dv.as<float>(), t, lr, dl.as<double>(), dloss.as<double>() + (t - 1), s));
     if (t % target_sync == 0)
@@ -1404,6 +1412,32 @@ mpcg_status mpcg_mlp_train(mpcg_ctx_t ctx, mpcg_policy_t P, const mpcg_transitio
   CK(ctx, cudaStreamSynchronize(s));
   if (loss_out)
     for (int t = 0; t < steps; ++t) loss_out[t] = (float)hl[t];
+  return MPCG_OK;
+}
+
+mpcg_status mpcg_mlp_targets(mpcg_ctx_t ctx, const float* target_params, int64_t B, const float* feats_next,
+                             const float* rew, const int32_t* done, float* y, void* stream) {
+  if (!ctx || !target_params || B < 1 || !feats_next || !rew || !done || !y)
+    return fail(ctx, MPCG_ERR_INVALID_ARG, "NULL argument or empty batch");
+  if (B > (int64_t)1 << 30) return fail(ctx, MPCG_ERR_INVALID_ARG, "batch too large");
+  const mpcg_options& o = ctx->opt;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long np = mlp_nparams_dev(o.mlp_hidden, o.nprec);
+  DevBuf dw, dfn, dr, dd, dy;
+  CK(ctx, dw.ensure(sizeof(float) * np));
+  CK(ctx, dfn.ensure(sizeof(float) * kNFeat * B));
+  CK(ctx, dr.ensure(sizeof(float) * B));
+  CK(ctx, dd.ensure(sizeof(int) * B));
+  CK(ctx, dy.ensure(sizeof(float) * 4 * B));
+  CK(ctx, cudaMemcpyAsync(dw.p, target_params, sizeof(float) * np, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(dfn.p, feats_next, sizeof(float) * kNFeat * B, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(dr.p, rew, sizeof(float) * B, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(dd.p, done, sizeof(int) * B, cudaMemcpyHostToDevice, s));
+  CK(ctx, launch_mlp_targets(dw.as<float>(), o.mlp_hidden, o.nprec, dfn.as<float>(), dr.as<float>(), dd.as<int>(),
+                             (int)B, (float)o.gamma, op_masks(o), dy.as<float>(), s));
+  CK(ctx, cudaMemcpyAsync(y, dy.p, sizeof(float) * 4 * B, cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
   return MPCG_OK;
 }
 

@@ -164,10 +164,16 @@ cudaError_t launch_convert(const DevMatrix& A, float* v32, float* vtf, __half* v
 long long mlp_nparams_dev(int H, int nprec);
 size_t mlp_grad_smem(int H, int nprec);
 cudaError_t mlp_set_smem_limit(size_t bytes);
+// Allowed precision entries per operation (bit p = entry p of precs), for the MLP targets.
+struct OpMask {
+  unsigned m[4];
+};
 cudaError_t launch_mlp_grad(const float* w, const float* wt, int H, int nprec, const float* feats,
                             const float* feats_next, const int* acts, const float* rew, const int* done, const float* y,
-                            const long long* idx, int B, int chunk, float gamma, float* part, double* lpart,
-                            cudaStream_t s);
+                            const long long* idx, int B, int chunk, float gamma, OpMask mask, float* part,
+                            double* lpart, cudaStream_t s);
+cudaError_t launch_mlp_targets(const float* wt, int H, int nprec, const float* feats_next, const float* rew,
+                               const int* done, int B, float gamma, OpMask mask, float* y, cudaStream_t s);
 cudaError_t launch_mlp_reduce_adam(const float* part, int nparts, long long np, float* grad, float* w, float* m,
                                    float* v, int t, float lr, const double* lpart, double* loss, cudaStream_t s);
 cudaError_t launch_mlp_sample(long long* idx, int B, long long count, unsigned long long seed, unsigned long long t,

@@ -64,6 +64,37 @@ __device__ void fwd(const float* __restrict__ w, const MlpShape& s, const float*
   __syncthreads();
 }
 
+// r + gamma (1 - done) max over the entries p allowed for operation j of out[j nprec + p]
+// (the one-step Bellman backup of Section 4.1 with Q given by the network).
+__device__ __forceinline__ float target_of(const float* out, int nprec, int j, const OpMask& mask, float r, int done,
+                                           float gamma) {
+  float m = -INFINITY;
+  for (int p = 0; p < nprec; ++p)
+    if ((mask.m[j] >> p) & 1u) m = fmaxf(m, out[j * nprec + p]);
+  return r + (done ? 0.f : gamma * m);
+}
+
+// Fitted-Q targets y[b][4] from the target network wt on feats_next[b], one CTA per sample.
+__global__ void __launch_bounds__(kMlpThreads) mlp_targets_kernel(const float* __restrict__ wt, int H, int nprec,
+                                                                  const float* __restrict__ feats_next,
+                                                                  const float* __restrict__ rew,
+                                                                  const int* __restrict__ done, int B, float gamma,
+                                                                  OpMask mask, float* y) {
+  extern __shared__ float sh[];
+  const MlpShape s = mlp_shape(H, nprec);
+  float* f = sh;
+  float* h1 = f + kNFeat;
+  float* h2 = h1 + s.H;
+  float* out = h2 + s.H;
+  for (int b = blockIdx.x; b < B; b += gridDim.x) {
+    if (threadIdx.x < kNFeat) f[threadIdx.x] = feats_next[(long long)b * kNFeat + threadIdx.x];
+    __syncthreads();
+    fwd(wt, s, f, h1, h2, out);
+    if (threadIdx.x < 4) y[(long long)b * 4 + threadIdx.x] = target_of(out, nprec, threadIdx.x, mask, rew[b], done[b], gamma);
+    __syncthreads();
+  }
+}
+
 // One chunk of the batch per CTA: gradient partials of the CTA -> part[blockIdx.x][np],
 // loss partial -> lpart[blockIdx.x]. With y == nullptr the targets come from the target
 // network on the next features (fitted Q); otherwise y[b][4] are the targets.
@@ -71,7 +102,7 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_grad_kernel(
     const float* __restrict__ w, const float* __restrict__ wt, int H, int nprec, const float* __restrict__ feats,
     const float* __restrict__ feats_next, const int* __restrict__ acts, const float* __restrict__ rew,
     const int* __restrict__ done, const float* __restrict__ y, const long long* __restrict__ idx, int B, int chunk,
-    float gamma, float* part, double* lpart) {
+    float gamma, OpMask mask, float* part, double* lpart) {
   extern __shared__ float sh[];
   const MlpShape s = mlp_shape(H, nprec);
   float* g = sh;                      // [np] gradient accumulator
@@ -100,12 +131,7 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_grad_kernel(
       if (threadIdx.x < kNFeat) f[threadIdx.x] = feats_next[src * kNFeat + threadIdx.x];
       __syncthreads();
       fwd(wt, s, f, h1, h2, out);
-      if (threadIdx.x < 4) {
-        const int j = threadIdx.x;
-        float m = out[j * nprec];
-        for (int p = 1; p < nprec; ++p) m = fmaxf(m, out[j * nprec + p]);
-        yt[j] = rew[src] + (done[src] ? 0.f : gamma * m);
-      }
+      if (threadIdx.x < 4) yt[threadIdx.x] = target_of(out, nprec, threadIdx.x, mask, rew[src], done[src], gamma);
       __syncthreads();
     }
     if (threadIdx.x < kNFeat) f[threadIdx.x] = feats[src * kNFeat + threadIdx.x];
@@ -209,12 +235,23 @@ cudaError_t mlp_set_smem_limit(size_t bytes) {
 
 cudaError_t launch_mlp_grad(const float* w, const float* wt, int H, int nprec, const float* feats,
                             const float* feats_next, const int* acts, const float* rew, const int* done, const float* y,
-                            const long long* idx, int B, int chunk, float gamma, float* part, double* lpart,
-                            cudaStream_t s) {
+                            const long long* idx, int B, int chunk, float gamma, OpMask mask, float* part,
+                            double* lpart, cudaStream_t s) {
   const int nparts = (B + chunk - 1) / chunk;
   cudaGetLastError();
   mlp_grad_kernel<<<nparts, kMlpThreads, mlp_grad_smem(H, nprec), s>>>(w, wt, H, nprec, feats, feats_next, acts, rew,
-                                                                       done, y, idx, B, chunk, gamma, part, lpart);
+                                                                       done, y, idx, B, chunk, gamma, mask, part, lpart);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_targets(const float* wt, int H, int nprec, const float* feats_next, const float* rew,
+                               const int* done, int B, float gamma, OpMask mask, float* y, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  const MlpShape sh = mlp_shape(H, nprec);
+  const size_t smem = sizeof(float) * (size_t)(kNFeat + 2 * sh.H + sh.nout);
+  cudaGetLastError();
+  mlp_targets_kernel<<<B < 1024 ? B : 1024, kMlpThreads, smem, s>>>(wt, H, nprec, feats_next, rew, done, B, gamma,
+                                                                     mask, y);
   return cudaGetLastError();
 }
 

@@ -109,6 +109,7 @@ SIGNATURES = {
     "mpcg_collect": (_st, [_vp, _i32, _vp, _vp, _d, _i32, _vp, _d, C.c_uint64, _vp, _i64, C.POINTER(_i64), _vp]),
     "mpcg_mlp_loss_grad": (_st, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, C.POINTER(_d), _vp]),
     "mpcg_mlp_train": (_st, [_vp, _vp, _vp, _i64, _i32, _i32, C.c_float, _i32, C.c_uint64, _vp, _vp]),
+    "mpcg_mlp_targets": (_st, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]),
 }
 
 _LIB = None
@@ -376,6 +377,17 @@ class Context:
         self._check(lib().mpcg_mlp_loss_grad(self.handle, _ptr(p), f.shape[0], _ptr(f), _ptr(a), _ptr(yy), _ptr(g),
                                              C.byref(loss), _stream(stream)))
         return loss.value, g
+
+    def mlp_targets(self, target_params, feats_next, rew, done, stream=None) -> np.ndarray:
+        """mpcg_mlp_targets: fitted-Q targets y[B][4] (host arrays in and out)."""
+        w = np.ascontiguousarray(target_params, dtype=np.float32)
+        fn = np.ascontiguousarray(feats_next, dtype=np.float32)
+        r = np.ascontiguousarray(rew, dtype=np.float32)
+        dn = np.ascontiguousarray(done, dtype=np.int32)
+        y = np.zeros((fn.shape[0], 4), dtype=np.float32)
+        self._check(lib().mpcg_mlp_targets(self.handle, _ptr(w), fn.shape[0], _ptr(fn), _ptr(r), _ptr(dn), _ptr(y),
+                                           _stream(stream)))
+        return y
 
     def mlp_train(self, policy: "Policy", data, steps: int, batch: int = 4096, lr: float = 1e-3,
                   target_sync: int = 200, seed: int = 0, stream=None) -> np.ndarray:
