@@ -272,6 +272,30 @@ __device__ void spmv_vec(const DevSys& S, const VT* __restrict__ vals, const VT*
   }
 }
 
+// Element k of a 16-byte word holding 16 / sizeof(VT) values (k known at compile time after
+// unrolling, so the values stay in registers).
+__device__ __forceinline__ unsigned word_of(const int4& q, int w) {
+  return (unsigned)(w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w);
+}
+template <typename VT>
+__device__ __forceinline__ VT lane_of(const int4& q, int k);
+template <>
+__device__ __forceinline__ __half lane_of<__half>(const int4& q, int k) {
+  return __ushort_as_half((unsigned short)(word_of(q, k >> 1) >> (16 * (k & 1))));
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 lane_of<__nv_bfloat16>(const int4& q, int k) {
+  return __ushort_as_bfloat16((unsigned short)(word_of(q, k >> 1) >> (16 * (k & 1))));
+}
+template <>
+__device__ __forceinline__ float lane_of<float>(const int4& q, int k) {
+  return __uint_as_float(word_of(q, k));
+}
+template <>
+__device__ __forceinline__ double lane_of<double>(const int4& q, int k) {
+  return __hiloint2double((int)word_of(q, 2 * k + 1), (int)word_of(q, 2 * k));
+}
+
 // One thread per row with 16-byte loads: the row's column indices and values are read in
 // aligned groups of G elements (G = 8 for 16-bit values, 4 otherwise; group starts rounded
 // down to a multiple of G, the arrays are padded so the last group stays in bounds), so a
@@ -316,7 +340,9 @@ __device__ void spmv_vload(const DevSys& S, const VT* __restrict__ vals, const V
 #pragma unroll
       for (int h = 0; h < NV; ++h) {
         const int4 vv = __ldg(reinterpret_cast<const int4*>(vals + g) + h);
-        memcpy(v + h * (16 / sizeof(VT)), &vv, 16);
+        constexpr int PER = 16 / (int)sizeof(VT);
+#pragma unroll
+        for (int k = 0; k < PER; ++k) v[h * PER + k] = lane_of<VT>(vv, k);
       }
       VT xv[G];
 #pragma unroll

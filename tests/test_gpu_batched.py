@@ -1,0 +1,119 @@
+"""The uneven batch (512 SPD systems, n log-uniform on [1e3, 2e5]: 2D and 3D variable-
+coefficient diffusion and banded L L^T + lam I), solved in one persistent launch captured in
+a CUDA graph with autotuned SpMV schedules: replays reproduce the results bit for bit, every
+system ends converged or capped (no breakdown for fp64 CG on SPD matrices), the smallest
+system of each kind matches the oracle's fp64 solve, and the batch throughput is printed
+(solves/s, fraction converged) for fp64 CG and for the tabular policy."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2504_14268_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TAU, CAP = 1e-8, 5000
+
+
+@pytest.fixture(scope="module")
+def batch():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2504_14268_gb300 import mpcg as M
+
+    t0 = time.time()
+    sets = I.cfg_batched(count=512)
+    gen = time.time() - t0
+    ctx = M.Context(0, M.Options(true_res_at_conv=1))
+    mats = []
+    for A, _, _ in sets:
+        n, rp, ci, val = A
+        mats.append(ctx.matrix((n, torch.as_tensor(rp).cuda(), torch.as_tensor(ci).cuda(),
+                                torch.as_tensor(val).cuda())))
+    t0 = time.time()
+    for m in mats:
+        m.autotune(1)
+    tune = time.time() - t0
+    bs = [torch.as_tensor(b).cuda() for _, b, _ in sets]
+    print(f"\n512 systems: {sum(A[0] for A, _, _ in sets)} rows, {sum(len(A[3]) for A, _, _ in sets)} nonzeros; "
+          f"generated in {gen:.1f} s, autotuned in {tune:.1f} s")
+    return M, ctx, sets, mats, bs
+
+
+def _run_graph(M, ctx, mats, bs, pol, reps=1):
+    xs = [torch.zeros_like(b) for b in bs]
+    g = ctx.graph(mats, bs, xs, [TAU] * len(bs), [CAP] * len(bs), pol)
+    g.launch()
+    first = g.results()
+    x_first = [x.clone() for x in xs]
+    times = []
+    for _ in range(reps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        g.launch()
+        ev[1].record()
+        torch.cuda.synchronize()
+        times.append(ev[0].elapsed_time(ev[1]) / 1e3)
+    last = g.results()
+    g.close()
+    return first, last, x_first, xs, float(np.median(times))
+
+
+def test_batched_graph_fp64(batch):
+    M, ctx, sets, mats, bs = batch
+    first, last, x1, x2, t = _run_graph(M, ctx, mats, bs, ctx.policy_fixed((4, 4, 4, 4)))
+    outcomes = np.array([r["outcome"] for r in last])
+    conv = float(np.mean(outcomes == 0))
+    print(f"fp64 CG: {len(bs) / t:.1f} solves/s ({t * 1e3:.1f} ms per batch), converged {conv:.3f}, "
+          f"iterations median {np.median([r['iters'] for r in last]):.0f} max {max(r['iters'] for r in last)}")
+    assert set(outcomes.tolist()) <= {0, 1}  # converged or capped
+    assert [r["iters"] for r in first] == [r["iters"] for r in last]
+    assert all(torch.equal(a, b) for a, b in zip(x1, x2))
+    # the smallest system of each kind against the oracle's fp64 CG
+    for kind in range(3):
+        idx = min(range(kind, len(sets), 3), key=lambda i: sets[i][0][0])
+        A, b, xs = sets[idx]
+        ref = O.solve(O.Options(true_res_at_conv=1), A, b, TAU, CAP, fixed=(4, 4, 4, 4))
+        assert last[idx]["outcome"] == ref.outcome
+        # badly conditioned banded systems (lambda_min down to 1e-6) take thousands of
+        # iterations whose count moves with the summation order of the dots
+        assert abs(last[idx]["iters"] - ref.iters) <= max(2, ref.iters // 10)
+        eg = np.linalg.norm(x2[idx].cpu().numpy() - xs)
+        eo = np.linalg.norm(ref.x - xs)
+        assert eg <= 10 * eo + 1e-14
+
+
+def test_batched_graph_tabular_policy(batch):
+    """The tabular policy trained (Algorithm 1, batched) on 16 systems of the 3D diffusion
+    training family, every operation choosing from {fp32, fp64}; applied to the whole batch."""
+    M, ctx, sets, mats, bs = batch
+    o = M.Options(true_res_at_conv=1, on_breakdown=1, op_mask=(0b11000,) * 4, seed=2)
+    c2 = M.Context(0, o)
+    train = I.cfg_train_set(count=16, m_lo=16, m_hi=32)
+    tm = [c2.matrix((A[0], torch.as_tensor(A[1]).cuda(), torch.as_tensor(A[2]).cuda(), torch.as_tensor(A[3]).cuda()))
+          for A, _, _ in train]
+    tb = [torch.as_tensor(b).cuda() for _, b, _ in train]
+    tab = c2.policy_qtable(np.zeros((4, 100, 5)), np.zeros((4, 100), dtype=np.int32))
+    c2.train_qtable(tm, tb, TAU, 1000, 60, tab, want_iters=True)
+    Q, v = tab.qtable()
+    mats2 = []
+    for A, _, _ in sets:
+        m = c2.matrix((A[0], torch.as_tensor(A[1]).cuda(), torch.as_tensor(A[2]).cuda(), torch.as_tensor(A[3]).cuda()))
+        m.autotune(1)
+        mats2.append(m)
+    first, last, x1, x2, t = _run_graph(M, c2, mats2, bs, tab)
+    outcomes = np.array([r["outcome"] for r in last])
+    conv = float(np.mean(outcomes == 0))
+    print(f"tabular policy: {len(bs) / t:.1f} solves/s ({t * 1e3:.1f} ms per batch), converged {conv:.3f}, "
+          f"iterations median {np.median([r['iters'] for r in last]):.0f}")
+    assert [r["iters"] for r in first] == [r["iters"] for r in last]
+    assert all(torch.equal(a, b) for a, b in zip(x1, x2))
+    assert set(outcomes.tolist()) <= {0, 1}
+    for r, (A, b, xs), x in zip(last, sets, x2):
+        if r["outcome"] == 0:
+            assert r["rel_res_true"] < TAU
