@@ -116,6 +116,11 @@ typedef struct {
                               recompute r = b - A x in fp64, restart with p = r and finish
                               with every operation in fp64 (at most once per solve)     */
   int32_t mlp_hidden;      /* hidden width of the MLP policy (64)                       */
+  int32_t batch_mode;      /* launches with several systems: 0 = automatic (lockstep),
+                            * 1 = teams (each system solved by its own group of CTAs from
+                            * start to end), 2 = lockstep (every CTA works on a slice of
+                            * every unfinished system at every phase; slices re-cut as
+                            * systems finish)                                            */
 } mpcg_options;
 
 /* Result of one solve. */

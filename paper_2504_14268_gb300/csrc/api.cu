@@ -65,6 +65,8 @@ struct Plan {
   DevBuf sys, st, res, cta_team, cta_rank, team_size, team_first, team_sys_off, team_sys, bars, partials, err;
   DevBuf work, bstage, xstage, hstage;
   DevBuf qpriv, trans, feats;
+  DevBuf lk_w, lk_pref, lk_cfirst, lk_clast, lk_base, lk_done, lk_seg, lk_nseg;
+  bool lockstep = false;
   std::vector<DevSys> hsys;
   std::vector<mpcg_result> hres;
   Launch L;
@@ -166,6 +168,7 @@ mpcg_status build_optview(mpcg_ctx_t ctx, const mpcg_options& o, OptView& v) {
   if (o.nprec < 1 || o.nprec > MPCG_MAX_PREC) return fail(ctx, MPCG_ERR_INVALID_ARG, "nprec must be in [1, 8]");
   if (!(o.eps_min > 0.0 && o.eps_min < 1.0)) return fail(ctx, MPCG_ERR_INVALID_ARG, "eps_min must be in (0, 1)");
   if (o.mlp_hidden < 1 || o.mlp_hidden > kMaxHidden) return fail(ctx, MPCG_ERR_INVALID_ARG, "mlp_hidden must be in [1, %d]", kMaxHidden);
+  if (o.batch_mode < 0 || o.batch_mode > 2) return fail(ctx, MPCG_ERR_INVALID_ARG, "batch_mode must be 0, 1 or 2");
   for (int a = 0; a < o.nprec; ++a)
     if (!valid_fmt(o.precs[a])) return fail(ctx, MPCG_ERR_INVALID_ARG, "precs[%d] = %d is not a format code", a, o.precs[a]);
   if (o.unvisited_fallback != -1 && !valid_fmt(o.unvisited_fallback))
@@ -411,7 +414,24 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
   CK(ctx, pl.team_sys_off.ensure(sizeof(int) * (nteams_all + 1)));
   CK(ctx, pl.team_sys.ensure(sizeof(int) * std::max<size_t>(1, team_sys_flat.size())));
   CK(ctx, pl.bars.ensure(sizeof(unsigned) * kBarStride * nteams_all));
-  CK(ctx, pl.partials.ensure(sizeof(double) * kNSlot * grid));
+  // Lockstep batches: every CTA works on a slice of every unfinished system.
+  const int bm = ctx->opt.batch_mode;
+  pl.lockstep = force_team == 0 && ((bm == 0 && nsys >= 2) || bm == 2) && nsys >= 1;
+  CK(ctx, pl.partials.ensure(sizeof(double) * kNSlot * (size_t)(grid + (pl.lockstep ? nsys : 0))));
+  if (pl.lockstep) {
+    std::vector<long long> w(nsys);
+    for (int i = 0; i < nsys; ++i) w[i] = std::max(1LL, in[i].A->dm.nnz + 3LL * in[i].A->dm.n);
+    CK(ctx, pl.lk_w.ensure(sizeof(long long) * nsys));
+    CK(ctx, pl.lk_pref.ensure(sizeof(long long) * (nsys + 1)));
+    CK(ctx, pl.lk_cfirst.ensure(sizeof(int) * nsys));
+    CK(ctx, pl.lk_clast.ensure(sizeof(int) * nsys));
+    CK(ctx, pl.lk_base.ensure(sizeof(int) * nsys));
+    CK(ctx, pl.lk_done.ensure(sizeof(int)));
+    CK(ctx, pl.lk_seg.ensure(sizeof(int4) * (size_t)grid * (nsys + 1)));
+    CK(ctx, pl.lk_nseg.ensure(sizeof(int) * grid));
+    CK(ctx, cudaMemcpyAsync(pl.lk_w.p, w.data(), sizeof(long long) * nsys, cudaMemcpyHostToDevice, s));
+    CK(ctx, cudaStreamSynchronize(s));
+  }
   CK(ctx, pl.err.ensure(sizeof(unsigned)));
   if (nsys) CK(ctx, cudaMemcpyAsync(pl.sys.p, pl.hsys.data(), sizeof(DevSys) * nsys, cudaMemcpyHostToDevice, s));
   CK(ctx, cudaMemcpyAsync(pl.cta_team.p, cta_team.data(), sizeof(int) * grid, cudaMemcpyHostToDevice, s));
@@ -449,6 +469,17 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
   L.stream_stage = stream_shape ? kStageBytes : 0;
   L.timeout_cycles = kTimeoutCycles;
   if (const char* t = getenv("MPCG_TIMEOUT_CYCLES")) L.timeout_cycles = atoll(t);
+  L.lockstep = pl.lockstep ? 1 : 0;
+  if (pl.lockstep) {
+    L.lk_w = pl.lk_w.as<long long>();
+    L.lk_pref = pl.lk_pref.as<long long>();
+    L.lk_cfirst = pl.lk_cfirst.as<int>();
+    L.lk_clast = pl.lk_clast.as<int>();
+    L.lk_base = pl.lk_base.as<int>();
+    L.lk_done = pl.lk_done.as<int>();
+    L.lk_seg = pl.lk_seg.as<int4>();
+    L.lk_nseg = pl.lk_nseg.as<int>();
+  }
   return MPCG_OK;
 }
 
@@ -456,8 +487,17 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
 mpcg_status enqueue_plan(mpcg_ctx_t ctx, Plan& pl, cudaStream_t s) {
   CK(ctx, cudaMemsetAsync(pl.bars.p, 0, sizeof(unsigned) * kBarStride * pl.nteams, s));
   CK(ctx, cudaMemsetAsync(pl.err.p, 0, sizeof(unsigned), s));
+  const size_t smem = pl.L.stream_stage > 0 ? 2 * (size_t)pl.L.stream_stage : 0;
+  if (pl.lockstep) {
+    // every system starts in its initialisation phase; no system has finished
+    CK(ctx, cudaMemsetAsync(pl.st.p, 0, sizeof(SysState) * pl.nsys, s));
+    CK(ctx, cudaMemsetAsync(pl.lk_done.p, 0, sizeof(int), s));
+    cudaGetLastError();
+    CK(ctx, launch_cg_lockstep(pl.L, pl.grid, smem, s));
+    return MPCG_OK;
+  }
   cudaGetLastError();
-  CK(ctx, launch_cg(pl.L, pl.grid, pl.L.stream_stage > 0 ? 2 * (size_t)pl.L.stream_stage : 0, s));
+  CK(ctx, launch_cg(pl.L, pl.grid, smem, s));
   return MPCG_OK;
 }
 
@@ -520,6 +560,7 @@ void mpcg_options_default(mpcg_options* o) {
   o->warm_start = 0;
   o->on_breakdown = 0;
   o->mlp_hidden = 64;
+  o->batch_mode = 0;
 }
 
 mpcg_status mpcg_create(mpcg_ctx_t* out, int device, const mpcg_options* opt) {

@@ -48,6 +48,7 @@ struct Smem {
   int need_action;
   int flag;
   int r0, r1;
+  int lk_phase, lk_known, lk_done;
   int a_fmt[4], a_act[4], a_expl, a_state;
   unsigned long long mbar[2];
   unsigned mbar_phase;
@@ -1121,6 +1122,351 @@ __device__ __forceinline__ bool solve_system(const Launch& L, const TeamCtx& T, 
   return true;
 }
 
+// ----------------------------------------------------------------------------------------
+// Lockstep batches: all CTAs work on all active systems at every super-step
+// ----------------------------------------------------------------------------------------
+// Each system runs the same sequence of phases as solve_system, as a state machine: at a
+// super-step every CTA does the row work of the current phase of each system it holds a
+// slice of (partials per slice), a grid barrier follows, then the CTA that owns a system
+// (system index modulo the grid) reduces the slices' partials in slice order, runs the
+// phase's scalar step and sets the next phase, and a second grid barrier closes the
+// super-step. The slices are cut from the active systems' row work (nnz + 3 n per system,
+// rows located by bisection on rp[r] + 3 r) and re-cut whenever a system finishes, so the
+// whole GPU keeps working on whatever systems are left.
+
+enum LkPhase : int { PH_INIT = 0, PH_PLOW, PH_A, PH_B, PH_C, PH_X, PH_T, PH_RZ, PH_R64, PH_FINAL, PH_DONE };
+
+__device__ __forceinline__ bool grid_sync(const Launch& L, const TeamCtx& G, Smem& sm) {
+  if (team_arrive(G, sm)) {
+    team_release(G);
+    return true;
+  }
+  return team_wait(L, G, sm);
+}
+
+// Exclusive prefix over the CTA's threads (thread order) of v; *total receives the sum.
+__device__ __forceinline__ long long cta_excl_scan(long long v, long long* tmp, long long* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  __syncthreads();
+  if (lane == 31) tmp[w] = x;
+  __syncthreads();
+  long long before = 0, all = 0;
+  for (int i = 0; i < kThreads / 32; ++i) {
+    if (i < w) before += tmp[i];
+    all += tmp[i];
+  }
+  *total = all;
+  return before + x - v;
+}
+
+// Re-cuts the slices (run by CTA 0 with all threads): prefix of the active systems' work,
+// the CTA range of each active system and the partial slot of its first slice.
+__device__ void lk_partition(const Launch& L, Smem& sm) {
+  long long* tmp = reinterpret_cast<long long*>(sm.red);
+  const int ns = L.nsys;
+  const long long G = gridDim.x;
+  long long carry = 0;
+  for (int c0 = 0; c0 < ns; c0 += kThreads) {
+    const int s = c0 + threadIdx.x;
+    long long w = 0;
+    if (s < ns && ((const volatile SysState*)(L.st + s))->phase != PH_DONE) w = L.lk_w[s];
+    long long tot;
+    const long long ex = cta_excl_scan(w, tmp, &tot);
+    if (s < ns) L.lk_pref[s] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) L.lk_pref[ns] = carry;
+  __syncthreads();
+  const long long W = carry;
+  long long slots = 0;
+  for (int c0 = 0; c0 < ns; c0 += kThreads) {
+    const int s = c0 + threadIdx.x;
+    long long cnt = 0;
+    int cf = -1, cl = -1;
+    if (s < ns && W > 0) {
+      const long long a = L.lk_pref[s], b = L.lk_pref[s + 1];
+      if (b > a) {
+        cf = (int)((a * G) / W);
+        cl = (int)(((b - 1) * G) / W);
+        cnt = cl - cf + 1;
+      }
+    }
+    long long tot;
+    const long long ex = cta_excl_scan(cnt, tmp, &tot);
+    if (s < ns) {
+      L.lk_cfirst[s] = cf;
+      L.lk_clast[s] = cl;
+      L.lk_base[s] = (int)(slots + ex);
+    }
+    slots += tot;
+  }
+}
+
+// First row r of system S with rp[r] + 3 r >= t (0 <= t <= nnz + 3 n).
+__device__ __forceinline__ int lk_row_at(const DevSys& S, long long t) {
+  int lo = 0, hi = S.A.n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((long long)__ldg(S.A.rp + mid) + 3LL * mid < t) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// The slices of this CTA under the current cut (thread 0 writes them, the CTA reads them
+// after the barrier at the end of the function).
+__device__ void lk_slices(const Launch& L, Smem& sm) {
+  if (threadIdx.x == 0) {
+    const int c = blockIdx.x, ns = L.nsys;
+    const long long G = gridDim.x, W = L.lk_pref[ns];
+    int4* out = L.lk_seg + (long long)c * (ns + 1);
+    int cnt = 0;
+    if (W > 0) {
+      // positions x in [0, W) belong to CTA floor(x G / W): this CTA holds [a, b)
+      const long long a = (W * c + G - 1) / G, b = (W * (c + 1) + G - 1) / G;
+      // first system whose work ends after a
+      int lo = 0, hi = ns;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (L.lk_pref[mid + 1] <= a) lo = mid + 1;
+        else hi = mid;
+      }
+      for (int s = lo; s < ns && cnt <= ns; ++s) {
+        const long long ps = L.lk_pref[s], pe = L.lk_pref[s + 1];
+        if (ps >= b) break;
+        if (pe <= ps || pe <= a) continue;
+        const DevSys& S = L.sys[s];
+        const long long t0 = (a > ps ? a : ps) - ps, t1 = (b < pe ? b : pe) - ps;
+        const int r0 = lk_row_at(S, t0), r1 = lk_row_at(S, t1);
+        out[cnt++] = make_int4(s, r0, r1, L.lk_base[s] + (c - L.lk_cfirst[s]));
+      }
+    }
+    L.lk_nseg[c] = cnt;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void lk_partial(const Launch& L, int slot, int k, double v) {
+  if (threadIdx.x == 0) L.partials[(long long)slot * kNSlot + k] = v;
+}
+
+// Row work of one slice in the current phase of its system.
+__device__ void lk_slice_rows(const Launch& L, int s, Rows R, int slot, Smem& sm, const StreamCtx* sc) {
+  const DevSys& S = L.sys[s];
+  SysState* st = L.st + s;
+  if (threadIdx.x == 0) {
+    const volatile SysState* v = st;
+    sm.lk_phase = v->phase;
+    sm.lk_known = v->true_known;
+  }
+  load_bcast(st, sm);  // ends with __syncthreads
+  const int phase = sm.lk_phase;
+  switch (phase) {
+    case PH_INIT: {
+      double bb = 0.0, rr = 0.0;
+      DotAcc unused{0.0, 0.f, 0.f};
+      const bool warm = L.opt.warm_start != 0;
+      for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
+        const double bi = __ldg(S.b + i);
+        bb = fma(bi, bi, bb);
+        if (!warm) {
+          S.x[i] = 0.0;
+          S.r[i] = bi;
+          S.p[i] = bi;
+          rr = fma(bi, bi, rr);
+        }
+      }
+      if (warm) true_res_rows(S, R, -1, -1, true, rr, unused);
+      bb = cta_sum(bb, sm.red);
+      rr = cta_sum(rr, sm.red);
+      lk_partial(L, slot, 0, bb);
+      lk_partial(L, slot, 1, rr);
+      break;
+    }
+    case PH_PLOW: {
+      const int p1 = sm.bc.fmt[0];
+      if (p1 != F64)
+        for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) store_low(S.plow, i, S.p[i], p1);
+      break;
+    }
+    case PH_A: {
+      DotAcc nu{0.0, 0.f, 0.f};
+      spmv_rows(S, R, sm.bc.fmt[0], sm.bc.fmt[2], nu, sc);
+      lk_partial(L, slot, 0, cta_dot(nu, sm.red));
+      break;
+    }
+    case PH_B: {
+      const int p1 = sm.bc.fmt[0], p2 = sm.bc.fmt[1], p4 = sm.bc.fmt[3];
+      const bool sig_rr = (p2 == F64 && p4 == F64);
+      double rr = 0.0;
+      DotAcc sg{0.0, 0.f, 0.f};
+      phase_b(S, R, sm.bc.alpha, p1, p2, p4, sig_rr, rr, sg);
+      rr = cta_sum(rr, sm.red);
+      const double sp = sig_rr ? rr : cta_dot(sg, sm.red);
+      lk_partial(L, slot, 0, rr);
+      lk_partial(L, slot, 1, sp);
+      break;
+    }
+    case PH_C:
+      phase_c(S, R, sm.bc.alpha, sm.bc.beta, sm.bc.zfmt, sm.bc.fmt[0]);
+      break;
+    case PH_X: {
+      const double alpha = sm.bc.alpha;
+      for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) S.x[i] = fma(alpha, S.p[i], S.x[i]);
+      break;
+    }
+    case PH_T: {
+      double rr = 0.0;
+      DotAcc sg{0.0, 0.f, 0.f};
+      true_res_rows(S, R, sm.bc.fmt[1], sm.bc.fmt[3], false, rr, sg);
+      rr = cta_sum(rr, sm.red);
+      const double sp = cta_dot(sg, sm.red);
+      lk_partial(L, slot, 0, rr);
+      lk_partial(L, slot, 1, sp);
+      break;
+    }
+    case PH_RZ: {
+      const int p1n = sm.bc.fmt[0], p2 = sm.bc.zfmt;
+      for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
+        const double pn = z_of(S.r[i], p2);
+        S.p[i] = pn;
+        if (p1n != F64) store_low(S.plow, i, pn, p1n);
+      }
+      break;
+    }
+    case PH_R64: {
+      double rr = 0.0;
+      DotAcc unused{0.0, 0.f, 0.f};
+      true_res_rows(S, R, -1, -1, true, rr, unused);
+      lk_partial(L, slot, 0, cta_sum(rr, sm.red));
+      break;
+    }
+    case PH_FINAL: {
+      double rr = 0.0;
+      DotAcc unused{0.0, 0.f, 0.f};
+      if (!sm.lk_known) true_res_rows(S, R, -1, -1, false, rr, unused);
+      lk_partial(L, slot, 0, cta_sum(rr, sm.red));
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// Sum of partial k over the slices of a system (slice order per thread, fixed tree across
+// threads: deterministic for a given cut).
+__device__ __forceinline__ double lk_sum(const Launch& L, int base, int np, int k, Smem& sm) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < np; i += kThreads) v += __ldcg(&L.partials[(long long)(base + i) * kNSlot + k]);
+  return cta_sum(v, sm.red);
+}
+
+// Scalar step of the phase system s has just run, by the CTA that owns s; sets the next
+// phase (the transitions of solve_system).
+__device__ void lk_step(const Launch& L, int s, Smem& sm) {
+  const DevSys& S = L.sys[s];
+  SysState* st = L.st + s;
+  if (threadIdx.x == 0) sm.lk_phase = ((const volatile SysState*)st)->phase;
+  __syncthreads();
+  const int phase = sm.lk_phase;
+  if (phase == PH_DONE) return;
+  const int cf = L.lk_cfirst[s], base = L.lk_base[s];
+  const int np = cf < 0 ? 0 : L.lk_clast[s] - cf + 1;
+  switch (phase) {
+    case PH_INIT: {
+      const double tb = lk_sum(L, base, np, 0, sm), tr = lk_sum(L, base, np, 1, sm);
+      step_init(L, S, st, tb, tr, sm);
+      break;
+    }
+    case PH_A: step_A(L, S, st, lk_sum(L, base, np, 0, sm)); break;
+    case PH_B: {
+      const double trr = lk_sum(L, base, np, 0, sm), tsg = lk_sum(L, base, np, 1, sm);
+      step_B(L, S, st, trr, tsg, sm);
+      break;
+    }
+    case PH_C: stamp_c(S, st); break;
+    case PH_T: {
+      const double trr = lk_sum(L, base, np, 0, sm), tsg = lk_sum(L, base, np, 1, sm);
+      step_T(L, S, st, trr, tsg, sm);
+      break;
+    }
+    case PH_R64: step_restart(L, S, st, lk_sum(L, base, np, 0, sm), sm); break;
+    case PH_FINAL: step_final(L, S, st, s, lk_sum(L, base, np, 0, sm)); break;
+    default: break;  // PH_PLOW, PH_X, PH_RZ: no scalar work
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const volatile SysState* v = st;
+    const int mode = v->mode;
+    int next = PH_FINAL;
+    switch (phase) {
+      case PH_INIT: next = mode == M_CONT ? (v->fmt[0] != F64 ? PH_PLOW : PH_A) : PH_FINAL; break;
+      case PH_PLOW: next = PH_A; break;
+      case PH_A: next = mode == M_RESTART64 ? PH_R64 : mode == M_CONT ? PH_B : PH_FINAL; break;
+      case PH_B: next = mode == M_CONT ? PH_C : mode == M_DONE ? PH_FINAL : PH_X; break;
+      case PH_C: next = v->k >= S.max_iter ? PH_FINAL : PH_A; break;
+      case PH_X: next = mode == M_X_THEN_DONE ? PH_FINAL : mode == M_X_THEN_RESTART64 ? PH_R64 : PH_T; break;
+      case PH_T: next = mode == M_RESTART64 ? PH_R64 : mode == M_RESTART ? PH_RZ : PH_FINAL; break;
+      case PH_RZ: next = v->k >= S.max_iter ? PH_FINAL : PH_A; break;
+      case PH_R64: next = mode == M_CONT ? PH_A : PH_FINAL; break;
+      default: next = PH_DONE; break;  // PH_FINAL
+    }
+    st->phase = next;
+    if (next == PH_DONE) atomicAdd(L.lk_done, 1);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads, 4) cg_lockstep(const Launch L) {
+  __shared__ Smem sm;
+  extern __shared__ __align__(128) unsigned char dyn[];
+  StreamCtx scx{dyn, sm.mbar, &sm.mbar_phase, L.err, L.stream_stage};
+  if (L.stream_stage > 0) {
+    if (threadIdx.x == 0) {
+      mbar_init(sm.mbar + 0, 1);
+      mbar_init(sm.mbar + 1, 1);
+      mbar_fence_init();
+      sm.mbar_phase = 0;
+    }
+    __syncthreads();
+  }
+  const StreamCtx* sc = L.stream_stage > 0 ? &scx : nullptr;
+  TeamCtx G;
+  G.team = 0;
+  G.rank = blockIdx.x;
+  G.size = gridDim.x;
+  G.first = 0;
+  G.bar = L.bars;
+  int seen = -1;
+  while (true) {
+    if (threadIdx.x == 0) sm.lk_done = *(volatile int*)L.lk_done;
+    __syncthreads();
+    const int done = sm.lk_done;
+    __syncthreads();
+    if (done >= L.nsys) break;
+    if (done != seen) {
+      if (blockIdx.x == 0) lk_partition(L, sm);
+      if (!grid_sync(L, G, sm)) return;
+      lk_slices(L, sm);
+      seen = done;
+    }
+    const int nseg = L.lk_nseg[blockIdx.x];
+    for (int i = 0; i < nseg; ++i) {
+      const int4 sg = L.lk_seg[(long long)blockIdx.x * (L.nsys + 1) + i];
+      lk_slice_rows(L, sg.x, Rows{sg.y, sg.z}, sg.w, sm, sc);
+    }
+    if (!grid_sync(L, G, sm)) return;
+    for (int s = blockIdx.x; s < L.nsys; s += gridDim.x) lk_step(L, s, sm);
+    if (!grid_sync(L, G, sm)) return;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 4) cg_persistent(const Launch L) {
   __shared__ Smem sm;
   extern __shared__ __align__(128) unsigned char dyn[];
@@ -1153,12 +1499,27 @@ cudaError_t launch_cg(const Launch& L, int grid, size_t smem, cudaStream_t s) {
   return cudaLaunchCooperativeKernel((const void*)cg_persistent, dim3(grid), dim3(kThreads), args, smem, s);
 }
 
+cudaError_t launch_cg_lockstep(const Launch& L, int grid, size_t smem, cudaStream_t s) {
+  void* args[] = {(void*)&L};
+  return cudaLaunchCooperativeKernel((const void*)cg_lockstep, dim3(grid), dim3(kThreads), args, smem, s);
+}
+
+// Resident CTAs per SM of the solver kernels (the smaller of the two, so that one grid size
+// serves both).
 cudaError_t cg_occupancy(int* blocks_per_sm, size_t smem) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, cg_persistent, kThreads, smem);
+  int a = 0, b = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, cg_persistent, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cg_lockstep, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  *blocks_per_sm = a < b ? a : b;
+  return cudaSuccess;
 }
 
 cudaError_t cg_set_smem_limit(size_t bytes) {
-  return cudaFuncSetAttribute(cg_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  const cudaError_t e = cudaFuncSetAttribute(cg_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(cg_lockstep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 size_t cg_static_smem() { return sizeof(Smem); }

@@ -89,7 +89,8 @@ struct SysState {
   int prev_act[4];
   int have_prev, n_true, ntrans, true_known;
   int explored, s_cur;      // exploration flag and state index of the current iteration
-  int zfmt, pad;            // p2 of the iteration whose direction update is pending
+  int zfmt;                 // p2 of the iteration whose direction update is pending
+  int phase;                // lockstep batches: the phase the system runs next (0 = initialisation)
   int fp64_lock, n_restart;   // after a breakdown restart every operation runs in fp64
   unsigned long long t_last;  // globaltimer at the previous team barrier
   unsigned ns_a, ns_b;        // phase times of the current iteration
@@ -148,6 +149,18 @@ struct Launch {
   unsigned long long episode;
   double eps;
   long long timeout_cycles;
+  // Lockstep batches (lockstep != 0): at every super-step each CTA works on a slice of every
+  // active system, the slices re-cut whenever systems finish.
+  int lockstep;
+  int pad_lk;
+  const long long* lk_w;    // [nsys] row work of each system: nnz + 3 n (at least 1)
+  long long* lk_pref;       // [nsys + 1] prefix of the work of the active systems
+  int* lk_cfirst;           // [nsys] first CTA holding rows of the system (-1: finished)
+  int* lk_clast;            // [nsys] last such CTA
+  int* lk_base;             // [nsys] partial slot of the system's first slice
+  int* lk_done;             // number of finished systems
+  int4* lk_seg;             // [grid][nsys + 1] slices of each CTA: (system, r0, r1, partial slot)
+  int* lk_nseg;             // [grid] number of slices of each CTA
 };
 
 // Device status word values.
@@ -155,6 +168,7 @@ enum DevErr : unsigned { DERR_NONE = 0, DERR_TIMEOUT = 1, DERR_BAD_STATE = 2 };
 
 // Host entry points of the kernels (cg_kernel.cu, setup_kernels.cu).
 cudaError_t launch_cg(const Launch& L, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_cg_lockstep(const Launch& L, int grid, size_t smem, cudaStream_t s);
 cudaError_t cg_occupancy(int* blocks_per_sm, size_t smem);
 size_t cg_static_smem();
 cudaError_t launch_validate(int n, long long nnz, const int* rp, const int* ci, const double* v,

@@ -44,6 +44,7 @@ class COptions(C.Structure):
         ("unvisited_fallback", C.c_int32), ("true_res_every", C.c_int32), ("true_res_at_conv", C.c_int32),
         ("warm_start", C.c_int32), ("op_mask", C.c_int32 * 4), ("on_breakdown", C.c_int32),
         ("mlp_hidden", C.c_int32),
+        ("batch_mode", C.c_int32),
     ]
 
 
@@ -192,6 +193,7 @@ class Options:
     op_mask: tuple = (0, 0, 0, 0)
     on_breakdown: int = 0
     mlp_hidden: int = 64
+    batch_mode: int = 0
 
     def c(self) -> COptions:
         o = COptions()

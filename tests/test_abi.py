@@ -41,7 +41,7 @@ def test_struct_layouts():
 
     assert ctypes.sizeof(mpcg.CResult) == 288
     assert mpcg.REC_DTYPE.itemsize == 80
-    assert ctypes.sizeof(mpcg.COptions) == 232
+    assert ctypes.sizeof(mpcg.COptions) == 240
     assert ctypes.sizeof(mpcg.Csr) == 40
 
 
