@@ -79,6 +79,40 @@ def train_policy(M, ctx):
     return pol, dt, (float(its[:3].mean()), float(its[-3:].mean()))
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_cg_persistent_fem27_256.md")
+
+
+def sources_sha256() -> str:
+    """Hash of the kernel sources and the C header (the build the ncu counters belong to)."""
+    import glob
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2504_14268_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(csrc, "*"))) + [os.path.join(ROOT, "include", "mpcg.h")]:
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the solver kernel on this workload from the committed ncu
+    summary, or None when that summary was taken on other kernel sources."""
+    try:
+        vals = {}
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "sources_sha256")):
+                    k, v = line.strip().split(":", 1)
+                    vals[k.strip()] = v.strip().strip("`")
+        if vals.get("sources_sha256") == sources_sha256():
+            return float(vals["traffic_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
 def peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -380,8 +414,8 @@ def main():
             "action_mix": {M.FORMAT_NAMES[f]: int(ah[:, f].sum()) for f in range(7)},
             "spmv": spmv,
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                         "frac": round(achieved / hbm, 3), "traffic": None, "peak_source": peak_kind,
-                         "kernel": "cg_persistent", "bytes_per_launch": lb},
+                         "frac": round(achieved / hbm, 3), "traffic": measured_traffic(), "peak_source": peak_kind,
+                         "kernel": "cg_persistent", "bytes_per_launch": lb, "sources_sha256": sources_sha256()},
             "e2e": {"value": args.steps / e2e_T, "unit": "solves/s", "h2d_bytes_per_step": 8 * n,
                     "d2h_bytes_per_step": 8 * n + 288},
             "cpu_baseline": cpu,
