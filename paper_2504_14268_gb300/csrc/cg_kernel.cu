@@ -930,9 +930,163 @@ __device__ __forceinline__ void phase_c_rows(const DevSys& S, Rows R, double alp
   }
 }
 
+// Pair-vectorised variants: a thread takes rows 2j and 2j+1 with one 16-byte load of each
+// fp64 vector (and one load of two q / p-copy elements); the odd first and last rows of the
+// range go through the element-wise code. Used when every vector is 16-byte aligned.
+template <typename T> struct PairOf;
+template <> struct PairOf<double> { using type = double2; };
+template <> struct PairOf<float> { using type = float2; };
+template <> struct PairOf<__half> { using type = __half2; };
+template <> struct PairOf<__nv_bfloat16> { using type = __nv_bfloat162; };
+
+constexpr int kPairs = 2;  // row pairs per thread in flight
+
+template <typename QT, bool SCALED>
+__device__ __forceinline__ void phase_b_row(const DevSys& S, int i, double alpha, int p2, int p4, bool sig_rr,
+                                            double& rr, DotAcc& sg) {
+  double qd = stored_as_double(((const QT*)S.q)[i]);
+  if constexpr (SCALED) qd = scale2(qd, __ldg(S.A.rexp + i));
+  const double ri = fma(-alpha, qd, S.r[i]);
+  S.r[i] = ri;
+  rr = fma(ri, ri, rr);
+  if (!sig_rr) sigma_term(ri, p2, p4, sg);
+}
+
+template <typename QT, bool SCALED>
+__device__ __forceinline__ void phase_b_pairs(const DevSys& S, Rows R, double alpha, int p2, int p4, bool sig_rr,
+                                              double& rr, DotAcc& sg) {
+  using Q2 = typename PairOf<QT>::type;
+  int a = R.r0, e = R.r1;
+  if (a < e && (a & 1)) {
+    if (threadIdx.x == 0) phase_b_row<QT, SCALED>(S, a, alpha, p2, p4, sig_rr, rr, sg);
+    ++a;
+  }
+  if (a < e && (e & 1)) {
+    if (threadIdx.x == 1) phase_b_row<QT, SCALED>(S, e - 1, alpha, p2, p4, sig_rr, rr, sg);
+    --e;
+  }
+  const Q2* __restrict__ q2 = (const Q2*)S.q;
+  double2* r2 = (double2*)S.r;
+  const short2* e2 = (const short2*)S.A.rexp;
+  const int j1 = e >> 1;
+  for (int j0 = (a >> 1) + threadIdx.x; j0 < j1; j0 += kPairs * kThreads) {
+    Q2 qv[kPairs];
+    double2 ro[kPairs];
+    short2 ev[kPairs];
+#pragma unroll
+    for (int u = 0; u < kPairs; ++u) {
+      const int j = j0 + u * kThreads;
+      if (j < j1) {
+        qv[u] = q2[j];
+        ro[u] = r2[j];
+        if constexpr (SCALED) ev[u] = __ldg(e2 + j);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPairs; ++u) {
+      const int j = j0 + u * kThreads;
+      if (j < j1) {
+        double qa = stored_as_double(qv[u].x), qb = stored_as_double(qv[u].y);
+        if constexpr (SCALED) {
+          qa = scale2(qa, ev[u].x);
+          qb = scale2(qb, ev[u].y);
+        }
+        double2 rn;
+        rn.x = fma(-alpha, qa, ro[u].x);
+        rn.y = fma(-alpha, qb, ro[u].y);
+        r2[j] = rn;
+        rr = fma(rn.x, rn.x, rr);
+        rr = fma(rn.y, rn.y, rr);
+        if (!sig_rr) {
+          sigma_term(rn.x, p2, p4, sg);
+          sigma_term(rn.y, p2, p4, sg);
+        }
+      }
+    }
+  }
+}
+
+template <typename PT>
+__device__ __forceinline__ void phase_c_row(const DevSys& S, int i, double alpha, double beta, int p2, int p1n) {
+  const double pv = S.p[i];
+  S.x[i] = fma(alpha, pv, S.x[i]);
+  const double rv = S.r[i];
+  const double z = p2 != F64 ? f2d(round_d2f(rv, p2)) : rv;
+  const double pn = fma(beta, pv, z);
+  S.p[i] = pn;
+  if constexpr (sizeof(PT) != 8) ((PT*)S.plow)[i] = to_storage<PT>(round_d2f(pn, p1n));
+}
+
+template <typename PT>
+__device__ __forceinline__ void phase_c_pairs(const DevSys& S, Rows R, double alpha, double beta, int p2, int p1n) {
+  const bool zlow = p2 != F64;
+  int a = R.r0, e = R.r1;
+  if (a < e && (a & 1)) {
+    if (threadIdx.x == 0) phase_c_row<PT>(S, a, alpha, beta, p2, p1n);
+    ++a;
+  }
+  if (a < e && (e & 1)) {
+    if (threadIdx.x == 1) phase_c_row<PT>(S, e - 1, alpha, beta, p2, p1n);
+    --e;
+  }
+  double2* p2v = (double2*)S.p;
+  double2* x2v = (double2*)S.x;
+  const double2* r2v = (const double2*)S.r;
+  const int j1 = e >> 1;
+  for (int j0 = (a >> 1) + threadIdx.x; j0 < j1; j0 += kPairs * kThreads) {
+    double2 pv[kPairs], xv[kPairs], rv[kPairs];
+#pragma unroll
+    for (int u = 0; u < kPairs; ++u) {
+      const int j = j0 + u * kThreads;
+      if (j < j1) {
+        pv[u] = p2v[j];
+        xv[u] = x2v[j];
+        rv[u] = r2v[j];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPairs; ++u) {
+      const int j = j0 + u * kThreads;
+      if (j < j1) {
+        double2 xn, pn;
+        xn.x = fma(alpha, pv[u].x, xv[u].x);
+        xn.y = fma(alpha, pv[u].y, xv[u].y);
+        x2v[j] = xn;
+        const double za = zlow ? f2d(round_d2f(rv[u].x, p2)) : rv[u].x;
+        const double zb = zlow ? f2d(round_d2f(rv[u].y, p2)) : rv[u].y;
+        pn.x = fma(beta, pv[u].x, za);
+        pn.y = fma(beta, pv[u].y, zb);
+        p2v[j] = pn;
+        if constexpr (sizeof(PT) != 8) {
+          typename PairOf<PT>::type lw;
+          lw.x = to_storage<PT>(round_d2f(pn.x, p1n));
+          lw.y = to_storage<PT>(round_d2f(pn.y, p1n));
+          ((typename PairOf<PT>::type*)S.plow)[j] = lw;
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ bool aligned16(const void* a, const void* b, const void* c) {
+  return ((reinterpret_cast<unsigned long long>(a) | reinterpret_cast<unsigned long long>(b) |
+           reinterpret_cast<unsigned long long>(c)) & 15ull) == 0ull;
+}
+
 // Row phases B and C, out of line (one register allocation each, as for the product).
 __device__ __noinline__ void phase_b(const DevSys& S, Rows R, double alpha, int p1, int p2, int p4, bool sig_rr,
                                      double& rr, DotAcc& sg) {
+  if (aligned16(S.r, S.q, S.r)) {
+    switch (p1) {
+      case F64: phase_b_pairs<double, false>(S, R, alpha, p2, p4, sig_rr, rr, sg); return;
+      case F32:
+      case TF32: phase_b_pairs<float, false>(S, R, alpha, p2, p4, sig_rr, rr, sg); return;
+      case F16: phase_b_pairs<__half, false>(S, R, alpha, p2, p4, sig_rr, rr, sg); return;
+      case BF16: phase_b_pairs<__nv_bfloat16, false>(S, R, alpha, p2, p4, sig_rr, rr, sg); return;
+      case F16R: phase_b_pairs<__half, true>(S, R, alpha, p2, p4, sig_rr, rr, sg); return;
+      default: phase_b_pairs<__nv_bfloat16, true>(S, R, alpha, p2, p4, sig_rr, rr, sg); return;
+    }
+  }
   switch (p1) {
     case F64: phase_b_rows<double, false>(S, R, alpha, p2, p4, sig_rr, rr, sg); break;
     case F32:
@@ -945,6 +1099,14 @@ __device__ __noinline__ void phase_b(const DevSys& S, Rows R, double alpha, int 
 }
 
 __device__ __noinline__ void phase_c(const DevSys& S, Rows R, double alpha, double beta, int p2, int p1n) {
+  if (aligned16(S.p, S.x, S.r)) {
+    switch (store_of(p1n)) {
+      case ST_DOUBLE: phase_c_pairs<double>(S, R, alpha, beta, p2, p1n); return;
+      case ST_FLOAT: phase_c_pairs<float>(S, R, alpha, beta, p2, p1n); return;
+      case ST_HALF: phase_c_pairs<__half>(S, R, alpha, beta, p2, p1n); return;
+      default: phase_c_pairs<__nv_bfloat16>(S, R, alpha, beta, p2, p1n); return;
+    }
+  }
   switch (store_of(p1n)) {
     case ST_DOUBLE: phase_c_rows<double>(S, R, alpha, beta, p2, p1n); break;
     case ST_FLOAT: phase_c_rows<float>(S, R, alpha, beta, p2, p1n); break;
