@@ -188,7 +188,10 @@ mpcg_status mpcg_matrix_create(mpcg_ctx_t ctx, const mpcg_csr* A, mpcg_matrix_t*
 mpcg_status mpcg_matrix_destroy(mpcg_matrix_t A);
 mpcg_status mpcg_matrix_info(mpcg_matrix_t A, mpcg_matrix_stats* info);
 /* Times every SpMV schedule on A for each value format (a few launches each) and keeps
- * the fastest (the autotuner). `reps` timed launches per candidate. */
+ * the fastest (the autotuner). `reps` timed launches per candidate. Matrices with fewer
+ * than 2^22 nonzeros, whose products are too short to time apart, keep the row-length rule
+ * that mpcg_matrix_create applies (vector loads for rows up to ~32 nonzeros, K lanes with
+ * about 24 nonzeros per lane beyond, a warp per row when a row exceeds 1024). */
 mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, void* stream);
 /* Forces the SpMV schedule of value format `fmt` (sched: 0 = sub-warp vector CSR with
  * `lanes` lanes per row (1, 2, 4, 8, 16 or 32); 1 = staged stream CSR, shared-memory tiles

@@ -53,6 +53,7 @@ bool is_device_ptr(const void* p) {
 }
 
 constexpr long long kTimeoutCycles = 4000000000ll;  // about two seconds at 2 GHz per wait
+constexpr long long kTuneMinNnz = 4LL << 20;        // smallest matrix the autotuner times
 
 }  // namespace
 
@@ -513,12 +514,21 @@ mpcg_status finish_plan(mpcg_ctx_t ctx, Plan& pl, mpcg_result* res, cudaStream_t
   return MPCG_OK;
 }
 
+// Row-length rule for the product schedule (from timings on GB300 across the workloads'
+// row lengths): one thread per row with 16-byte loads for rows of up to about 32 nonzeros;
+// longer rows get K lanes, K the power of two near mean / 24 (banded rows of 65 nonzeros:
+// 4 lanes, of 129: 8); a warp per row when some row exceeds 1024 nonzeros (power-law hubs).
 void default_schedule(mpcg_matrix_s* M) {
-  // Sub-warp vector CSR with about four nonzeros per lane.
-  int lanes = 1;
-  while (lanes < 32 && lanes * 4 < M->mean) lanes *= 2;
+  int sched = SCHED_VECTOR, lanes = 1;
+  if (M->maxr > 1024) {
+    lanes = 32;
+  } else if (M->mean <= 32.0) {
+    sched = SCHED_VLOAD;
+  } else {
+    while (lanes < 32 && lanes * 24 < M->mean) lanes *= 2;
+  }
   for (int f = 0; f < 8; ++f) {
-    M->dm.sched[f] = SCHED_VECTOR;
+    M->dm.sched[f] = sched;
     M->dm.lanes[f] = lanes;
   }
 }
@@ -823,6 +833,12 @@ mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, 
   cudaSetDevice(ctx->device);
   const int n = A->dm.n;
   if (n == 0) return MPCG_OK;
+  // A product of a small matrix takes a few microseconds on the whole GPU, within the noise
+  // of the launch itself: such matrices keep the row-length rule.
+  if (A->dm.nnz < kTuneMinNnz) {
+    default_schedule(A);
+    return MPCG_OK;
+  }
   DevBuf x, y;
   CK(ctx, x.ensure(8 * (size_t)n));
   CK(ctx, y.ensure(8 * (size_t)n));
