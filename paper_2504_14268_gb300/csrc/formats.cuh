@@ -136,23 +136,31 @@ __device__ __forceinline__ void store_fmt(void* p, long long i, double v, int f)
 // so the per-row work converts between fp32 and fp64 by assembling bit patterns and rounds
 // fp64 values onto the 16-bit formats through fp32.
 
-// The rare cases of the conversions below go through out-of-line functions, so that the
-// common path never issues (even predicated off) an instruction of the fp64 pipe.
-static __device__ __noinline__ double f2d_slow(float v) { return (double)v; }
-static __device__ __noinline__ double mul_pow2_slow(double x, int e) {
-  return x * __longlong_as_double((long long)((unsigned long long)(e + 1023) << 52));
-}
-
-// Exact fp32 -> fp64.
+// Exact fp32 -> fp64 from the bit pattern (normal, zero, subnormal, infinite, NaN). Integer
+// instructions only: GB300 runs fp64 conversions on its narrow fp64 pipe, and a call to an
+// out-of-line slow path in a per-row loop makes the compiler save registers around it.
 __device__ __forceinline__ double f2d(float v) {
   const unsigned u = __float_as_uint(v);
+  const unsigned sgn = u & 0x80000000u;
   const unsigned a = u & 0x7fffffffu;
+  unsigned hi, lo;
   if (a - 0x00800000u < 0x7f000000u) {  // normal
-    const unsigned hi = (u & 0x80000000u) | ((a >> 3) + (896u << 20));
-    return __hiloint2double((int)hi, (int)(a << 29));
+    hi = sgn | ((a >> 3) + (896u << 20));
+    lo = a << 29;
+  } else if (a == 0u) {
+    hi = sgn;
+    lo = 0u;
+  } else if (a >= 0x7f800000u) {  // infinite or NaN: same fraction bits, top of the exponent
+    hi = sgn | 0x7ff00000u | ((a & 0x7fffffu) >> 3);
+    lo = a << 29;
+  } else {  // subnormal: a 2^-149 with the leading one at bit p
+    const int p = 31 - __clz((int)a);
+    const unsigned long long bits =
+        ((unsigned long long)(p - 149 + 1023) << 52) | (((unsigned long long)a << (52 - p)) & 0xfffffffffffffull);
+    hi = sgn | (unsigned)(bits >> 32);
+    lo = (unsigned)bits;
   }
-  if (a == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
-  return f2d_slow(v);  // subnormal, infinite or NaN
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 // x * 2^e for an fp64 x whose result stays in the normal range (exponent-field add);
@@ -162,7 +170,10 @@ __device__ __forceinline__ double scale2(double x, int e) {
   const int ex = (hi >> 20) & 0x7ff;
   if (e == 0 || x == 0.0) return x;
   if (ex > 0 && ex < 0x7ff && ex + e > 0 && ex + e < 0x7ff) return __hiloint2double(hi + (e << 20), __double2loint(x));
-  return mul_pow2_slow(x, e);
+  // subnormal operand or result (rare): two exact power-of-two factors
+  const int e1 = e / 2, e2 = e - e1;
+  return x * __longlong_as_double((long long)((unsigned long long)(e1 + 1023) << 52)) *
+         __longlong_as_double((long long)((unsigned long long)(e2 + 1023) << 52));
 }
 
 // Truncation of x onto fp32 with the last bit set when bits were dropped ("round to odd").
