@@ -55,7 +55,7 @@ class Opts(C.Structure):
         ("w1", C.c_double), ("w2", C.c_double), ("w3", C.c_double), ("lr", C.c_double),
         ("gamma", C.c_double), ("eps0", C.c_double), ("eps_floor", C.c_double), ("seed", C.c_uint64),
         ("unvisited_fallback", C.c_int), ("true_res_every", C.c_int), ("true_res_at_conv", C.c_int),
-        ("op_mask", C.c_int * 4), ("on_breakdown", C.c_int), ("mlp_hidden", C.c_int),
+        ("op_mask", C.c_int * 4), ("on_breakdown", C.c_int), ("mlp_hidden", C.c_int), ("precond", C.c_int),
     ]
 
 
@@ -163,12 +163,13 @@ class Options:
     op_mask: tuple = (0, 0, 0, 0)
     on_breakdown: int = 0
     mlp_hidden: int = 64
+    precond: int = 0
 
     def c(self) -> Opts:
         o = Opts()
         for name in ("b_bins", "r_bins", "t_bin", "min_k", "eps_min", "w1", "w2", "w3", "lr", "gamma",
                      "eps0", "eps_floor", "seed", "unvisited_fallback", "true_res_every",
-                     "true_res_at_conv", "on_breakdown", "mlp_hidden"):
+                     "true_res_at_conv", "on_breakdown", "mlp_hidden", "precond"):
             setattr(o, name, getattr(self, name))
         for j in range(4):
             o.op_mask[j] = int(self.op_mask[j])
@@ -347,10 +348,12 @@ def solve(opts: Options, A, b, tau: float, max_iter: int, *, fixed=None, sched=N
     trans = np.zeros(max(max_iter, 1), dtype=TRANS_DTYPE) if want_trans else None
     ntrans = np.zeros(1, dtype=np.int32)
     res = Result()
-    lib().orc_run(C.byref(o), n, _p(rp), _p(ci), _p(val), _p(b), _p(x), tau, max_iter, C.byref(P),
-                  MODE_TRAIN if train else MODE_INFER, episode, lane, eps, _p(trans), _p(ntrans),
-                  _p(hist), _p(feats), C.byref(res))
+    rc = lib().orc_run(C.byref(o), n, _p(rp), _p(ci), _p(val), _p(b), _p(x), tau, max_iter, C.byref(P),
+                       MODE_TRAIN if train else MODE_INFER, episode, lane, eps, _p(trans), _p(ntrans),
+                       _p(hist), _p(feats), C.byref(res))
     del keep
+    if rc < 0:
+        raise ValueError("Jacobi preconditioning needs a positive diagonal entry in every row")
     hist = hist[: res.nrec]
     return SolveOut(x, res.outcome, res.iters, res.rho_rec, res.rho_true, hist,
                     feats[: len(hist) + 1] if feats is not None else None,

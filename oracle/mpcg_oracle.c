@@ -148,6 +148,9 @@ typedef struct {
   int on_breakdown;       /* 1: an inference solve that breaks down restarts once from
                              r = b - A x, p = r (fp64) and finishes in fp64            */
   int mlp_hidden;         /* MLP hidden width (64)                                     */
+  int precond;            /* 0: M = I (the hot path); 1: Jacobi, M = diag(A): op 2 becomes
+                             z = fl_p2(r_i d_i) with d_i = 1 / a_ii in fp64, and the
+                             initial and restart directions and sigmas use z = d r      */
 } orc_opts;
 
 enum { ORC_POL_FIXED = 0, ORC_POL_SCHEDULE = 1, ORC_POL_QTABLE = 2, ORC_POL_MLP = 3 };
@@ -594,14 +597,33 @@ int orc_run(const orc_opts* o, int n, const int32_t* rp, const int32_t* ci, cons
   memset(&fs, 0, sizeof(fs));
   if (ntrans) *ntrans = 0;
 
-  /* Initialisation (Algorithms 1 and 2): r_0 = b - A x_0, z_0 = M^-1 r_0 with M = I,
-   * p_0 = z_0, sigma_0 = r_0^T z_0, b_norm = ||b||_2; all in fp64. */
+  /* M^-1 as the fp64 reciprocals of the diagonal (Jacobi) or the identity. A row without a
+   * positive diagonal entry makes Jacobi undefined: the solve is refused (return -1). */
+  double* dinv = malloc(nb);
+  for (int i = 0; i < n; ++i) dinv[i] = 1.0;
+  if (o->precond == 1) {
+    for (int i = 0; i < n; ++i) {
+      double d = 0.0;
+      for (int e = rp[i]; e < rp[i + 1]; ++e)
+        if (ci[e] == i) d = val[e];
+      if (!(d > 0.0)) {
+        free(r); free(p); free(q); free(z); free(rt); free(h1); free(h2); free(qout); free(dinv);
+        return -1;
+      }
+      dinv[i] = 1.0 / d;
+    }
+  }
+  /* Initialisation (Algorithms 1 and 2): r_0 = b - A x_0, z_0 = M^-1 r_0, p_0 = z_0,
+   * sigma_0 = r_0^T z_0, b_norm = ||b||_2; all in fp64. */
   double bb = 0.0;
   for (int i = 0; i < n; ++i) bb += b[i] * b[i];
   double bnorm = sqrt(bb);
   double rr0 = orc_true_residual(n, rp, ci, val, b, x, r);
-  for (int i = 0; i < n; ++i) p[i] = r[i];
-  double sigma = rr0;
+  double sigma = 0.0;
+  for (int i = 0; i < n; ++i) {
+    p[i] = o->precond == 1 ? r[i] * dinv[i] : r[i];
+    sigma += r[i] * p[i];
+  }
   double rho = bnorm > 0 ? sqrt(rr0) / bnorm : 0.0;
   int outcome = ORC_MAX_ITER, iters = max_iter, nrec = 0;
   if (n == 0 || bnorm == 0.0) {
@@ -730,9 +752,9 @@ int orc_run(const orc_opts* o, int n, const int32_t* rp, const int32_t* ci, cons
         rho = rho_new;
         stop = 1;
       } else {
-        /* z_{k+1} = fl_p2(M^-1 r_{k+1}) with M = I; sigma_{k+1} = fl_p4(r^T z);
-         * beta_k = sigma_{k+1} / sigma_k (fp64). */
-        for (int i = 0; i < n; ++i) z[i] = orc_chop(r[i], fmt[1]);
+        /* z_{k+1} = fl_p2(M^-1 r_{k+1}) (M = I, or the fp64 product r_i d_i for Jacobi,
+         * rounded once); sigma_{k+1} = fl_p4(r^T z); beta_k = sigma_{k+1} / sigma_k (fp64). */
+        for (int i = 0; i < n; ++i) z[i] = orc_chop(o->precond == 1 ? r[i] * dinv[i] : r[i], fmt[1]);
         double sigma_new = orc_dot(n, r, z, fmt[3]);
         /* READING: after r was replaced by b - A x the old direction no longer matches the
          * residual history, so the iteration restarts with beta = 0 (p_{k+1} = z_{k+1}). */
@@ -764,11 +786,14 @@ int orc_run(const orc_opts* o, int n, const int32_t* rp, const int32_t* ci, cons
     }
     if (stop && outcome == ORC_BREAKDOWN && mode == ORC_MODE_INFER && o->on_breakdown && !locked) {
       /* READING (extension): restart from the current x (x_k after a curvature breakdown,
-       * x_{k+1} after a later one) with r = b - A x, p = r, sigma = r^T r, every operation
+       * x_{k+1} after a later one) with r = b - A x, p = M^-1 r, sigma = r^T M^-1 r, every operation
        * in fp64 from here on; iteration k counts as done. */
       double nt = orc_true_residual(n, rp, ci, val, b, x, r);
-      for (int i = 0; i < n; ++i) p[i] = r[i];
-      sigma = nt;
+      sigma = 0.0;
+      for (int i = 0; i < n; ++i) {
+        p[i] = o->precond == 1 ? r[i] * dinv[i] : r[i];
+        sigma += r[i] * p[i];
+      }
       rho = sqrt(nt) / bnorm;
       locked = 1;
       restarts += 1;
@@ -811,7 +836,7 @@ int orc_run(const orc_opts* o, int n, const int32_t* rp, const int32_t* ci, cons
     res->rho_rec = bnorm > 0 ? sqrt(rr) / bnorm : 0.0;
   }
   free(r); free(p); free(q); free(z); free(rt);
-  free(h1); free(h2); free(qout);
+  free(h1); free(h2); free(qout); free(dinv);
   return outcome;
 }
 

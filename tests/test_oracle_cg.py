@@ -253,3 +253,92 @@ def test_true_residual_replacement_restores_accuracy():
     checked = O.solve(_opts(true_res_at_conv=1), A, b, 1e-8, 1000, sched=sched)
     assert checked.outcome == O.CONVERGED and checked.rho_true < 1e-8
     assert plain.rho_true >= checked.rho_true or plain.rho_true < 1e-8
+
+
+# ---- Jacobi preconditioning (op 2 with M = diag(A)) ------------------------------------
+
+def _scaled(A):
+    """D^-1/2 A D^-1/2 for a CSR matrix with positive diagonal D."""
+    n, rp, ci, val = A
+    D = np.zeros(n)
+    for i in range(n):
+        for e in range(rp[i], rp[i + 1]):
+            if ci[e] == i:
+                D[i] = val[e]
+    s = 1.0 / np.sqrt(D)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    return (n, rp.copy(), ci.copy(), val * s[rows] * s[ci]), s
+
+
+def test_jacobi_pcg_is_cg_on_the_symmetrically_scaled_system():
+    """Jacobi-preconditioned CG on A x = b and plain CG on (D^-1/2 A D^-1/2) y = D^-1/2 b
+    produce the same iterates x_k = D^-1/2 y_k (exact arithmetic); in fp64 they agree to
+    rounding after every number of steps."""
+    rng = np.random.default_rng(5)
+    A = I.diffusion_varcoef((7, 6, 5), 2.0, rng)
+    _, b = I.rhs_from_xstar(A, rng)
+    As, s = _scaled(A)
+    for k in (1, 3, 8, 20):
+        xo = O.solve(_opts(precond=1), A, b, 1e-30, k, fixed=(4, 4, 4, 4)).x
+        ys = O.solve(_opts(), As, b * s, 1e-30, k, fixed=(4, 4, 4, 4)).x
+        assert np.allclose(xo, ys * s, rtol=1e-9, atol=1e-12 * np.abs(xo).max())
+
+
+def test_jacobi_on_a_diagonal_matrix_converges_in_one_step():
+    """M = A: z_0 = A^-1 b is the solution and the first step reaches it."""
+    n = 12
+    d = np.linspace(0.5, 40.0, n)
+    A = (n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), d)
+    b = np.arange(1.0, n + 1.0)
+    out = O.solve(_opts(precond=1), A, b, 1e-12, 5, fixed=(4, 4, 4, 4))
+    assert out.outcome == O.CONVERGED and out.iters == 1
+    assert np.allclose(out.x, b / d, rtol=1e-15)
+    plain = O.solve(_opts(), A, b, 1e-12, 50, fixed=(4, 4, 4, 4))
+    assert plain.iters > 1
+
+
+def test_jacobi_with_power_of_two_diagonal_is_plain_cg_bit_for_bit():
+    """The 2D Poisson matrix has 4 on the diagonal: M = 4 I scales z, p and sigma by exact
+    powers of two, so every iterate and residual equals plain CG's exactly."""
+    A, b, _ = I.cfg_poisson32()
+    o1 = O.solve(_opts(precond=1), A, b, 1e-10, 200, fixed=(4, 4, 4, 4))
+    o0 = O.solve(_opts(), A, b, 1e-10, 200, fixed=(4, 4, 4, 4))
+    assert o1.iters == o0.iters
+    assert np.array_equal(o1.x, o0.x)
+    assert np.array_equal(o1.hist["rho"], o0.hist["rho"])
+
+
+def test_jacobi_reduces_iterations_on_variable_coefficients():
+    """Coefficients varying over orders of magnitude: diagonal scaling removes most of the
+    ill-conditioning that comes from the coefficient contrast."""
+    rng = np.random.default_rng(8)
+    A = I.diffusion_varcoef((10, 10, 10), 2.5, rng)
+    _, b = I.rhs_from_xstar(A, rng)
+    o0 = O.solve(_opts(), A, b, 1e-8, 5000, fixed=(4, 4, 4, 4))
+    o1 = O.solve(_opts(precond=1), A, b, 1e-8, 5000, fixed=(4, 4, 4, 4))
+    assert o0.outcome == o1.outcome == O.CONVERGED
+    assert o1.iters < 0.7 * o0.iters
+
+
+def test_jacobi_low_precision_z_is_the_rounded_fp64_product():
+    """With p2 = fp16 the first direction after the start is z_1 = fl_16(r_1 d) (one rounding
+    of the fp64 product): a one-step solve recovers it from p_1 = z_1 + beta_0 p_0."""
+    rng = np.random.default_rng(9)
+    A = I.diffusion_varcoef((5, 5, 4), 1.0, rng)
+    _, b = I.rhs_from_xstar(A, rng)
+    n, rp, ci, val = A
+    out = O.solve(_opts(precond=1), A, b, 1e-30, 1, fixed=(4, 0, 4, 4))
+    h = out.hist[0]
+    D = np.array([val[rp[i]:rp[i + 1]][ci[rp[i]:rp[i + 1]] == i][0] for i in range(n)])
+    dinv = 1.0 / D
+    r0 = b.copy()
+    p0 = r0 * dinv
+    r1 = r0 - h["alpha"] * np.asarray(O.spmv(A, 4, p0))
+    z1 = O.chop(r1 * dinv, O.FP16)
+    assert h["sigma"] == pytest.approx(float(np.dot(r1, z1)), rel=1e-12)
+
+
+def test_jacobi_refuses_a_row_without_positive_diagonal():
+    A = _csr_from_dense(np.array([[2.0, 1.0], [1.0, 0.0]]))
+    with pytest.raises(ValueError, match="positive diagonal"):
+        O.solve(_opts(precond=1), A, np.ones(2), 1e-8, 10, fixed=(4, 4, 4, 4))
