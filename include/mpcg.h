@@ -121,6 +121,11 @@ typedef struct {
                             * start to end), 2 = lockstep (every CTA works on a slice of
                             * every unfinished system at every phase; slices re-cut as
                             * systems finish)                                            */
+  int32_t precond;         /* 0: M = I (op 2 is z = fl_p2(r)); 1: Jacobi, M = diag(A): op 2
+                            * is z = fl_p2(r_i d_i) with d_i = 1 / a_ii in fp64, and the
+                            * first and restart directions are p = M^-1 r. Solves of a
+                            * matrix with a row lacking a positive diagonal entry fail
+                            * with MPCG_ERR_INVALID_ARG.                                  */
 } mpcg_options;
 
 /* Result of one solve. */

@@ -89,7 +89,8 @@ struct mpcg_ctx_s {
 struct mpcg_matrix_s {
   mpcg_ctx_t ctx = nullptr;
   DevMatrix dm;
-  DevBuf rp, ci, v64, v32, vtf, v16, vbf, v16r, vbfr, rexp;
+  DevBuf rp, ci, v64, v32, vtf, v16, vbf, v16r, vbfr, rexp, dinv;
+  bool diag_ok = false;             // every row has a positive diagonal entry (Jacobi defined)
   int device = 0;
   double mean = 0, maxr = 0, cv = 0;
   long long win[4] = {0, 0, 0, 0};  // largest nonzero count of 256, 128, 64, 32 consecutive rows
@@ -170,6 +171,7 @@ mpcg_status build_optview(mpcg_ctx_t ctx, const mpcg_options& o, OptView& v) {
   if (!(o.eps_min > 0.0 && o.eps_min < 1.0)) return fail(ctx, MPCG_ERR_INVALID_ARG, "eps_min must be in (0, 1)");
   if (o.mlp_hidden < 1 || o.mlp_hidden > kMaxHidden) return fail(ctx, MPCG_ERR_INVALID_ARG, "mlp_hidden must be in [1, %d]", kMaxHidden);
   if (o.batch_mode < 0 || o.batch_mode > 2) return fail(ctx, MPCG_ERR_INVALID_ARG, "batch_mode must be 0, 1 or 2");
+  if (o.precond < 0 || o.precond > 1) return fail(ctx, MPCG_ERR_INVALID_ARG, "precond must be 0 or 1");
   for (int a = 0; a < o.nprec; ++a)
     if (!valid_fmt(o.precs[a])) return fail(ctx, MPCG_ERR_INVALID_ARG, "precs[%d] = %d is not a format code", a, o.precs[a]);
   if (o.unvisited_fallback != -1 && !valid_fmt(o.unvisited_fallback))
@@ -206,6 +208,7 @@ mpcg_status build_optview(mpcg_ctx_t ctx, const mpcg_options& o, OptView& v) {
   v.true_at_conv = o.true_res_at_conv;
   v.warm_start = o.warm_start;
   v.on_breakdown = o.on_breakdown;
+  v.precond = o.precond;
   for (int j = 0; j < 4; ++j) {
     const unsigned all = (1u << o.nprec) - 1u;
     const unsigned m = o.op_mask[j] ? ((unsigned)o.op_mask[j] & all) : all;
@@ -328,6 +331,11 @@ mpcg_status fill_policy(mpcg_ctx_t ctx, mpcg_policy_t P, PolicyView& pv) {
 mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, mpcg_policy_t policy, int train,
                        int trans_cap, int force_team, cudaStream_t s, int feat_cap = 0) {
   const int nsys = (int)in.size();
+  if (ctx->opt.precond == 1)
+    for (int i = 0; i < nsys; ++i)
+      if (!in[i].A->diag_ok)
+        return fail(ctx, MPCG_ERR_INVALID_ARG,
+                    "system %d: Jacobi preconditioning needs a positive diagonal entry in every row", i);
   bool stream_shape = false;
   for (int i = 0; i < nsys; ++i) stream_shape = stream_shape || uses_stream(in[i].A->dm);
   const int grid = ctx->nsm * (stream_shape ? ctx->occ_s : ctx->occ);
@@ -382,6 +390,7 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
     DevSys& d = pl.hsys[i];
     memset(&d, 0, sizeof(d));
     d.A = in[i].A->dm;
+    d.A.dinv = ctx->opt.precond == 1 ? in[i].A->dinv.as<double>() : nullptr;
     const int n = d.A.n;
     d.b = in[i].b;
     d.x = in[i].x;
@@ -571,6 +580,7 @@ void mpcg_options_default(mpcg_options* o) {
   o->on_breakdown = 0;
   o->mlp_hidden = 64;
   o->batch_mode = 0;
+  o->precond = 0;
 }
 
 mpcg_status mpcg_create(mpcg_ctx_t* out, int device, const mpcg_options* opt) {
@@ -690,6 +700,19 @@ mpcg_status mpcg_matrix_create(mpcg_ctx_t ctx, const mpcg_csr* A, mpcg_matrix_t*
   d.rexp = M->rexp.as<short>();
   CK(ctx, launch_convert(d, M->v32.as<float>(), M->vtf.as<float>(), M->v16.as<__half>(), M->vbf.as<__nv_bfloat16>(),
                          M->v16r.as<__half>(), M->vbfr.as<__nv_bfloat16>(), M->rexp.as<short>(), s));
+  // Jacobi: fp64 reciprocals of the diagonal, and whether every row has a positive one.
+  {
+    DevBuf bad;
+    CK(ctx, M->dinv.ensure(8 * (size_t)std::max(n, 1)));
+    CK(ctx, bad.ensure(sizeof(unsigned)));
+    CK(ctx, cudaMemsetAsync(bad.p, 0, sizeof(unsigned), s));
+    CK(ctx, launch_jacobi_diag(n, d.rp, d.ci, d.v64, M->dinv.as<double>(), bad.as<unsigned>(), s));
+    unsigned hb = 0;
+    CK(ctx, cudaMemcpyAsync(&hb, bad.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(ctx, cudaStreamSynchronize(s));
+    M->diag_ok = hb == 0;
+    M->bytes += 8LL * n;
+  }
   // Row statistics (host) and static features of the MLP policy.
   std::vector<int> hrp((size_t)n + 1);
   CK(ctx, cudaMemcpyAsync(hrp.data(), M->rp.p, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToHost, s));
@@ -1531,6 +1554,8 @@ mpcg_status mpcg_solve_noalloc(mpcg_ctx_t ctx, mpcg_matrix_t A, const double* b,
   if (n > 0 && (!b || !x)) return fail(ctx, MPCG_ERR_INVALID_ARG, "b or x is NULL");
   if (n > 0 && (!is_device_ptr(b) || !is_device_ptr(x)))
     return fail(ctx, MPCG_ERR_INVALID_ARG, "mpcg_solve_noalloc needs device pointers for b and x");
+  if (ctx->opt.precond == 1 && !A->diag_ok)
+    return fail(ctx, MPCG_ERR_INVALID_ARG, "Jacobi preconditioning needs a positive diagonal entry in every row");
   if (!(tol >= 0.0) || max_iter < 0) return fail(ctx, MPCG_ERR_INVALID_ARG, "tol must be >= 0 and max_iter >= 0");
   if (A->ctx != ctx || policy->ctx != ctx) return fail(ctx, MPCG_ERR_INVALID_ARG, "objects belong to another context");
   if (ctx->device < 0 || ctx->device >= 64) return fail(ctx, MPCG_ERR_INVALID_ARG, "device ordinal out of range");
@@ -1573,6 +1598,7 @@ mpcg_status mpcg_solve_noalloc(mpcg_ctx_t ctx, mpcg_matrix_t A, const double* b,
   DevSys hs;
   memset(&hs, 0, sizeof(hs));
   hs.A = A->dm;
+  hs.A.dinv = ctx->opt.precond == 1 ? A->dinv.as<double>() : nullptr;
   hs.b = b;
   hs.x = x;
   hs.r = (double*)take(8 * (size_t)n);

@@ -376,27 +376,34 @@ __device__ void choose_action(const Launch& L, const DevSys& S, SysState* st, in
 // Row phases
 // ----------------------------------------------------------------------------------------
 
-// sigma term of row i: fl_p4(r_i) fl_p4(z_i) with z_i = fl_p2(r_i): a DFMA when p4 = fp64,
-// otherwise the compensated fp32 pair. Roundings that are identities (p4's value set
-// contains p2's) are skipped.
-__device__ __forceinline__ void sigma_term(double ri, int p2, int p4, DotAcc& sg) {
+// M^-1 r_i in fp64: r_i times the fp64 reciprocal of the diagonal when the launch runs the
+// Jacobi preconditioner (dinv set), r_i itself otherwise (M = I).
+__device__ __forceinline__ double minv_r(const DevSys& S, int i, double ri) {
+  return S.A.dinv ? ri * __ldg(S.A.dinv + i) : ri;
+}
+
+// sigma term of row i: fl_p4(r_i) fl_p4(z_i) with z_i = fl_p2(w_i), w_i = M^-1 r_i: a DFMA
+// when p4 = fp64, otherwise the compensated fp32 pair. Roundings that are identities
+// (p4's value set contains p2's) are skipped.
+__device__ __forceinline__ void sigma_term(double ri, double wi, int p2, int p4, DotAcc& sg) {
   if (p4 == F64) {
-    const double z = (p2 == F64) ? ri : f2d(round_d2f(ri, p2));
+    const double z = (p2 == F64) ? wi : f2d(round_d2f(wi, p2));
     sg.d = fma(ri, z, sg.d);
   } else {
     const float a = round_d2f(ri, p4);
     float b;
-    if (p2 == F64 || base_fmt(p2) == base_fmt(p4)) b = a;
+    if (wi == ri && (p2 == F64 || base_fmt(p2) == base_fmt(p4))) b = a;
+    else if (p2 == F64) b = round_d2f(wi, p4);
     else {
-      const float zf = round_d2f(ri, p2);
+      const float zf = round_d2f(wi, p2);
       b = contains_fmt(p4, p2) ? zf : round_f2f(zf, p4);
     }
     dot_low(sg, a, b, p4);
   }
 }
 
-// z = fl_p2(r) as fp64.
-__device__ __forceinline__ double z_of(double ri, int p2) { return p2 == F64 ? ri : f2d(round_d2f(ri, p2)); }
+// z = fl_p2(w) as fp64, w = M^-1 r.
+__device__ __forceinline__ double z_of(double wi, int p2) { return p2 == F64 ? wi : f2d(round_d2f(wi, p2)); }
 
 // Element i of q (stored in p1's format) as fp64, times 2^e_i for the row-scaled formats.
 __device__ __forceinline__ double load_q(const DevSys& S, int i, int p1) {
@@ -440,9 +447,13 @@ __device__ void true_res_vec(const DevSys& S, Rows R, int p2, int p4, bool copy_
     if (lane == 0) {
       const double ri = __ldg(S.b + row) - acc;
       S.r[row] = ri;
-      if (copy_p) S.p[row] = ri;
+      const double wi = minv_r(S, row, ri);
+      if (copy_p) {  // restart direction p = M^-1 r, sigma = r^T M^-1 r in fp64
+        S.p[row] = wi;
+        sg.d = fma(ri, wi, sg.d);
+      }
       rr = fma(ri, ri, rr);
-      if (p2 >= 0) sigma_term(ri, p2, p4, sg);
+      if (p2 >= 0) sigma_term(ri, wi, p2, p4, sg);
     }
   }
 }
@@ -533,12 +544,13 @@ __device__ __forceinline__ bool restart_ok(const Launch& L, const SysState* st) 
 }
 
 // After the initial phase: ||b||, rho_0, sigma_0 = r_0^T r_0, action of iteration 0.
-__device__ void step_init(const Launch& L, const DevSys& S, SysState* st, double bb, double rr, Smem& sm) {
+__device__ void step_init(const Launch& L, const DevSys& S, SysState* st, double bb, double rr, double sig,
+                          Smem& sm) {
   if (threadIdx.x == 0) {
     const double bnorm = sqrt(bb);
     st->bnorm = bnorm;
     st->rho = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
-    st->sigma = rr;
+    st->sigma = sig;
     st->k = 0;
     st->alpha = 0.0;
     st->beta = 0.0;
@@ -762,7 +774,7 @@ __device__ void step_T(const Launch& L, const DevSys& S, SysState* st, double rr
 
 // After the fp64 restart's residual recomputation (r = b - A x, p = r): iteration k counts
 // as done; sigma = ||r||^2, every later operation in fp64; stop test as after any iteration.
-__device__ void step_restart(const Launch& L, const DevSys& S, SysState* st, double rr, Smem& sm) {
+__device__ void step_restart(const Launch& L, const DevSys& S, SysState* st, double rr, double sig, Smem& sm) {
   if (threadIdx.x == 0) {
     sm.need_action = 0;
     const double rho = sqrt(rr) / st->bnorm;
@@ -770,7 +782,7 @@ __device__ void step_restart(const Launch& L, const DevSys& S, SysState* st, dou
     st->fp64_lock = 1;
     st->n_restart += 1;
     st->n_true += 1;
-    st->sigma = rr;
+    st->sigma = sig;
     st->beta = 0.0;
     st->rho = rho;
     for (int h = 8; h > 0; --h) st->rho_hist[h] = st->rho_hist[h - 1];
@@ -894,7 +906,7 @@ __device__ __forceinline__ void phase_b_rows(const DevSys& S, Rows R, double alp
         const double ri = fma(-alpha, qd, ro[u]);
         S.r[i] = ri;
         rr = fma(ri, ri, rr);
-        if (!sig_rr) sigma_term(ri, p2, p4, sg);
+        if (!sig_rr) sigma_term(ri, minv_r(S, i, ri), p2, p4, sg);
       }
     }
   }
@@ -921,7 +933,8 @@ __device__ __forceinline__ void phase_c_rows(const DevSys& S, Rows R, double alp
       const int i = i0 + u * kThreads;
       if (i < R.r1) {
         S.x[i] = fma(alpha, pv[u], xv[u]);
-        const double z = zlow ? f2d(round_d2f(rv[u], p2)) : rv[u];
+        const double w = minv_r(S, i, rv[u]);
+        const double z = zlow ? f2d(round_d2f(w, p2)) : w;
         const double pn = fma(beta, pv[u], z);
         S.p[i] = pn;
         if constexpr (sizeof(PT) != 8) ((PT*)S.plow)[i] = to_storage<PT>(round_d2f(pn, p1n));
@@ -949,7 +962,7 @@ __device__ __forceinline__ void phase_b_row(const DevSys& S, int i, double alpha
   const double ri = fma(-alpha, qd, S.r[i]);
   S.r[i] = ri;
   rr = fma(ri, ri, rr);
-  if (!sig_rr) sigma_term(ri, p2, p4, sg);
+  if (!sig_rr) sigma_term(ri, minv_r(S, i, ri), p2, p4, sg);
 }
 
 template <typename QT, bool SCALED>
@@ -998,8 +1011,8 @@ __device__ __forceinline__ void phase_b_pairs(const DevSys& S, Rows R, double al
         rr = fma(rn.x, rn.x, rr);
         rr = fma(rn.y, rn.y, rr);
         if (!sig_rr) {
-          sigma_term(rn.x, p2, p4, sg);
-          sigma_term(rn.y, p2, p4, sg);
+          sigma_term(rn.x, minv_r(S, 2 * j, rn.x), p2, p4, sg);
+          sigma_term(rn.y, minv_r(S, 2 * j + 1, rn.y), p2, p4, sg);
         }
       }
     }
@@ -1011,7 +1024,8 @@ __device__ __forceinline__ void phase_c_row(const DevSys& S, int i, double alpha
   const double pv = S.p[i];
   S.x[i] = fma(alpha, pv, S.x[i]);
   const double rv = S.r[i];
-  const double z = p2 != F64 ? f2d(round_d2f(rv, p2)) : rv;
+  const double w = minv_r(S, i, rv);
+  const double z = p2 != F64 ? f2d(round_d2f(w, p2)) : w;
   const double pn = fma(beta, pv, z);
   S.p[i] = pn;
   if constexpr (sizeof(PT) != 8) ((PT*)S.plow)[i] = to_storage<PT>(round_d2f(pn, p1n));
@@ -1052,8 +1066,9 @@ __device__ __forceinline__ void phase_c_pairs(const DevSys& S, Rows R, double al
         xn.x = fma(alpha, pv[u].x, xv[u].x);
         xn.y = fma(alpha, pv[u].y, xv[u].y);
         x2v[j] = xn;
-        const double za = zlow ? f2d(round_d2f(rv[u].x, p2)) : rv[u].x;
-        const double zb = zlow ? f2d(round_d2f(rv[u].y, p2)) : rv[u].y;
+        const double wa = minv_r(S, 2 * j, rv[u].x), wb = minv_r(S, 2 * j + 1, rv[u].y);
+        const double za = zlow ? f2d(round_d2f(wa, p2)) : wa;
+        const double zb = zlow ? f2d(round_d2f(wb, p2)) : wb;
         pn.x = fma(beta, pv[u].x, za);
         pn.y = fma(beta, pv[u].y, zb);
         p2v[j] = pn;
@@ -1118,11 +1133,17 @@ __device__ __noinline__ void phase_c(const DevSys& S, Rows R, double alpha, doub
 // fp64 restart after a breakdown: r = b - A x and p = r in fp64, then step_restart.
 __device__ bool restart64(const Launch& L, const TeamCtx& T, const DevSys& S, SysState* st, Rows R, Smem& sm) {
   double rr = 0.0;
-  DotAcc unused{0.0, 0.f, 0.f};
-  true_res_rows(S, R, -1, -1, true, rr, unused);
+  DotAcc sg{0.0, 0.f, 0.f};
+  true_res_rows(S, R, -1, -1, true, rr, sg);
   rr = cta_sum(rr, sm.red);
+  const double sp = cta_dot(sg, sm.red);
   write_partial(L, 0, rr);
-  return team_step(L, T, st, sm, [&] { step_restart(L, S, st, team_sum(L, T, 0, sm.red), sm); });
+  write_partial(L, 1, sp);
+  return team_step(L, T, st, sm, [&] {
+    const double trr = team_sum(L, T, 0, sm.red);
+    const double tsg = team_sum(L, T, 1, sm.red);
+    step_restart(L, S, st, trr, tsg, sm);
+  });
 }
 
 __device__ __forceinline__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& sm, const StreamCtx* sc) {
@@ -1136,29 +1157,35 @@ __device__ __forceinline__ bool solve_system(const Launch& L, const TeamCtx& T, 
   __syncthreads();
   const Rows R{sm.r0, sm.r1};
 
-  // ---- initialisation: x_0, r_0 = b - A x_0, p_0 = r_0, ||b||^2, sigma_0 = ||r_0||^2 ----
+  // ---- initialisation: x_0, r_0 = b - A x_0, p_0 = z_0 = M^-1 r_0, ||b||^2, ||r_0||^2,
+  //      sigma_0 = r_0^T z_0 ----
   {
     double bb = 0.0, rr = 0.0;
-    DotAcc unused{0.0, 0.f, 0.f};
+    DotAcc sg{0.0, 0.f, 0.f};
     for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
       const double bi = __ldg(S.b + i);
       bb = fma(bi, bi, bb);
       if (!o.warm_start) {
+        const double wi = minv_r(S, i, bi);
         S.x[i] = 0.0;
         S.r[i] = bi;
-        S.p[i] = bi;
+        S.p[i] = wi;
         rr = fma(bi, bi, rr);
+        sg.d = fma(bi, wi, sg.d);
       }
     }
-    if (o.warm_start) true_res_rows(S, R, -1, -1, true, rr, unused);
+    if (o.warm_start) true_res_rows(S, R, -1, -1, true, rr, sg);
     bb = cta_sum(bb, sm.red);
     rr = cta_sum(rr, sm.red);
+    const double sp = cta_dot(sg, sm.red);
     write_partial(L, 0, bb);
     write_partial(L, 1, rr);
+    write_partial(L, 2, sp);
     if (!team_step(L, T, st, sm, [&] {
           const double tb = team_sum(L, T, 0, sm.red);
           const double tr = team_sum(L, T, 1, sm.red);
-          step_init(L, S, st, tb, tr, sm);
+          const double ts = team_sum(L, T, 2, sm.red);
+          step_init(L, S, st, tb, tr, ts, sm);
         }))
       return false;
   }
@@ -1190,8 +1217,9 @@ __device__ __forceinline__ bool solve_system(const Launch& L, const TeamCtx& T, 
       {
         const double alpha = sm.bc.alpha;
         const int p1 = sm.bc.fmt[0], p2 = sm.bc.fmt[1], p4 = sm.bc.fmt[3];
-        // with z = r and an fp64 dot, sigma is ||r||^2 itself: one DFMA per row saved
-        const bool sig_rr = (p2 == F64 && p4 == F64);
+        // with z = r (no preconditioner) and an fp64 dot, sigma is ||r||^2 itself: one DFMA
+        // per row saved
+        const bool sig_rr = (p2 == F64 && p4 == F64 && !S.A.dinv);
         double rr = 0.0;
         DotAcc sg{0.0, 0.f, 0.f};
         phase_b(S, R, alpha, p1, p2, p4, sig_rr, rr, sg);
@@ -1257,7 +1285,7 @@ __device__ __forceinline__ bool solve_system(const Launch& L, const TeamCtx& T, 
         const int p1n = sm.bc.fmt[0];
         const int p2 = sm.bc.zfmt;
         for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
-          const double pn = z_of(S.r[i], p2);
+          const double pn = z_of(minv_r(S, i, S.r[i]), p2);
           S.p[i] = pn;
           if (p1n != F64) store_low(S.plow, i, pn, p1n);
         }
@@ -1432,23 +1460,27 @@ __device__ void lk_slice_rows(const Launch& L, int s, Rows R, int slot, Smem& sm
   switch (phase) {
     case PH_INIT: {
       double bb = 0.0, rr = 0.0;
-      DotAcc unused{0.0, 0.f, 0.f};
+      DotAcc sg{0.0, 0.f, 0.f};
       const bool warm = L.opt.warm_start != 0;
       for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
         const double bi = __ldg(S.b + i);
         bb = fma(bi, bi, bb);
         if (!warm) {
+          const double wi = minv_r(S, i, bi);
           S.x[i] = 0.0;
           S.r[i] = bi;
-          S.p[i] = bi;
+          S.p[i] = wi;
           rr = fma(bi, bi, rr);
+          sg.d = fma(bi, wi, sg.d);
         }
       }
-      if (warm) true_res_rows(S, R, -1, -1, true, rr, unused);
+      if (warm) true_res_rows(S, R, -1, -1, true, rr, sg);
       bb = cta_sum(bb, sm.red);
       rr = cta_sum(rr, sm.red);
+      const double sp = cta_dot(sg, sm.red);
       lk_partial(L, slot, 0, bb);
       lk_partial(L, slot, 1, rr);
+      lk_partial(L, slot, 2, sp);
       break;
     }
     case PH_PLOW: {
@@ -1465,7 +1497,7 @@ __device__ void lk_slice_rows(const Launch& L, int s, Rows R, int slot, Smem& sm
     }
     case PH_B: {
       const int p1 = sm.bc.fmt[0], p2 = sm.bc.fmt[1], p4 = sm.bc.fmt[3];
-      const bool sig_rr = (p2 == F64 && p4 == F64);
+      const bool sig_rr = (p2 == F64 && p4 == F64 && !S.A.dinv);
       double rr = 0.0;
       DotAcc sg{0.0, 0.f, 0.f};
       phase_b(S, R, sm.bc.alpha, p1, p2, p4, sig_rr, rr, sg);
@@ -1496,7 +1528,7 @@ __device__ void lk_slice_rows(const Launch& L, int s, Rows R, int slot, Smem& sm
     case PH_RZ: {
       const int p1n = sm.bc.fmt[0], p2 = sm.bc.zfmt;
       for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
-        const double pn = z_of(S.r[i], p2);
+        const double pn = z_of(minv_r(S, i, S.r[i]), p2);
         S.p[i] = pn;
         if (p1n != F64) store_low(S.plow, i, pn, p1n);
       }
@@ -1504,9 +1536,12 @@ __device__ void lk_slice_rows(const Launch& L, int s, Rows R, int slot, Smem& sm
     }
     case PH_R64: {
       double rr = 0.0;
-      DotAcc unused{0.0, 0.f, 0.f};
-      true_res_rows(S, R, -1, -1, true, rr, unused);
-      lk_partial(L, slot, 0, cta_sum(rr, sm.red));
+      DotAcc sg{0.0, 0.f, 0.f};
+      true_res_rows(S, R, -1, -1, true, rr, sg);
+      rr = cta_sum(rr, sm.red);
+      const double sp = cta_dot(sg, sm.red);
+      lk_partial(L, slot, 0, rr);
+      lk_partial(L, slot, 1, sp);
       break;
     }
     case PH_FINAL: {
@@ -1543,7 +1578,8 @@ __device__ void lk_step(const Launch& L, int s, Smem& sm) {
   switch (phase) {
     case PH_INIT: {
       const double tb = lk_sum(L, base, np, 0, sm), tr = lk_sum(L, base, np, 1, sm);
-      step_init(L, S, st, tb, tr, sm);
+      const double ts = lk_sum(L, base, np, 2, sm);
+      step_init(L, S, st, tb, tr, ts, sm);
       break;
     }
     case PH_A: step_A(L, S, st, lk_sum(L, base, np, 0, sm)); break;
@@ -1558,7 +1594,11 @@ __device__ void lk_step(const Launch& L, int s, Smem& sm) {
       step_T(L, S, st, trr, tsg, sm);
       break;
     }
-    case PH_R64: step_restart(L, S, st, lk_sum(L, base, np, 0, sm), sm); break;
+    case PH_R64: {
+      const double trr = lk_sum(L, base, np, 0, sm), tsg = lk_sum(L, base, np, 1, sm);
+      step_restart(L, S, st, trr, tsg, sm);
+      break;
+    }
     case PH_FINAL: step_final(L, S, st, s, lk_sum(L, base, np, 0, sm)); break;
     default: break;  // PH_PLOW, PH_X, PH_RZ: no scalar work
   }

@@ -42,6 +42,7 @@ struct DevMatrix {
   int lanes[8];             // lanes per row per format
   int tile_rows[8];         // stream schedule: rows per shared-memory tile (kThreads / lanes)
   int tile_bytes[8];        // stream schedule: bytes of a stage's value region (columns follow)
+  const double* dinv;       // Jacobi: 1 / a_ii in fp64 when the launch preconditions, else nullptr
 };
 
 // One transition of an exploration episode (Algorithm 1), recorded for the end-of-round merge.
@@ -122,7 +123,7 @@ struct OptView {
   int fallback_fmt;         // unvisited-row action (format code), -1 = argmax
   int fallback_idx;         // its index in precs (-1 if absent)
   int true_every, true_at_conv, warm_start, t_bin;
-  int on_breakdown, pad;
+  int on_breakdown, precond;
   int op_mask[4];           // allowed action indices per operation (all bits set = no restriction)
 };
 
@@ -192,6 +193,8 @@ cudaError_t launch_mlp_reduce_adam(const float* part, int nparts, long long np, 
                                    float* v, int t, float lr, const double* lpart, double* loss, cudaStream_t s);
 cudaError_t launch_mlp_sample(long long* idx, int B, long long count, unsigned long long seed, unsigned long long t,
                               cudaStream_t s);
+cudaError_t launch_jacobi_diag(int n, const int* rp, const int* ci, const double* v, double* dinv, unsigned* bad,
+                               cudaStream_t s);
 cudaError_t launch_row_features(int n, const int* rp, const int* ci, const double* v, unsigned long long* out,
                                 cudaStream_t s);
 cudaError_t launch_to_format(const double* x, void* xlow, int n, int f, cudaStream_t s);

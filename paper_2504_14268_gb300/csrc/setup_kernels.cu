@@ -167,6 +167,24 @@ __global__ void __launch_bounds__(kThreads) spmv_standalone(const DevSys S, int 
   spmv_rows(S, Rows{r01[0], r01[1]}, fmt, -1, nu, stream_stage > 0 ? &scx : nullptr);
 }
 
+// Jacobi preconditioner: dinv[i] = 1 / a_ii in fp64 (one thread per row); a row without a
+// positive diagonal entry sets *bad and gets dinv = 0.
+__global__ void jacobi_diag(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                            const double* __restrict__ v, double* dinv, unsigned* bad) {
+  for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < n;
+       row += (long long)gridDim.x * blockDim.x) {
+    double d = 0.0;
+    for (int e = rp[row]; e < rp[row + 1]; ++e)
+      if (ci[e] == row) d = v[e];
+    if (d > 0.0) {
+      dinv[row] = 1.0 / d;
+    } else {
+      dinv[row] = 0.0;
+      atomicOr(bad, 1u);
+    }
+  }
+}
+
 __global__ void qcopy_kernel(const double* __restrict__ Q, double* Qpriv, int nlanes, long long qsize) {
   const long long total = qsize * nlanes;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
@@ -245,6 +263,14 @@ cudaError_t launch_convert(const DevMatrix& A, float* v32, float* vtf, __half* v
   cudaGetLastError();
   convert_values<<<grid_for((long long)A.n * 32, kThreads), kThreads, 0, s>>>(A.n, A.rp, A.v64, v32, vtf, v16, vbf,
                                                                              v16r, vbfr, rexp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi_diag(int n, const int* rp, const int* ci, const double* v, double* dinv, unsigned* bad,
+                               cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  cudaGetLastError();
+  jacobi_diag<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, rp, ci, v, dinv, bad);
   return cudaGetLastError();
 }
 

@@ -45,6 +45,7 @@ class COptions(C.Structure):
         ("warm_start", C.c_int32), ("op_mask", C.c_int32 * 4), ("on_breakdown", C.c_int32),
         ("mlp_hidden", C.c_int32),
         ("batch_mode", C.c_int32),
+        ("precond", C.c_int32),
     ]
 
 
@@ -194,6 +195,7 @@ class Options:
     on_breakdown: int = 0
     mlp_hidden: int = 64
     batch_mode: int = 0
+    precond: int = 0
 
     def c(self) -> COptions:
         o = COptions()
