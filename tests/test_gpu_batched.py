@@ -16,6 +16,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TAU, CAP = 1e-8, 5000
+_CONVERGED = {}  # fraction of the diffusion systems converged, per preconditioner
 
 
 @pytest.fixture(scope="module")
@@ -72,6 +73,7 @@ def test_batched_graph_fp64(batch):
     print(f"fp64 CG: {len(bs) / t:.1f} solves/s ({t * 1e3:.1f} ms per batch), converged {conv:.3f}, "
           f"iterations median {np.median([r['iters'] for r in last]):.0f} max {max(r['iters'] for r in last)}")
     assert set(outcomes.tolist()) <= {0, 1}  # converged or capped
+    _CONVERGED["none"] = float(np.mean(outcomes[np.arange(len(sets)) % 3 != 2] == 0))
     assert [r["iters"] for r in first] == [r["iters"] for r in last]
     assert all(torch.equal(a, b) for a, b in zip(x1, x2))
     # the smallest system of each kind against the oracle's fp64 CG
@@ -117,3 +119,28 @@ def test_batched_graph_tabular_policy(batch):
     for r, (A, b, xs), x in zip(last, sets, x2):
         if r["outcome"] == 0:
             assert r["rel_res_true"] < TAU
+
+
+def test_batched_graph_fp64_jacobi(batch):
+    """The same batch with the Jacobi preconditioner (M = diag(A)): the diffusion systems'
+    coefficient contrast moves into the diagonal, so more systems reach the tolerance
+    within the cap than with M = I."""
+    M, ctx, sets, mats, bs = batch
+    c3 = M.Context(0, M.Options(true_res_at_conv=1, precond=1))
+    mats3 = []
+    for A, _, _ in sets:
+        m = c3.matrix((A[0], torch.as_tensor(A[1]).cuda(), torch.as_tensor(A[2]).cuda(), torch.as_tensor(A[3]).cuda()))
+        m.autotune(1)
+        mats3.append(m)
+    first, last, x1, x2, t = _run_graph(M, c3, mats3, bs, c3.policy_fixed((4, 4, 4, 4)))
+    outcomes = np.array([r["outcome"] for r in last])
+    conv = float(np.mean(outcomes == 0))
+    print(f"fp64 CG + Jacobi: {len(bs) / t:.1f} solves/s ({t * 1e3:.1f} ms per batch), converged {conv:.3f}, "
+          f"iterations median {np.median([r['iters'] for r in last]):.0f}")
+    assert [r["iters"] for r in first] == [r["iters"] for r in last]
+    assert set(outcomes.tolist()) <= {0, 1}
+    kinds = np.arange(len(sets)) % 3
+    conv_diff = float(np.mean(outcomes[kinds != 2] == 0))
+    print(f"diffusion systems converged: {conv_diff:.3f} with Jacobi, {_CONVERGED.get('none', float('nan')):.3f} without")
+    if "none" in _CONVERGED:
+        assert conv_diff >= _CONVERGED["none"]
