@@ -195,14 +195,16 @@ mpcg_status mpcg_matrix_info(mpcg_matrix_t A, mpcg_matrix_stats* info);
 /* Times every SpMV schedule on A for each value format (a few launches each) and keeps
  * the fastest (the autotuner). `reps` timed launches per candidate. Matrices with fewer
  * than 2^22 nonzeros, whose products are too short to time apart, keep the row-length rule
- * that mpcg_matrix_create applies (vector loads for rows up to ~32 nonzeros, K lanes with
- * about 24 nonzeros per lane beyond, a warp per row when a row exceeds 1024). */
+ * that mpcg_matrix_create applies (vector loads for a mean row length up to ~32 nonzeros,
+ * K lanes with about 24 nonzeros per lane beyond). */
 mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, void* stream);
 /* Forces the SpMV schedule of value format `fmt` (sched: 0 = sub-warp vector CSR with
  * `lanes` lanes per row (1, 2, 4, 8, 16 or 32); 1 = staged stream CSR, shared-memory tiles
  * filled by bulk copies, `lanes` = 1, 2 or 4 lanes per row; 2 = one thread per row reading
- * columns and values with 16-byte loads, `lanes` = 1). INVALID_ARG for other combinations
- * and for a stream tile that does not fit its shared-memory stage. */
+ * columns and values with 16-byte loads, `lanes` = 1). In schedules 0 and 2 a row longer
+ * than 1024 nonzeros (a power-law hub) is summed by a whole CTA after the CTA's other rows.
+ * INVALID_ARG for other combinations and for a stream tile that does not fit its
+ * shared-memory stage. */
 mpcg_status mpcg_matrix_set_schedule(mpcg_matrix_t A, int32_t fmt, int32_t sched, int32_t lanes);
 
 /* y = fl_fmt(A fl_fmt(x)) with the matrix's schedule for `fmt` (op 1 of Section 4.2 on its

@@ -524,14 +524,13 @@ mpcg_status finish_plan(mpcg_ctx_t ctx, Plan& pl, mpcg_result* res, cudaStream_t
 }
 
 // Row-length rule for the product schedule (from timings on GB300 across the workloads'
-// row lengths): one thread per row with 16-byte loads for rows of up to about 32 nonzeros;
-// longer rows get K lanes, K the power of two near mean / 24 (banded rows of 65 nonzeros:
-// 4 lanes, of 129: 8); a warp per row when some row exceeds 1024 nonzeros (power-law hubs).
+// row lengths): one thread per row with 16-byte loads for a mean row length of up to about
+// 32 nonzeros; longer rows get K lanes, K the power of two near mean / 24 (banded rows of 65
+// nonzeros: 4 lanes, of 129: 8). Rows over 1024 nonzeros (power-law hubs) are summed by the
+// whole CTA in both schedules.
 void default_schedule(mpcg_matrix_s* M) {
   int sched = SCHED_VECTOR, lanes = 1;
-  if (M->maxr > 1024) {
-    lanes = 32;
-  } else if (M->mean <= 32.0) {
+  if (M->mean <= 32.0) {
     sched = SCHED_VLOAD;
   } else {
     while (lanes < 32 && lanes * 24 < M->mean) lanes *= 2;

@@ -134,6 +134,18 @@ struct RowAcc {
       }
     }
   }
+  // Adds another partial accumulation of the same row (the cross-warp step of a row summed
+  // by the whole CTA).
+  __device__ __forceinline__ void merge(double os, double oc, double oa) {
+    if constexpr (COMP) {
+      float t;
+      two_sum(s, (float)os, s, t);
+      c = __fadd_rn(__fadd_rn(c, (float)oc), t);
+      a = __fadd_rn(__fadd_rn(a, (float)oa), fabsf(t));
+    } else {
+      s += (float)os;
+    }
+  }
   // Row sum rounded onto p1 (fp32 result). `exact` recomputes the row in fp64 when needed.
   template <class Exact>
   __device__ __forceinline__ float rounded(int p1, int len, Exact&& exact) const {
@@ -150,9 +162,10 @@ struct RowAcc {
       if (!isfinite(r)) return r;
       float below, above;
       half_gaps(r, p1, below, above);
-      // |exact - (s + c)| <= gamma_m a with m <= len + 2 log2(K) + 2 additions into c, inflated
-      // for the roundings of a and d
-      const float err = __fmul_rn(a, (float)(len + 16) * 1.2e-7f);
+      // |exact - (s + c)| <= gamma_m a with m <= len + 2 log2(K) + 2 additions into c (plus
+      // the cross-warp merges of a row summed by the whole CTA), inflated for the roundings of
+      // a and d
+      const float err = __fmul_rn(a, (float)(len + 32) * 1.2e-7f);
       const float d = __fadd_rn(__fsub_rn(hi, r), lo);
       const float slack = fabsf(d) * 1.2e-7f;
       if (d + err + slack < above && -d + err + slack < below) return r;
@@ -164,8 +177,9 @@ struct RowAcc {
 
 template <>
 struct RowAcc<double, false> {
-  double s = 0.0;
-  __device__ __forceinline__ void add(double a, double x) { s = fma(a, x, s); }
+  double s = 0.0, c = 0.0, a = 0.0;  // c and a unused (fp64 accumulation)
+  __device__ __forceinline__ void add(double av, double x) { s = fma(av, x, s); }
+  __device__ __forceinline__ void merge(double os, double, double) { s += os; }
   template <int K>
   __device__ __forceinline__ void reduce(unsigned mask) {
 #pragma unroll
@@ -249,6 +263,61 @@ __device__ __forceinline__ void stage_wait(const StreamCtx& sc, int stage) {
   }
 }
 
+// Rows longer than kLongRow nonzeros (power-law hubs) are summed by the whole CTA after its
+// other rows: up to kLongMax of them per CTA range are queued in shared memory; beyond that
+// the row's own lane group sums it as any other row.
+constexpr int kLongRow = 1024;
+constexpr int kLongMax = 32;
+struct LongRows {
+  int n;
+  int rows[kLongMax];
+  double part[3][kThreads / 32];
+};
+__device__ __forceinline__ LongRows& long_rows() {
+  __shared__ LongRows lr;
+  return lr;
+}
+// Empties the CTA's queue (all threads of the CTA call it).
+__device__ __forceinline__ void long_begin(LongRows& lr) {
+  if (threadIdx.x == 0) lr.n = 0;
+  __syncthreads();
+}
+// Queues a long row (one thread per row); false when the queue is full.
+__device__ __forceinline__ bool long_queue(LongRows& lr, int row) {
+  const int slot = atomicAdd(&lr.n, 1);
+  if (slot < kLongMax) lr.rows[slot] = row;
+  return slot < kLongMax;
+}
+// Sums the queued rows, each by all kThreads threads: a strided pass per thread, a warp
+// butterfly, then thread 0 merges the warps' partials and finishes the row.
+template <typename VT, bool COMP>
+__device__ void long_pass(LongRows& lr, const DevSys& S, const VT* __restrict__ vals, const VT* xin, int p1,
+                          int nu_fmt, DotAcc& nu) {
+  const int* __restrict__ rp = S.A.rp;
+  const int* __restrict__ ci = S.A.ci;
+  __syncthreads();
+  const int nl = lr.n < kLongMax ? lr.n : kLongMax;
+  for (int i = 0; i < nl; ++i) {
+    const int row = lr.rows[i];
+    const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
+    RowAcc<VT, COMP> acc;
+    for (int e = e0 + threadIdx.x; e < e1; e += kThreads) acc.add(__ldg(vals + e), xin[__ldg(ci + e)]);
+    acc.template reduce<32>(kFull);
+    if ((threadIdx.x & 31) == 0) {
+      lr.part[0][threadIdx.x >> 5] = acc.s;
+      lr.part[1][threadIdx.x >> 5] = acc.c;
+      lr.part[2][threadIdx.x >> 5] = acc.a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < kThreads / 32; ++w) acc.merge(lr.part[0][w], lr.part[1][w], lr.part[2][w]);
+      finish_row<VT, COMP>(S, row, e0, e1, acc, p1, nu_fmt, nu_fmt >= 0 ? S.p[row] : 0.0, nu,
+                           [&](int e) { return __ldg(vals + e); }, [&](int e) { return __ldg(ci + e); }, xin);
+    }
+    __syncthreads();
+  }
+}
+
 // Sub-warp vector CSR: K lanes per row, rows strided over the CTA, operands read from
 // global memory. The K lane accumulators are combined by an xor butterfly. With nu_fmt < 0
 // no nu partial is formed.
@@ -261,8 +330,14 @@ __device__ void spmv_vec(const DevSys& S, const VT* __restrict__ vals, const VT*
   const unsigned mask = (K == 32) ? kFull : (((1u << K) - 1u) << ((threadIdx.x & 31) & ~(K - 1)));
   const int* __restrict__ rp = S.A.rp;
   const int* __restrict__ ci = S.A.ci;
+  LongRows& lr = long_rows();
+  long_begin(lr);
   for (int row = R.r0 + grp; row < R.r1; row += NG) {
     const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
+    if (e1 - e0 > kLongRow) {
+      const bool queued = lane == 0 ? long_queue(lr, row) : false;
+      if (__shfl_sync(mask, queued, (threadIdx.x & 31) & ~(K - 1))) continue;
+    }
     RowAcc<VT, COMP> acc;
     for (int e = e0 + lane; e < e1; e += K) acc.add(__ldg(vals + e), xin[__ldg(ci + e)]);
     acc.template reduce<K>(mask);
@@ -270,6 +345,7 @@ __device__ void spmv_vec(const DevSys& S, const VT* __restrict__ vals, const VT*
       finish_row<VT, COMP>(S, row, e0, e1, acc, p1, nu_fmt, nu_fmt >= 0 ? S.p[row] : 0.0, nu,
                            [&](int e) { return __ldg(vals + e); }, [&](int e) { return __ldg(ci + e); }, xin);
   }
+  long_pass<VT, COMP>(lr, S, vals, xin, p1, nu_fmt, nu);
 }
 
 // Element k of a 16-byte word holding 16 / sizeof(VT) values (k known at compile time after
@@ -300,7 +376,7 @@ __device__ __forceinline__ double lane_of<double>(const int4& q, int k) {
 // aligned groups of G elements (G = 8 for 16-bit values, 4 otherwise; group starts rounded
 // down to a multiple of G, the arrays are padded so the last group stays in bounds), so a
 // thread issues one load per 4 columns and per 16 bytes of values instead of one per
-// element; elements of a group outside the row are skipped.
+// element; elements of a group outside the row are skipped. Long rows go to the CTA queue.
 template <typename VT, bool COMP>
 __device__ void spmv_vload(const DevSys& S, const VT* __restrict__ vals, const VT* xin, Rows R, int p1, int nu_fmt,
                            DotAcc& nu) {
@@ -317,6 +393,8 @@ __device__ void spmv_vload(const DevSys& S, const VT* __restrict__ vals, const V
     ne1 = __ldg(rp + row + 1);
     if (nu_fmt >= 0) npi = S.p[row];
   }
+  LongRows& lr = long_rows();
+  long_begin(lr);
   for (; row < R.r1; row += kThreads) {
     const int e0 = ne0, e1 = ne1;
     const double pi = npi;
@@ -325,6 +403,7 @@ __device__ void spmv_vload(const DevSys& S, const VT* __restrict__ vals, const V
       ne1 = __ldg(rp + row + kThreads + 1);
       if (nu_fmt >= 0) npi = S.p[row + kThreads];
     }
+    if (e1 - e0 > kLongRow && long_queue(lr, row)) continue;
     RowAcc<VT, COMP> acc;
     for (int g = e0 & ~(G - 1); g < e1; g += G) {
       int c[G];
@@ -355,6 +434,7 @@ __device__ void spmv_vload(const DevSys& S, const VT* __restrict__ vals, const V
     finish_row<VT, COMP>(S, row, e0, e1, acc, p1, nu_fmt, pi, nu, [&](int e) { return __ldg(vals + e); },
                          [&](int e) { return __ldg(ci + e); }, xin);
   }
+  long_pass<VT, COMP>(lr, S, vals, xin, p1, nu_fmt, nu);
 }
 
 // Staged stream CSR: the CTA's rows are cut into tiles of kThreads / K rows; the tile's

@@ -215,6 +215,34 @@ def ba_laplacian(n: int, m: int, shift: float, rng: np.random.Generator, block: 
     return _from_scipy(Lap)
 
 
+def hub_laplacian(n: int, hubs: int, deg_lo: int, deg_hi: int, shift: float, rng: np.random.Generator,
+                  hub_rows=None):
+    """Shifted Laplacian L + shift I of a ring of n nodes plus `hubs` hub nodes, each joined to
+    a log-uniform number in [deg_lo, deg_hi] of distinct random nodes: the few very long rows
+    of a power-law graph next to many short ones. `hub_rows` places the hubs (default: spread
+    evenly over the rows)."""
+    import scipy.sparse as sp
+
+    if hub_rows is None:
+        hub_rows = np.linspace(0, n - 1, hubs).astype(np.int64)
+    hub_rows = np.asarray(hub_rows, dtype=np.int64)
+    src = [np.arange(n), ]
+    dst = [(np.arange(n) + 1) % n]
+    degs = np.exp(rng.uniform(np.log(deg_lo), np.log(deg_hi), hub_rows.size)).astype(np.int64)
+    for h, d in zip(hub_rows, degs):
+        nb = rng.choice(n, size=int(min(d, n - 1)), replace=False)
+        nb = nb[nb != h]
+        src.append(np.full(nb.size, h))
+        dst.append(nb)
+    s_all = np.concatenate(src)
+    d_all = np.concatenate(dst)
+    Wm = sp.coo_matrix((np.ones(s_all.size), (s_all, d_all)), shape=(n, n)).tocsr()
+    Wm = ((Wm + Wm.T) > 0).astype(np.float64)
+    deg = np.asarray(Wm.sum(axis=1)).ravel()
+    Lap = sp.diags(deg + shift) - Wm
+    return _from_scipy(Lap)
+
+
 def random_spd_small(n: int, rng: np.random.Generator, density: float = 0.3, shift: float = 0.5):
     """Small sparse SPD matrix B B^T + shift I with a random sparse B (the construction of the
     paper's synthetic set, Section 5.1, at test sizes)."""
