@@ -128,6 +128,9 @@ def lib():
             L.orc_mlp_targets.argtypes = [vp, i, i, i, vp, vp, vp, d, vp, vp]
             L.orc_adam.argtypes = [vp, vp, vp, vp, i64, i, d, d, d, d]
             L.orc_static_features.argtypes = [i, vp, vp, vp, vp]
+            L.orc_ic0.restype = i
+            L.orc_ic0.argtypes = [i, vp, vp, vp, vp]
+            L.orc_ic0_apply.argtypes = [i, vp, vp, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -353,11 +356,40 @@ def solve(opts: Options, A, b, tau: float, max_iter: int, *, fixed=None, sched=N
                        _p(hist), _p(feats), C.byref(res))
     del keep
     if rc < 0:
-        raise ValueError("Jacobi preconditioning needs a positive diagonal entry in every row")
+        raise ValueError(_PRECOND_ERRORS.get(rc, f"solve refused ({rc})"))
     hist = hist[: res.nrec]
     return SolveOut(x, res.outcome, res.iters, res.rho_rec, res.rho_true, hist,
                     feats[: len(hist) + 1] if feats is not None else None,
                     trans[: int(ntrans[0])] if trans is not None else None)
+
+
+_PRECOND_ERRORS = {
+    -1: "Jacobi preconditioning needs a positive diagonal entry in every row",
+    -2: "incomplete Cholesky breaks down (a non-positive pivot)",
+    -3: "incomplete Cholesky needs a diagonal entry in every row, strictly increasing columns "
+        "and a symmetric pattern",
+}
+
+
+def ic0(A) -> np.ndarray:
+    """IC(0) factor in fp32 (orc_ic0): one value per stored entry, l_ij at (i, j) for j <= i
+    and l_ji at (i, j) for j > i. Raises ValueError on breakdown or an unusable pattern."""
+    n, rp, ci, val = _csr(A)
+    L = np.zeros(max(len(ci), 1), dtype=np.float32)
+    rc = lib().orc_ic0(n, _p(rp), _p(ci), _p(val), _p(L))
+    if rc < 0:
+        raise ValueError(_PRECOND_ERRORS[rc])
+    return L[: len(ci)]
+
+
+def ic0_apply(A, L, r) -> np.ndarray:
+    """M^-1 r for M = L L^T in fp32 (forward then backward substitution), returned in fp64."""
+    n, rp, ci, _ = _csr(A)
+    L = np.ascontiguousarray(L, dtype=np.float32)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    w = np.zeros(n)
+    lib().orc_ic0_apply(n, _p(rp), _p(ci), _p(L), _p(r), _p(w))
+    return w
 
 
 def train_sequential(opts: Options, A, b, tau: float, t_max: int, E: int, qt: QTable, ep_base: int = 0):

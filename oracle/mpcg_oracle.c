@@ -150,7 +150,10 @@ typedef struct {
   int mlp_hidden;         /* MLP hidden width (64)                                     */
   int precond;            /* 0: M = I (the hot path); 1: Jacobi, M = diag(A): op 2 becomes
                              z = fl_p2(r_i d_i) with d_i = 1 / a_ii in fp64, and the
-                             initial and restart directions and sigmas use z = d r      */
+                             initial and restart directions and sigmas use z = d r;
+                             2: IC(0) in fp32 (orc_ic0): z = fl_p2(L^-T L^-1 r) with
+                             the solves in fp32, the initial and restart directions
+                             z = L^-T L^-1 r unrounded beyond fp32                      */
 } orc_opts;
 
 enum { ORC_POL_FIXED = 0, ORC_POL_SCHEDULE = 1, ORC_POL_QTABLE = 2, ORC_POL_MLP = 3 };
@@ -515,6 +518,114 @@ double orc_true_residual(int n, const int32_t* rp, const int32_t* ci, const doub
 }
 
 /* ------------------------------------------------------------------------- */
+/* Incomplete Cholesky preconditioner in fp32 (Section 5's fixed-precision    */
+/* preconditioner M ~ A, p_fixed = fp32).                                     */
+/* ------------------------------------------------------------------------- */
+
+/* READING: Section 5 factors with an fp32 incomplete LU (drop tolerance 1e-4, fill factor 10).
+ * For SPD A this is taken as its symmetric, zero-fill form IC(0): M = L L^T with L lower
+ * triangular on the pattern of A's lower triangle and (L L^T)_ij = a_ij wherever a_ij is
+ * stored (Meijerink and van der Vorst 1977, the reference the paper cites for M). Every
+ * operation runs in fp32 (the paper's p_fixed), rows in order, each sum over increasing
+ * column index:
+ *   l_ij = (fl32(a_ij) - sum_{k<j} l_ik l_jk) / l_jj   for stored j < i,
+ *   l_ii = sqrt(fl32(a_ii) - sum_{k<i} l_ik^2),
+ * the sums running over the columns k stored in both rows i and j.
+ * Output layout: one fp32 per stored entry of A; position (i, j) holds l_ij for j <= i and
+ * the transposed factor value l_ji for j > i (row i of L^T).
+ * Returns 0; -2 for a non-positive or non-finite pivot (IC(0) breaks down; it exists for
+ * M-matrices but not for every SPD matrix); -3 when a row lacks its diagonal, its columns are
+ * not strictly increasing, or the pattern is not symmetric. */
+int orc_ic0(int n, const int32_t* rp, const int32_t* ci, const double* val, float* L) {
+  for (int i = 0; i < n; ++i) {
+    for (int32_t e = rp[i] + 1; e < rp[i + 1]; ++e)
+      if (ci[e] <= ci[e - 1]) return -3;
+  }
+  for (int i = 0; i < n; ++i) {
+    int32_t di = -1;
+    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+      const int j = ci[e];
+      if (j > i) break;
+      if (j == i) {
+        di = e;
+        break;
+      }
+      /* l_ij: merge row i's entries left of column j with row j's entries left of column j */
+      float s = (float)val[e];
+      int32_t a = rp[i], c = rp[j];
+      while (a < e && c < rp[j + 1] && ci[c] < j) {
+        if (ci[a] < ci[c]) {
+          ++a;
+        } else if (ci[a] > ci[c]) {
+          ++c;
+        } else {
+          s = s - L[a] * L[c];
+          ++a;
+          ++c;
+        }
+      }
+      int32_t dj = -1;
+      for (int32_t f = rp[j]; f < rp[j + 1]; ++f)
+        if (ci[f] == j) dj = f;
+      if (dj < 0) return -3;
+      L[e] = s / L[dj];
+    }
+    if (di < 0) return -3;
+    float s = (float)val[di];
+    for (int32_t e = rp[i]; e < di; ++e) s = s - L[e] * L[e];
+    if (!(s > 0.0f) || !isfinite(s)) return -2;
+    L[di] = sqrtf(s);
+  }
+  /* upper part: position (i, j), j > i, takes l_ji from row j; every off-diagonal entry
+   * needs its transposed partner */
+  for (int i = 0; i < n; ++i) {
+    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+      const int j = ci[e];
+      if (j == i) continue;
+      int32_t t = -1;
+      for (int32_t f = rp[j]; f < rp[j + 1]; ++f)
+        if (ci[f] == i) t = f;
+      if (t < 0) return -3;
+      if (j > i) L[e] = L[t];
+    }
+  }
+  return 0;
+}
+
+/* w = M^-1 r with M = L L^T from orc_ic0, in fp32: the input rounded to fp32, the forward
+ * substitution L y = fl32(r) in increasing row order, then the backward substitution
+ * L^T w = y in decreasing row order; each row's sum over its stored columns in increasing
+ * order, then one division by l_ii. w is returned as fp64 (its values are fp32 numbers). */
+void orc_ic0_apply(int n, const int32_t* rp, const int32_t* ci, const float* L, const double* r,
+                   double* w) {
+  float* y = malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+  float* z = malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+  for (int i = 0; i < n; ++i) {
+    float s = (float)r[i];
+    int32_t di = rp[i];
+    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+      if (ci[e] >= i) {
+        di = e;
+        break;
+      }
+      s = s - L[e] * y[ci[e]];
+    }
+    y[i] = s / L[di];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    float s = y[i];
+    int32_t di = rp[i];
+    for (int32_t e = rp[i]; e < rp[i + 1]; ++e)
+      if (ci[e] == i) di = e;
+    for (int32_t e = di + 1; e < rp[i + 1]; ++e) s = s - L[e] * z[ci[e]];
+    z[i] = s / L[di];
+  }
+  for (int i = 0; i < n; ++i) w[i] = (double)z[i];
+  free(y);
+  free(z);
+}
+
+/* ------------------------------------------------------------------------- */
 /* One episode: Algorithm 2 (inference) or Algorithm 1's inner loop (training). */
 /* ------------------------------------------------------------------------- */
 
@@ -600,6 +711,8 @@ int orc_run(const orc_opts* o, int n, const int32_t* rp, const int32_t* ci, cons
   /* M^-1 as the fp64 reciprocals of the diagonal (Jacobi) or the identity. A row without a
    * positive diagonal entry makes Jacobi undefined: the solve is refused (return -1). */
   double* dinv = malloc(nb);
+  int64_t nnz = n > 0 ? rp[n] : 0;
+  float* icl = malloc(sizeof(float) * (size_t)(nnz > 0 ? nnz : 1));
   for (int i = 0; i < n; ++i) dinv[i] = 1.0;
   if (o->precond == 1) {
     for (int i = 0; i < n; ++i) {
@@ -607,10 +720,18 @@ int orc_run(const orc_opts* o, int n, const int32_t* rp, const int32_t* ci, cons
       for (int e = rp[i]; e < rp[i + 1]; ++e)
         if (ci[e] == i) d = val[e];
       if (!(d > 0.0)) {
-        free(r); free(p); free(q); free(z); free(rt); free(h1); free(h2); free(qout); free(dinv);
+        free(r); free(p); free(q); free(z); free(rt); free(h1); free(h2); free(qout); free(dinv); free(icl);
         return -1;
       }
       dinv[i] = 1.0 / d;
+    }
+  }
+  /* IC(0) in fp32 (precond 2): factored once per solve; a breakdown refuses the solve. */
+  if (o->precond == 2) {
+    int rc = orc_ic0(n, rp, ci, val, icl);
+    if (rc < 0) {
+      free(r); free(p); free(q); free(z); free(rt); free(h1); free(h2); free(qout); free(dinv); free(icl);
+      return rc;
     }
   }
   /* Initialisation (Algorithms 1 and 2): r_0 = b - A x_0, z_0 = M^-1 r_0, p_0 = z_0,
@@ -620,8 +741,9 @@ int orc_run(const orc_opts* o, int n, const int32_t* rp, const int32_t* ci, cons
   double bnorm = sqrt(bb);
   double rr0 = orc_true_residual(n, rp, ci, val, b, x, r);
   double sigma = 0.0;
+  if (o->precond == 2) orc_ic0_apply(n, rp, ci, icl, r, z);
   for (int i = 0; i < n; ++i) {
-    p[i] = o->precond == 1 ? r[i] * dinv[i] : r[i];
+    p[i] = o->precond == 2 ? z[i] : o->precond == 1 ? r[i] * dinv[i] : r[i];
     sigma += r[i] * p[i];
   }
   double rho = bnorm > 0 ? sqrt(rr0) / bnorm : 0.0;
@@ -752,9 +874,12 @@ int orc_run(const orc_opts* o, int n, const int32_t* rp, const int32_t* ci, cons
         rho = rho_new;
         stop = 1;
       } else {
-        /* z_{k+1} = fl_p2(M^-1 r_{k+1}) (M = I, or the fp64 product r_i d_i for Jacobi,
-         * rounded once); sigma_{k+1} = fl_p4(r^T z); beta_k = sigma_{k+1} / sigma_k (fp64). */
-        for (int i = 0; i < n; ++i) z[i] = orc_chop(o->precond == 1 ? r[i] * dinv[i] : r[i], fmt[1]);
+        /* z_{k+1} = fl_p2(M^-1 r_{k+1}) (M = I; the fp64 product r_i d_i for Jacobi; the fp32
+         * IC(0) solves), rounded once; sigma_{k+1} = fl_p4(r^T z); beta_k = sigma_{k+1} /
+         * sigma_k (fp64). */
+        if (o->precond == 2) orc_ic0_apply(n, rp, ci, icl, r, z);
+        for (int i = 0; i < n; ++i)
+          z[i] = orc_chop(o->precond == 2 ? z[i] : o->precond == 1 ? r[i] * dinv[i] : r[i], fmt[1]);
         double sigma_new = orc_dot(n, r, z, fmt[3]);
         /* READING: after r was replaced by b - A x the old direction no longer matches the
          * residual history, so the iteration restarts with beta = 0 (p_{k+1} = z_{k+1}). */
@@ -790,8 +915,9 @@ int orc_run(const orc_opts* o, int n, const int32_t* rp, const int32_t* ci, cons
        * in fp64 from here on; iteration k counts as done. */
       double nt = orc_true_residual(n, rp, ci, val, b, x, r);
       sigma = 0.0;
+      if (o->precond == 2) orc_ic0_apply(n, rp, ci, icl, r, z);
       for (int i = 0; i < n; ++i) {
-        p[i] = o->precond == 1 ? r[i] * dinv[i] : r[i];
+        p[i] = o->precond == 2 ? z[i] : o->precond == 1 ? r[i] * dinv[i] : r[i];
         sigma += r[i] * p[i];
       }
       rho = sqrt(nt) / bnorm;
@@ -836,7 +962,7 @@ int orc_run(const orc_opts* o, int n, const int32_t* rp, const int32_t* ci, cons
     res->rho_rec = bnorm > 0 ? sqrt(rr) / bnorm : 0.0;
   }
   free(r); free(p); free(q); free(z); free(rt);
-  free(h1); free(h2); free(qout); free(dinv);
+  free(h1); free(h2); free(qout); free(dinv); free(icl);
   return outcome;
 }
 
