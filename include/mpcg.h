@@ -125,7 +125,13 @@ typedef struct {
                             * is z = fl_p2(r_i d_i) with d_i = 1 / a_ii in fp64, and the
                             * first and restart directions are p = M^-1 r. Solves of a
                             * matrix with a row lacking a positive diagonal entry fail
-                            * with MPCG_ERR_INVALID_ARG.                                  */
+                            * with MPCG_ERR_INVALID_ARG. 2: incomplete Cholesky IC(0) in
+                            * fp32 (Section 5's fixed-precision fp32 preconditioner, in its
+                            * symmetric zero-fill form; see mpcg_matrix_ic0): op 2 is
+                            * z = fl_p2(L^-T L^-1 fl32(r)) with both substitutions in fp32,
+                            * and the first and restart directions are p = L^-T L^-1 r.
+                            * The factor is computed on the first such solve of a matrix
+                            * and kept with it.                                          */
 } mpcg_options;
 
 /* Result of one solve. */
@@ -198,6 +204,18 @@ mpcg_status mpcg_matrix_info(mpcg_matrix_t A, mpcg_matrix_stats* info);
  * that mpcg_matrix_create applies (vector loads for a mean row length up to ~32 nonzeros,
  * K lanes with about 24 nonzeros per lane beyond). */
 mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, void* stream);
+/* IC(0) factor of A in fp32, computed on the device once per matrix and kept with it
+ * (Section 5 preconditions with an fp32 incomplete factorization; for SPD A this is its
+ * symmetric zero-fill form M = L L^T, L on the pattern of A's lower triangle). Each entry:
+ * l_ij = (fl32(a_ij) - sum_{k<j} l_ik l_jk) / l_jj for j < i and l_ii = sqrt(fl32(a_ii) -
+ * sum_{k<i} l_ik^2), every operation in fp32, sums in increasing k over the columns stored
+ * in both rows. If `factor` (device, nnz floats, caller-owned; may be NULL) is given, it
+ * receives one value per stored entry of A in A's CSR order: l_ij at (i, j) for j <= i and
+ * l_ji at (i, j) for j > i. Needs strictly increasing column indices in every row, a
+ * diagonal entry in every row and a symmetric pattern (INVALID_ARG otherwise); a
+ * non-positive pivot (IC(0) exists for M-matrices, not for every SPD matrix) is INVALID_ARG
+ * "breaks down". Synchronises `stream`. */
+mpcg_status mpcg_matrix_ic0(mpcg_ctx_t ctx, mpcg_matrix_t A, float* factor, void* stream);
 /* Forces the SpMV schedule of value format `fmt` (sched: 0 = sub-warp vector CSR with
  * `lanes` lanes per row (1, 2, 4, 8, 16 or 32); 1 = staged stream CSR, shared-memory tiles
  * filled by bulk copies, `lanes` = 1, 2 or 4 lanes per row; 2 = one thread per row reading
@@ -289,7 +307,9 @@ mpcg_status mpcg_graph_destroy(mpcg_graph_t g);
  * be device pointers; the matrix and the policy are created beforehand with the calls
  * above. The first call on a device looks up the array's device address, so make that
  * first call before any stream capture. All calls share the one array: calls whose work
- * overlaps on the GPU (other streams, other host threads) race and must not be issued. */
+ * overlaps on the GPU (other streams, other host threads) race and must not be issued.
+ * Contexts with precond = 2 (IC(0), whose factor and marks need memory) are rejected with
+ * MPCG_ERR_INVALID_ARG. */
 mpcg_status mpcg_solve_noalloc(mpcg_ctx_t ctx, mpcg_matrix_t A, const double* b, double* x, double tol,
                                int32_t max_iter, mpcg_policy_t policy, mpcg_result* res, void* stream);
 

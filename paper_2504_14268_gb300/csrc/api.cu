@@ -67,6 +67,8 @@ struct Plan {
   DevBuf work, bstage, xstage, hstage;
   DevBuf qpriv, trans, feats;
   DevBuf lk_w, lk_pref, lk_cfirst, lk_clast, lk_base, lk_done, lk_seg, lk_nseg;
+  DevBuf icwork;             // IC(0): every system's substitution words, zeroed per launch
+  size_t icwork_bytes = 0;
   bool lockstep = false;
   std::vector<DevSys> hsys;
   std::vector<mpcg_result> hres;
@@ -91,6 +93,9 @@ struct mpcg_matrix_s {
   DevMatrix dm;
   DevBuf rp, ci, v64, v32, vtf, v16, vbf, v16r, vbfr, rexp, dinv;
   bool diag_ok = false;             // every row has a positive diagonal entry (Jacobi defined)
+  DevBuf icf, icd;                  // IC(0) factor (fp32, one value per stored entry), diagonal positions
+  unsigned ic_fail = 0;             // 0: not factored or factored fine; else the factorization's error bits
+  bool ic_ready = false;
   int device = 0;
   double mean = 0, maxr = 0, cv = 0;
   long long win[4] = {0, 0, 0, 0};  // largest nonzero count of 256, 128, 64, 32 consecutive rows
@@ -171,7 +176,7 @@ mpcg_status build_optview(mpcg_ctx_t ctx, const mpcg_options& o, OptView& v) {
   if (!(o.eps_min > 0.0 && o.eps_min < 1.0)) return fail(ctx, MPCG_ERR_INVALID_ARG, "eps_min must be in (0, 1)");
   if (o.mlp_hidden < 1 || o.mlp_hidden > kMaxHidden) return fail(ctx, MPCG_ERR_INVALID_ARG, "mlp_hidden must be in [1, %d]", kMaxHidden);
   if (o.batch_mode < 0 || o.batch_mode > 2) return fail(ctx, MPCG_ERR_INVALID_ARG, "batch_mode must be 0, 1 or 2");
-  if (o.precond < 0 || o.precond > 1) return fail(ctx, MPCG_ERR_INVALID_ARG, "precond must be 0 or 1");
+  if (o.precond < 0 || o.precond > 2) return fail(ctx, MPCG_ERR_INVALID_ARG, "precond must be 0, 1 or 2");
   for (int a = 0; a < o.nprec; ++a)
     if (!valid_fmt(o.precs[a])) return fail(ctx, MPCG_ERR_INVALID_ARG, "precs[%d] = %d is not a format code", a, o.precs[a]);
   if (o.unvisited_fallback != -1 && !valid_fmt(o.unvisited_fallback))
@@ -327,6 +332,44 @@ mpcg_status fill_policy(mpcg_ctx_t ctx, mpcg_policy_t P, PolicyView& pv) {
   return MPCG_OK;
 }
 
+mpcg_status ic0_error(mpcg_ctx_t ctx, unsigned bits) {
+  if (bits & 4u) return fail(ctx, MPCG_ERR_TIMEOUT, "the incomplete Cholesky factorization exceeded its wait limit");
+  if (bits & 2u)
+    return fail(ctx, MPCG_ERR_INVALID_ARG,
+                "incomplete Cholesky needs strictly increasing column indices, a diagonal entry in every row "
+                "and a symmetric pattern");
+  return fail(ctx, MPCG_ERR_INVALID_ARG, "incomplete Cholesky breaks down (a non-positive pivot)");
+}
+
+// IC(0) factor of A in fp32, computed once per matrix on the device (the factorization kernel
+// and the transposed copy for the backward substitution); a failed factorization is
+// remembered and reported again.
+mpcg_status ensure_ic0(mpcg_ctx_t ctx, mpcg_matrix_s* M, cudaStream_t s) {
+  if (M->ic_ready) return MPCG_OK;
+  if (M->ic_fail) return ic0_error(ctx, M->ic_fail);
+  const int n = M->dm.n;
+  const long long nnz = M->dm.nnz;
+  CK(ctx, M->icf.ensure(4 * (size_t)std::max(nnz, 1LL)));
+  CK(ctx, M->icd.ensure(4 * (size_t)std::max(n, 1)));
+  DevBuf done, err;
+  CK(ctx, done.ensure(4 * (size_t)std::max(n, 1)));
+  CK(ctx, err.ensure(sizeof(unsigned)));
+  CK(ctx, cudaMemsetAsync(done.p, 0, 4 * (size_t)std::max(n, 1), s));
+  CK(ctx, cudaMemsetAsync(err.p, 0, sizeof(unsigned), s));
+  CK(ctx, launch_ic0_factor(n, M->dm.rp, M->dm.ci, M->dm.v64, M->icf.as<float>(), M->icd.as<int>(),
+                            done.as<unsigned>(), err.as<unsigned>(), kTimeoutCycles, ctx->nsm, s));
+  unsigned bits = 0;
+  CK(ctx, cudaMemcpyAsync(&bits, err.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  if (bits) {
+    M->ic_fail = bits;
+    return ic0_error(ctx, bits);
+  }
+  M->ic_ready = true;
+  M->bytes += 4 * nnz + 4LL * n;
+  return MPCG_OK;
+}
+
 // Builds the device tables of a launch for `in` systems into `pl` and fills pl.L.
 mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, mpcg_policy_t policy, int train,
                        int trans_cap, int force_team, cudaStream_t s, int feat_cap = 0) {
@@ -336,6 +379,12 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
       if (!in[i].A->diag_ok)
         return fail(ctx, MPCG_ERR_INVALID_ARG,
                     "system %d: Jacobi preconditioning needs a positive diagonal entry in every row", i);
+  const bool ic = ctx->opt.precond == 2;
+  if (ic)
+    for (int i = 0; i < nsys; ++i) {
+      mpcg_status st = ensure_ic0(ctx, in[i].A, s);
+      if (st != MPCG_OK) return st;
+    }
   bool stream_shape = false;
   for (int i = 0; i < nsys; ++i) stream_shape = stream_shape || uses_stream(in[i].A->dm);
   const int grid = ctx->nsm * (stream_shape ? ctx->occ_s : ctx->occ);
@@ -369,9 +418,14 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
   const int nteams_all = nteams + 1;
 
   // Work vectors: r, p, q (8 bytes per row each) and p's low-precision copy (4 bytes).
-  size_t wbytes = 0;
+  // IC(0) adds one 64-bit word per row (value and mark of the substitutions).
+  size_t wbytes = 0, mbytes = 0;
   for (int i = 0; i < nsys; ++i) wbytes += 28 * (size_t)in[i].A->dm.n + 4 * 256;
+  for (int i = 0; i < nsys; ++i) mbytes += ic ? 8 * (size_t)in[i].A->dm.n : 0;
   CK(ctx, pl.work.ensure(wbytes));
+  pl.icwork_bytes = mbytes;
+  if (mbytes) CK(ctx, pl.icwork.ensure(mbytes));
+  unsigned long long* icw_next = pl.icwork.as<unsigned long long>();
   const int S = ctx->opt.b_bins * ctx->opt.r_bins;
   const long long qsize = 4LL * S * ctx->opt.nprec;
   if (train) {
@@ -391,6 +445,8 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
     memset(&d, 0, sizeof(d));
     d.A = in[i].A->dm;
     d.A.dinv = ctx->opt.precond == 1 ? in[i].A->dinv.as<double>() : nullptr;
+    d.A.icf = ic ? in[i].A->icf.as<float>() : nullptr;
+    d.A.icd = ic ? in[i].A->icd.as<int>() : nullptr;
     const int n = d.A.n;
     d.b = in[i].b;
     d.x = in[i].x;
@@ -398,6 +454,10 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
     d.p = (double*)take(8 * (size_t)n);
     d.q = take(8 * (size_t)n);
     d.plow = take(4 * (size_t)n);
+    if (ic) {
+      d.icw = icw_next;
+      icw_next += n;
+    }
     d.tol = in[i].tol;
     d.max_iter = in[i].max_iter;
     d.lane = i;
@@ -480,6 +540,7 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
   L.timeout_cycles = kTimeoutCycles;
   if (const char* t = getenv("MPCG_TIMEOUT_CYCLES")) L.timeout_cycles = atoll(t);
   L.lockstep = pl.lockstep ? 1 : 0;
+  L.ic = ctx->opt.precond == 2 ? 1 : 0;
   if (pl.lockstep) {
     L.lk_w = pl.lk_w.as<long long>();
     L.lk_pref = pl.lk_pref.as<long long>();
@@ -497,6 +558,7 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
 mpcg_status enqueue_plan(mpcg_ctx_t ctx, Plan& pl, cudaStream_t s) {
   CK(ctx, cudaMemsetAsync(pl.bars.p, 0, sizeof(unsigned) * kBarStride * pl.nteams, s));
   CK(ctx, cudaMemsetAsync(pl.err.p, 0, sizeof(unsigned), s));
+  if (pl.icwork_bytes) CK(ctx, cudaMemsetAsync(pl.icwork.p, 0, pl.icwork_bytes, s));
   const size_t smem = pl.L.stream_stage > 0 ? 2 * (size_t)pl.L.stream_stage : 0;
   if (pl.lockstep) {
     // every system starts in its initialisation phase; no system has finished
@@ -780,6 +842,20 @@ mpcg_status mpcg_matrix_info(mpcg_matrix_t A, mpcg_matrix_stats* info) {
   }
   info->device_bytes = A->bytes;
   for (int j = 0; j < 5; ++j) info->static_features[j] = A->feat[j];
+  return MPCG_OK;
+}
+
+mpcg_status mpcg_matrix_ic0(mpcg_ctx_t ctx, mpcg_matrix_t A, float* factor, void* stream) {
+  if (!ctx || !A) return fail(ctx, MPCG_ERR_INVALID_ARG, "NULL argument");
+  if (A->ctx != ctx) return fail(ctx, MPCG_ERR_INVALID_ARG, "matrix belongs to another context");
+  if (factor && !is_device_ptr(factor)) return fail(ctx, MPCG_ERR_INVALID_ARG, "factor must be a device pointer");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  mpcg_status st = ensure_ic0(ctx, A, s);
+  if (st != MPCG_OK) return st;
+  if (factor && A->dm.nnz > 0)
+    CK(ctx, cudaMemcpyAsync(factor, A->icf.p, 4 * (size_t)A->dm.nnz, cudaMemcpyDeviceToDevice, s));
+  CK(ctx, cudaStreamSynchronize(s));
   return MPCG_OK;
 }
 
@@ -1555,6 +1631,8 @@ mpcg_status mpcg_solve_noalloc(mpcg_ctx_t ctx, mpcg_matrix_t A, const double* b,
     return fail(ctx, MPCG_ERR_INVALID_ARG, "mpcg_solve_noalloc needs device pointers for b and x");
   if (ctx->opt.precond == 1 && !A->diag_ok)
     return fail(ctx, MPCG_ERR_INVALID_ARG, "Jacobi preconditioning needs a positive diagonal entry in every row");
+  if (ctx->opt.precond == 2)
+    return fail(ctx, MPCG_ERR_INVALID_ARG, "the no-allocation solve does not run the incomplete Cholesky preconditioner");
   if (!(tol >= 0.0) || max_iter < 0) return fail(ctx, MPCG_ERR_INVALID_ARG, "tol must be >= 0 and max_iter >= 0");
   if (A->ctx != ctx || policy->ctx != ctx) return fail(ctx, MPCG_ERR_INVALID_ARG, "objects belong to another context");
   if (ctx->device < 0 || ctx->device >= 64) return fail(ctx, MPCG_ERR_INVALID_ARG, "device ordinal out of range");

@@ -18,6 +18,7 @@
 // word and the kernel returns.
 #include "internal.h"
 #include "spmv.cuh"
+#include "ic0.cuh"
 
 namespace mpcg {
 
@@ -36,7 +37,8 @@ struct Bcast {
   double alpha, beta;
   int k, mode;
   int fmt[4];
-  int zfmt, pad;
+  int zfmt;
+  unsigned icep;  // epoch of the IC(0) application in this phase
 };
 
 struct Smem {
@@ -181,6 +183,7 @@ __device__ __forceinline__ void load_bcast(const SysState* st, Smem& sm) {
     sm.bc.k = v->k;
     sm.bc.mode = v->mode;
     sm.bc.zfmt = v->zfmt;
+    sm.bc.icep = v->icep;
 #pragma unroll
     for (int j = 0; j < 4; ++j) sm.bc.fmt[j] = v->fmt[j];
   }
@@ -376,11 +379,20 @@ __device__ void choose_action(const Launch& L, const DevSys& S, SysState* st, in
 // Row phases
 // ----------------------------------------------------------------------------------------
 
-// M^-1 r_i in fp64: r_i times the fp64 reciprocal of the diagonal when the launch runs the
-// Jacobi preconditioner (dinv set), r_i itself otherwise (M = I).
+// M^-1 r_i in fp64: with IC(0) the element of the last application (ic_rows), with Jacobi
+// r_i times the fp64 reciprocal of the diagonal (dinv set), r_i itself otherwise (M = I).
 __device__ __forceinline__ double minv_r(const DevSys& S, int i, double ri) {
+  if (S.icw) return (double)__uint_as_float((unsigned)__ldcg(S.icw + i));
   return S.A.dinv ? ri * __ldg(S.A.dinv + i) : ri;
 }
+
+// IC(0) application over the rows R in the phase with epoch ep (all CTAs that hold rows of
+// the system run it in the same phase); consume(i, r_i, w_i) per row, w = M^-1 r.
+template <class F>
+__device__ __forceinline__ void ic_rows(const Launch& L, const DevSys& S, Rows R, unsigned ep, F&& consume) {
+  ic_apply(S, R, ep, L.err, (unsigned)DERR_TIMEOUT, L.timeout_cycles, consume);
+}
+
 
 // sigma term of row i: fl_p4(r_i) fl_p4(z_i) with z_i = fl_p2(w_i), w_i = M^-1 r_i: a DFMA
 // when p4 = fp64, otherwise the compensated fp32 pair. Roundings that are identities
@@ -404,6 +416,23 @@ __device__ __forceinline__ void sigma_term(double ri, double wi, int p2, int p4,
 
 // z = fl_p2(w) as fp64, w = M^-1 r.
 __device__ __forceinline__ double z_of(double wi, int p2) { return p2 == F64 ? wi : f2d(round_d2f(wi, p2)); }
+
+// The IC(0) applications of the solver phases, out of line so that the preconditioner's
+// code does not enter the register allocation of the unpreconditioned phases. With copy_p
+// the direction becomes p = w and sg.d collects r^T w in fp64; with p2 >= 0 sg collects
+// the sigma terms of z = fl_p2(w).
+__device__ __noinline__ void ic_phase(const Launch& L, const DevSys& S, Rows R, unsigned ep, int p2, int p4,
+                                      bool copy_p, DotAcc& sg) {
+  DotAcc acc = sg;
+  ic_rows(L, S, R, ep, [&](int i, double ri, double wi) {
+    if (copy_p) {
+      S.p[i] = wi;
+      acc.d = fma(ri, wi, acc.d);
+    }
+    if (p2 >= 0) sigma_term(ri, wi, p2, p4, acc);
+  });
+  sg = acc;
+}
 
 // Element i of q (stored in p1's format) as fp64, times 2^e_i for the row-scaled formats.
 __device__ __forceinline__ double load_q(const DevSys& S, int i, int p1) {
@@ -429,7 +458,7 @@ __device__ __forceinline__ void store_low(void* plow, int i, double v, int f) {
 
 // r = b - A x in fp64 (residual recomputation), with ||r||^2 and, when p2 >= 0, sigma partials.
 // With copy_p the new residual is also written to p (warm-start initialisation).
-template <int K>
+template <int K, bool IC>
 __device__ void true_res_vec(const DevSys& S, Rows R, int p2, int p4, bool copy_p, double& rr, DotAcc& sg) {
   constexpr int NG = kThreads / K;
   const int lane = threadIdx.x & (K - 1);
@@ -447,26 +476,33 @@ __device__ void true_res_vec(const DevSys& S, Rows R, int p2, int p4, bool copy_
     if (lane == 0) {
       const double ri = __ldg(S.b + row) - acc;
       S.r[row] = ri;
-      const double wi = minv_r(S, row, ri);
-      if (copy_p) {  // restart direction p = M^-1 r, sigma = r^T M^-1 r in fp64
-        S.p[row] = wi;
-        sg.d = fma(ri, wi, sg.d);
-      }
       rr = fma(ri, ri, rr);
-      if (p2 >= 0) sigma_term(ri, wi, p2, p4, sg);
+      if (!(IC && S.icw)) {  // with IC(0), M^-1 r needs every row of r first (true_res_rows)
+        const double wi = minv_r(S, row, ri);
+        if (copy_p) {  // restart direction p = M^-1 r, sigma = r^T M^-1 r in fp64
+          S.p[row] = wi;
+          sg.d = fma(ri, wi, sg.d);
+        }
+        if (p2 >= 0) sigma_term(ri, wi, p2, p4, sg);
+      }
     }
   }
 }
 
-__device__ void true_res_rows(const DevSys& S, Rows R, int p2, int p4, bool copy_p, double& rr, DotAcc& sg) {
+// ep: the phase's IC(0) epoch (used when the launch preconditions with IC(0) and the
+// caller wants M^-1 r: copy_p or p2 >= 0).
+template <bool IC>
+__device__ void true_res_rows(const Launch& L, const DevSys& S, Rows R, int p2, int p4, bool copy_p, double& rr,
+                              DotAcc& sg, unsigned ep) {
   switch (S.A.lanes[F64]) {
-    case 1: true_res_vec<1>(S, R, p2, p4, copy_p, rr, sg); break;
-    case 2: true_res_vec<2>(S, R, p2, p4, copy_p, rr, sg); break;
-    case 4: true_res_vec<4>(S, R, p2, p4, copy_p, rr, sg); break;
-    case 8: true_res_vec<8>(S, R, p2, p4, copy_p, rr, sg); break;
-    case 16: true_res_vec<16>(S, R, p2, p4, copy_p, rr, sg); break;
-    default: true_res_vec<32>(S, R, p2, p4, copy_p, rr, sg); break;
+    case 1: true_res_vec<1, IC>(S, R, p2, p4, copy_p, rr, sg); break;
+    case 2: true_res_vec<2, IC>(S, R, p2, p4, copy_p, rr, sg); break;
+    case 4: true_res_vec<4, IC>(S, R, p2, p4, copy_p, rr, sg); break;
+    case 8: true_res_vec<8, IC>(S, R, p2, p4, copy_p, rr, sg); break;
+    case 16: true_res_vec<16, IC>(S, R, p2, p4, copy_p, rr, sg); break;
+    default: true_res_vec<32, IC>(S, R, p2, p4, copy_p, rr, sg); break;
   }
+  if (IC && S.icw && (copy_p || p2 >= 0)) ic_phase(L, S, R, ep, p2, p4, copy_p, sg);
 }
 
 // ----------------------------------------------------------------------------------------
@@ -552,6 +588,7 @@ __device__ void step_init(const Launch& L, const DevSys& S, SysState* st, double
     st->rho = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
     st->sigma = sig;
     st->k = 0;
+    st->icep = 0u;  // the phase after initialisation applies IC(0) with epoch 1
     st->alpha = 0.0;
     st->beta = 0.0;
     st->nu = 0.0;
@@ -843,6 +880,7 @@ __device__ __forceinline__ bool team_step(const Launch& L, const TeamCtx& T, Sys
   bool ok = true;
   if (last) {
     work();
+    if (threadIdx.x == 0) st->icep += 1u;
     team_release(T);
   } else {
     ok = team_wait(L, T, sm);
@@ -1131,10 +1169,11 @@ __device__ __noinline__ void phase_c(const DevSys& S, Rows R, double alpha, doub
 }
 
 // fp64 restart after a breakdown: r = b - A x and p = r in fp64, then step_restart.
+template <bool IC>
 __device__ bool restart64(const Launch& L, const TeamCtx& T, const DevSys& S, SysState* st, Rows R, Smem& sm) {
   double rr = 0.0;
   DotAcc sg{0.0, 0.f, 0.f};
-  true_res_rows(S, R, -1, -1, true, rr, sg);
+  true_res_rows<IC>(L, S, R, -1, -1, true, rr, sg, sm.bc.icep);
   rr = cta_sum(rr, sm.red);
   const double sp = cta_dot(sg, sm.red);
   write_partial(L, 0, rr);
@@ -1146,6 +1185,7 @@ __device__ bool restart64(const Launch& L, const TeamCtx& T, const DevSys& S, Sy
   });
 }
 
+template <bool IC>
 __device__ __forceinline__ bool solve_system(const Launch& L, const TeamCtx& T, int sid, Smem& sm, const StreamCtx* sc) {
   const DevSys& S = L.sys[sid];
   SysState* st = L.st + sid;
@@ -1162,19 +1202,25 @@ __device__ __forceinline__ bool solve_system(const Launch& L, const TeamCtx& T, 
   {
     double bb = 0.0, rr = 0.0;
     DotAcc sg{0.0, 0.f, 0.f};
+    const bool ic = IC && S.icw != nullptr;
     for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
       const double bi = __ldg(S.b + i);
       bb = fma(bi, bi, bb);
       if (!o.warm_start) {
-        const double wi = minv_r(S, i, bi);
         S.x[i] = 0.0;
         S.r[i] = bi;
-        S.p[i] = wi;
         rr = fma(bi, bi, rr);
-        sg.d = fma(bi, wi, sg.d);
+        if (!ic) {
+          const double wi = minv_r(S, i, bi);
+          S.p[i] = wi;
+          sg.d = fma(bi, wi, sg.d);
+        }
       }
     }
-    if (o.warm_start) true_res_rows(S, R, -1, -1, true, rr, sg);
+    // IC(0): epoch 0 (the marks are zeroed for every launch; later phases count from 1)
+    if (o.warm_start) true_res_rows<IC>(L, S, R, -1, -1, true, rr, sg, 0u);
+    else if (ic)
+      ic_phase(L, S, R, 0u, -1, -1, true, sg);
     bb = cta_sum(bb, sm.red);
     rr = cta_sum(rr, sm.red);
     const double sp = cta_dot(sg, sm.red);
@@ -1207,7 +1253,7 @@ __device__ __forceinline__ bool solve_system(const Launch& L, const TeamCtx& T, 
         write_partial(L, 0, cta_dot(nu, sm.red));
         if (!team_step(L, T, st, sm, [&] { step_A(L, S, st, team_sum(L, T, 0, sm.red)); })) return false;
         if (sm.bc.mode == M_RESTART64) {
-          if (!restart64(L, T, S, st, R, sm)) return false;
+          if (!restart64<IC>(L, T, S, st, R, sm)) return false;
           if (sm.bc.mode != M_CONT) break;
           continue;
         }
@@ -1219,10 +1265,13 @@ __device__ __forceinline__ bool solve_system(const Launch& L, const TeamCtx& T, 
         const int p1 = sm.bc.fmt[0], p2 = sm.bc.fmt[1], p4 = sm.bc.fmt[3];
         // with z = r (no preconditioner) and an fp64 dot, sigma is ||r||^2 itself: one DFMA
         // per row saved
-        const bool sig_rr = (p2 == F64 && p4 == F64 && !S.A.dinv);
+        const bool ic = IC && S.icw != nullptr;
+        const bool sig_rr = (p2 == F64 && p4 == F64 && !S.A.dinv && !ic);
         double rr = 0.0;
         DotAcc sg{0.0, 0.f, 0.f};
-        phase_b(S, R, alpha, p1, p2, p4, sig_rr, rr, sg);
+        // with IC(0) the sigma terms follow the substitutions
+        phase_b(S, R, alpha, p1, p2, p4, sig_rr || ic, rr, sg);
+        if (ic) ic_phase(L, S, R, sm.bc.icep, p2, p4, false, sg);
         rr = cta_sum(rr, sm.red);
         const double sp = sig_rr ? rr : cta_dot(sg, sm.red);
         write_partial(L, 0, rr);
@@ -1254,7 +1303,7 @@ __device__ __forceinline__ bool solve_system(const Launch& L, const TeamCtx& T, 
       }
       if (mode == M_X_THEN_DONE) break;
       if (mode == M_X_THEN_RESTART64) {
-        if (!restart64(L, T, S, st, R, sm)) return false;
+        if (!restart64<IC>(L, T, S, st, R, sm)) return false;
         if (sm.bc.mode != M_CONT) break;
         continue;
       }
@@ -1263,7 +1312,7 @@ __device__ __forceinline__ bool solve_system(const Launch& L, const TeamCtx& T, 
         const int p2 = sm.bc.fmt[1], p4 = sm.bc.fmt[3];
         double rr = 0.0;
         DotAcc sg{0.0, 0.f, 0.f};
-        true_res_rows(S, R, p2, p4, false, rr, sg);
+        true_res_rows<IC>(L, S, R, p2, p4, false, rr, sg, sm.bc.icep);
         rr = cta_sum(rr, sm.red);
         const double sp = cta_dot(sg, sm.red);
         write_partial(L, 0, rr);
@@ -1276,7 +1325,7 @@ __device__ __forceinline__ bool solve_system(const Launch& L, const TeamCtx& T, 
           return false;
       }
       if (sm.bc.mode == M_RESTART64) {
-        if (!restart64(L, T, S, st, R, sm)) return false;
+        if (!restart64<IC>(L, T, S, st, R, sm)) return false;
         if (sm.bc.mode != M_CONT) break;
         continue;
       }
@@ -1304,7 +1353,7 @@ __device__ __forceinline__ bool solve_system(const Launch& L, const TeamCtx& T, 
     int known = 0;
     if (threadIdx.x == 0) known = *(volatile int*)&st->true_known;
     known = __syncthreads_or(known);
-    if (!known) true_res_rows(S, R, -1, -1, false, rr, unused);
+    if (!known) true_res_rows<IC>(L, S, R, -1, -1, false, rr, unused, 0u);
     rr = cta_sum(rr, sm.red);
     write_partial(L, 0, rr);
     if (!team_step(L, T, st, sm, [&] { step_final(L, S, st, sid, team_sum(L, T, 0, sm.red)); })) return false;
@@ -1447,6 +1496,7 @@ __device__ __forceinline__ void lk_partial(const Launch& L, int slot, int k, dou
 }
 
 // Row work of one slice in the current phase of its system.
+template <bool IC>
 __device__ void lk_slice_rows(const Launch& L, int s, Rows R, int slot, Smem& sm, const StreamCtx* sc) {
   const DevSys& S = L.sys[s];
   SysState* st = L.st + s;
@@ -1462,19 +1512,24 @@ __device__ void lk_slice_rows(const Launch& L, int s, Rows R, int slot, Smem& sm
       double bb = 0.0, rr = 0.0;
       DotAcc sg{0.0, 0.f, 0.f};
       const bool warm = L.opt.warm_start != 0;
+      const bool ic = IC && S.icw != nullptr;
       for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
         const double bi = __ldg(S.b + i);
         bb = fma(bi, bi, bb);
         if (!warm) {
-          const double wi = minv_r(S, i, bi);
           S.x[i] = 0.0;
           S.r[i] = bi;
-          S.p[i] = wi;
           rr = fma(bi, bi, rr);
-          sg.d = fma(bi, wi, sg.d);
+          if (!ic) {
+            const double wi = minv_r(S, i, bi);
+            S.p[i] = wi;
+            sg.d = fma(bi, wi, sg.d);
+          }
         }
       }
-      if (warm) true_res_rows(S, R, -1, -1, true, rr, sg);
+      if (warm) true_res_rows<IC>(L, S, R, -1, -1, true, rr, sg, sm.bc.icep);
+      else if (ic)
+        ic_phase(L, S, R, sm.bc.icep, -1, -1, true, sg);
       bb = cta_sum(bb, sm.red);
       rr = cta_sum(rr, sm.red);
       const double sp = cta_dot(sg, sm.red);
@@ -1497,10 +1552,12 @@ __device__ void lk_slice_rows(const Launch& L, int s, Rows R, int slot, Smem& sm
     }
     case PH_B: {
       const int p1 = sm.bc.fmt[0], p2 = sm.bc.fmt[1], p4 = sm.bc.fmt[3];
-      const bool sig_rr = (p2 == F64 && p4 == F64 && !S.A.dinv);
+      const bool ic = IC && S.icw != nullptr;
+      const bool sig_rr = (p2 == F64 && p4 == F64 && !S.A.dinv && !ic);
       double rr = 0.0;
       DotAcc sg{0.0, 0.f, 0.f};
-      phase_b(S, R, sm.bc.alpha, p1, p2, p4, sig_rr, rr, sg);
+      phase_b(S, R, sm.bc.alpha, p1, p2, p4, sig_rr || ic, rr, sg);
+      if (ic) ic_phase(L, S, R, sm.bc.icep, p2, p4, false, sg);
       rr = cta_sum(rr, sm.red);
       const double sp = sig_rr ? rr : cta_dot(sg, sm.red);
       lk_partial(L, slot, 0, rr);
@@ -1518,7 +1575,7 @@ __device__ void lk_slice_rows(const Launch& L, int s, Rows R, int slot, Smem& sm
     case PH_T: {
       double rr = 0.0;
       DotAcc sg{0.0, 0.f, 0.f};
-      true_res_rows(S, R, sm.bc.fmt[1], sm.bc.fmt[3], false, rr, sg);
+      true_res_rows<IC>(L, S, R, sm.bc.fmt[1], sm.bc.fmt[3], false, rr, sg, sm.bc.icep);
       rr = cta_sum(rr, sm.red);
       const double sp = cta_dot(sg, sm.red);
       lk_partial(L, slot, 0, rr);
@@ -1537,7 +1594,7 @@ __device__ void lk_slice_rows(const Launch& L, int s, Rows R, int slot, Smem& sm
     case PH_R64: {
       double rr = 0.0;
       DotAcc sg{0.0, 0.f, 0.f};
-      true_res_rows(S, R, -1, -1, true, rr, sg);
+      true_res_rows<IC>(L, S, R, -1, -1, true, rr, sg, sm.bc.icep);
       rr = cta_sum(rr, sm.red);
       const double sp = cta_dot(sg, sm.red);
       lk_partial(L, slot, 0, rr);
@@ -1547,7 +1604,7 @@ __device__ void lk_slice_rows(const Launch& L, int s, Rows R, int slot, Smem& sm
     case PH_FINAL: {
       double rr = 0.0;
       DotAcc unused{0.0, 0.f, 0.f};
-      if (!sm.lk_known) true_res_rows(S, R, -1, -1, false, rr, unused);
+      if (!sm.lk_known) true_res_rows<IC>(L, S, R, -1, -1, false, rr, unused, 0u);
       lk_partial(L, slot, 0, cta_sum(rr, sm.red));
       break;
     }
@@ -1620,11 +1677,13 @@ __device__ void lk_step(const Launch& L, int s, Smem& sm) {
       default: next = PH_DONE; break;  // PH_FINAL
     }
     st->phase = next;
+    st->icep += 1u;  // a new epoch for the IC(0) marks of the next phase
     if (next == PH_DONE) atomicAdd(L.lk_done, 1);
   }
   __syncthreads();
 }
 
+template <bool IC>
 __global__ void __launch_bounds__(kThreads, 4) cg_lockstep(const Launch L) {
   __shared__ Smem sm;
   extern __shared__ __align__(128) unsigned char dyn[];
@@ -1661,7 +1720,7 @@ __global__ void __launch_bounds__(kThreads, 4) cg_lockstep(const Launch L) {
     const int nseg = L.lk_nseg[blockIdx.x];
     for (int i = 0; i < nseg; ++i) {
       const int4 sg = L.lk_seg[(long long)blockIdx.x * (L.nsys + 1) + i];
-      lk_slice_rows(L, sg.x, Rows{sg.y, sg.z}, sg.w, sm, sc);
+      lk_slice_rows<IC>(L, sg.x, Rows{sg.y, sg.z}, sg.w, sm, sc);
     }
     if (!grid_sync(L, G, sm)) return;
     for (int s = blockIdx.x; s < L.nsys; s += gridDim.x) lk_step(L, s, sm);
@@ -1669,6 +1728,9 @@ __global__ void __launch_bounds__(kThreads, 4) cg_lockstep(const Launch L) {
   }
 }
 
+// IC = true: the instantiation for launches that precondition with IC(0); the other one
+// carries none of its code.
+template <bool IC>
 __global__ void __launch_bounds__(kThreads, 4) cg_persistent(const Launch L) {
   __shared__ Smem sm;
   extern __shared__ __align__(128) unsigned char dyn[];
@@ -1690,7 +1752,7 @@ __global__ void __launch_bounds__(kThreads, 4) cg_persistent(const Launch L) {
   T.first = L.team_first[T.team];
   T.bar = L.bars + (long long)T.team * kBarStride;
   for (int i = L.team_sys_off[T.team]; i < L.team_sys_off[T.team + 1]; ++i) {
-    if (!solve_system(L, T, L.team_sys[i], sm, sc)) return;
+    if (!solve_system<IC>(L, T, L.team_sys[i], sm, sc)) return;
   }
 }
 
@@ -1698,30 +1760,40 @@ __global__ void __launch_bounds__(kThreads, 4) cg_persistent(const Launch L) {
 
 cudaError_t launch_cg(const Launch& L, int grid, size_t smem, cudaStream_t s) {
   void* args[] = {(void*)&L};
-  return cudaLaunchCooperativeKernel((const void*)cg_persistent, dim3(grid), dim3(kThreads), args, smem, s);
+  const void* k = L.ic ? (const void*)cg_persistent<true> : (const void*)cg_persistent<false>;
+  return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), args, smem, s);
 }
 
 cudaError_t launch_cg_lockstep(const Launch& L, int grid, size_t smem, cudaStream_t s) {
   void* args[] = {(void*)&L};
-  return cudaLaunchCooperativeKernel((const void*)cg_lockstep, dim3(grid), dim3(kThreads), args, smem, s);
+  const void* k = L.ic ? (const void*)cg_lockstep<true> : (const void*)cg_lockstep<false>;
+  return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), args, smem, s);
 }
 
 // Resident CTAs per SM of the solver kernels (the smaller of the two, so that one grid size
 // serves both).
 cudaError_t cg_occupancy(int* blocks_per_sm, size_t smem) {
-  int a = 0, b = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, cg_persistent, kThreads, smem);
-  if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cg_lockstep, kThreads, smem);
-  if (e != cudaSuccess) return e;
-  *blocks_per_sm = a < b ? a : b;
+  const void* ks[4] = {(const void*)cg_persistent<false>, (const void*)cg_persistent<true>,
+                       (const void*)cg_lockstep<false>, (const void*)cg_lockstep<true>};
+  int best = 1 << 30;
+  for (const void* k : ks) {
+    int a = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    best = a < best ? a : best;
+  }
+  *blocks_per_sm = best;
   return cudaSuccess;
 }
 
 cudaError_t cg_set_smem_limit(size_t bytes) {
-  const cudaError_t e = cudaFuncSetAttribute(cg_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(cg_lockstep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  const void* ks[4] = {(const void*)cg_persistent<false>, (const void*)cg_persistent<true>,
+                       (const void*)cg_lockstep<false>, (const void*)cg_lockstep<true>};
+  for (const void* k : ks) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 size_t cg_static_smem() { return sizeof(Smem); }

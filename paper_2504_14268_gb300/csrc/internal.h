@@ -43,6 +43,9 @@ struct DevMatrix {
   int tile_rows[8];         // stream schedule: rows per shared-memory tile (kThreads / lanes)
   int tile_bytes[8];        // stream schedule: bytes of a stage's value region (columns follow)
   const double* dinv;       // Jacobi: 1 / a_ii in fp64 when the launch preconditions, else nullptr
+  const float* icf;         // IC(0) factor in fp32 when the launch preconditions with it, else
+                            // nullptr: l_ij at (i, j) for j <= i, l_ji at (i, j) for j > i
+  const int* icd;           // IC(0): position of the diagonal entry of each row
 };
 
 // One transition of an exploration episode (Algorithm 1), recorded for the end-of-round merge.
@@ -75,6 +78,8 @@ struct DevSys {
   float feat_static[5];     // MLP static features of the matrix
   int feat_cap;             // capacity of feat_log in feature vectors
   float* feat_log;          // when set: the 16 features of every visited state, [k][16]
+  unsigned long long* icw;  // IC(0): the substitutions' work vector [n], per row the fp32 value
+                            // (y_i, then w_i = (M^-1 r)_i) in the low word and its mark above
 };
 
 // Per-system state that persists across phases; written only by the CTA that arrives
@@ -92,6 +97,7 @@ struct SysState {
   int explored, s_cur;      // exploration flag and state index of the current iteration
   int zfmt;                 // p2 of the iteration whose direction update is pending
   int phase;                // lockstep batches: the phase the system runs next (0 = initialisation)
+  unsigned icep;            // phases completed since initialisation: the IC(0) marks' epoch
   int fp64_lock, n_restart;   // after a breakdown restart every operation runs in fp64
   unsigned long long t_last;  // globaltimer at the previous team barrier
   unsigned ns_a, ns_b;        // phase times of the current iteration
@@ -153,7 +159,7 @@ struct Launch {
   // Lockstep batches (lockstep != 0): at every super-step each CTA works on a slice of every
   // active system, the slices re-cut whenever systems finish.
   int lockstep;
-  int pad_lk;
+  int ic;                   // IC(0) preconditioning: the solver kernels' IC instantiations run
   const long long* lk_w;    // [nsys] row work of each system: nnz + 3 n (at least 1)
   long long* lk_pref;       // [nsys + 1] prefix of the work of the active systems
   int* lk_cfirst;           // [nsys] first CTA holding rows of the system (-1: finished)
@@ -193,6 +199,11 @@ cudaError_t launch_mlp_reduce_adam(const float* part, int nparts, long long np, 
                                    float* v, int t, float lr, const double* lpart, double* loss, cudaStream_t s);
 cudaError_t launch_mlp_sample(long long* idx, int B, long long count, unsigned long long seed, unsigned long long t,
                               cudaStream_t s);
+// IC(0) factorization in fp32 (sync-free: one thread per row, rows in increasing order per
+// thread, each row waiting on the completion marks of the rows it depends on; all CTAs
+// resident, cooperative launch). err bits: 1 breakdown, 2 unusable pattern, 4 time limit.
+cudaError_t launch_ic0_factor(int n, const int* rp, const int* ci, const double* v, float* F, int* icd,
+                              unsigned* done, unsigned* err, long long timeout_cycles, int nsm, cudaStream_t s);
 cudaError_t launch_jacobi_diag(int n, const int* rp, const int* ci, const double* v, double* dinv, unsigned* bad,
                                cudaStream_t s);
 cudaError_t launch_row_features(int n, const int* rp, const int* ci, const double* v, unsigned long long* out,

@@ -3,6 +3,9 @@
 // the Q-table copy and end-of-round merge of the batched training reading of Algorithm 1.
 #include "internal.h"
 #include "spmv.cuh"
+#include "ic0.cuh"
+
+#include <algorithm>
 
 namespace mpcg {
 
@@ -185,6 +188,122 @@ __global__ void jacobi_diag(int n, const int* __restrict__ rp, const int* __rest
   }
 }
 
+// Position of column k in the sorted columns ci[lo..hi), or -1.
+__device__ __forceinline__ int find_col(const int* __restrict__ ci, int lo, int hi, int k) {
+  --hi;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int c = ci[mid];
+    if (c == k) return mid;
+    if (c < k) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
+// IC(0) in fp32 (the SPD reading of Section 5's fp32 incomplete factorization), row by row:
+//   l_ij = (fl32(a_ij) - sum_{k<j} l_ik l_jk) / l_jj   for the stored j < i,
+//   l_ii = sqrt(fl32(a_ii) - sum_{k<i} l_ik^2),
+// each sum over the columns k stored in both rows, in increasing k (a merge of the two sorted
+// rows), every operation a single correctly rounded fp32 one. One thread per row, each
+// thread's rows in increasing order (grid stride), all CTAs resident: row i waits on the
+// completion marks of the rows j < i it reads. A broken row (columns not strictly
+// increasing, no diagonal) sets err bit 2 and a non-positive or non-finite pivot bit 1; such
+// rows are still marked complete so that no wait is left hanging. Writes F at (i, j <= i)
+// and icd[i].
+__global__ void __launch_bounds__(kThreads) ic0_factor(int n, const int* __restrict__ rp,
+                                                       const int* __restrict__ ci, const double* __restrict__ v,
+                                                       float* F, int* icd, unsigned* done, unsigned* err,
+                                                       long long limit) {
+  bool ok = true;
+  for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < n;
+       row += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)row;
+    const int e0 = rp[i], e1 = rp[i + 1];
+    int di = -1;
+    bool broken = false;
+    for (int e = e0; e < e1; ++e) {
+      const int c = ci[e];
+      if (e > e0 && c <= ci[e - 1]) broken = true;
+      if (c == i) di = e;
+    }
+    if (broken || di < 0) {
+      atomicOr(err, 2u);
+      icd[i] = e0;
+      if (e1 > e0) F[e0] = 1.0f;
+      st_release(done + i, 1u);
+      continue;
+    }
+    icd[i] = di;
+    for (int e = e0; e < di; ++e) {
+      const int j = ci[e];
+      if (ok && ld_acquire(done + j) < 1u) ok = ic_wait_slow(done + j, 1u, err, 4u, limit);
+      const int jb = rp[j], jd = __ldcg(icd + j);
+      float s = __double2float_rn(v[e]);
+      const int la = e - e0, lc = jd - jb;
+      if (la > 8 * lc || lc > 8 * la) {
+        // lengths far apart (a hub row against short ones): walk the shorter list and bisect
+        // the longer; the matches come in the same increasing order as in the merge
+        if (la <= lc) {
+          for (int a = e0; a < e; ++a) {
+            const int c = find_col(ci, jb, jd, ci[a]);
+            if (c >= 0) s = __fsub_rn(s, __fmul_rn(F[a], __ldcg(F + c)));
+          }
+        } else {
+          for (int c = jb; c < jd; ++c) {
+            const int a = find_col(ci, e0, e, ci[c]);
+            if (a >= 0) s = __fsub_rn(s, __fmul_rn(F[a], __ldcg(F + c)));
+          }
+        }
+      } else {
+        int a = e0, c = jb;
+        while (a < e && c < jd) {
+          const int ka = ci[a], kc = ci[c];
+          if (ka < kc) {
+            ++a;
+          } else if (ka > kc) {
+            ++c;
+          } else {
+            s = __fsub_rn(s, __fmul_rn(F[a], __ldcg(F + c)));
+            ++a;
+            ++c;
+          }
+        }
+      }
+      F[e] = __fdiv_rn(s, jd < rp[j + 1] ? __ldcg(F + jd) : 1.0f);
+    }
+    float s = __double2float_rn(v[di]);
+    for (int e = e0; e < di; ++e) s = __fsub_rn(s, __fmul_rn(F[e], F[e]));
+    if (!(s > 0.0f) || !isfinite(s)) {
+      atomicOr(err, 1u);
+      s = 1.0f;
+    }
+    F[di] = __fsqrt_rn(s);
+    st_release(done + i, 1u);
+  }
+}
+
+// Upper positions of the factor: (i, j), j > i, takes l_ji from row j. Every off-diagonal
+// entry needs its transposed partner (found by bisection in the other row's sorted
+// columns); a missing one sets err bit 2.
+__global__ void ic0_transpose(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                              const int* __restrict__ icd, float* F, unsigned* err) {
+  for (long long row = blockIdx.x * (long long)blockDim.x + threadIdx.x; row < n;
+       row += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)row;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      const int j = ci[e];
+      if (j == i) continue;
+      const int t = find_col(ci, rp[j], rp[j + 1], i);
+      if (t < 0) {
+        atomicOr(err, 2u);
+        continue;
+      }
+      if (j > i) F[e] = F[t];
+    }
+  }
+}
+
 __global__ void qcopy_kernel(const double* __restrict__ Q, double* Qpriv, int nlanes, long long qsize) {
   const long long total = qsize * nlanes;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
@@ -271,6 +390,23 @@ cudaError_t launch_jacobi_diag(int n, const int* rp, const int* ci, const double
   if (n == 0) return cudaSuccess;
   cudaGetLastError();
   jacobi_diag<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, rp, ci, v, dinv, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ic0_factor(int n, const int* rp, const int* ci, const double* v, float* F, int* icd,
+                              unsigned* done, unsigned* err, long long timeout_cycles, int nsm, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  cudaGetLastError();
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ic0_factor, kThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long want = ((long long)n + kThreads - 1) / kThreads;
+  const int grid = (int)std::min<long long>(want, (long long)per_sm * nsm);
+  void* args[] = {&n, (void*)&rp, (void*)&ci, (void*)&v, &F, &icd, &done, &err, &timeout_cycles};
+  e = cudaLaunchCooperativeKernel((const void*)ic0_factor, dim3(grid), dim3(kThreads), args, 0, s);
+  if (e != cudaSuccess) return e;
+  ic0_transpose<<<grid_for(n, kThreads), kThreads, 0, s>>>(n, rp, ci, icd, F, err);
   return cudaGetLastError();
 }
 

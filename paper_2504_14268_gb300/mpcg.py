@@ -89,6 +89,7 @@ SIGNATURES = {
     "mpcg_matrix_info": (_st, [_vp, C.POINTER(CStats)]),
     "mpcg_matrix_autotune": (_st, [_vp, _vp, _i32, _vp]),
     "mpcg_matrix_set_schedule": (_st, [_vp, _i32, _i32, _i32]),
+    "mpcg_matrix_ic0": (_st, [_vp, _vp, _vp, _vp]),
     "mpcg_spmv": (_st, [_vp, _vp, _i32, _vp, _vp, _i32, C.POINTER(_d), _vp]),
     "mpcg_policy_fixed": (_st, [_vp, C.POINTER(_i32), C.POINTER(_vp)]),
     "mpcg_policy_schedule": (_st, [_vp, _vp, _i32, C.POINTER(_vp)]),
@@ -424,6 +425,13 @@ class Matrix:
 
     def set_schedule(self, fmt: int, sched: int, lanes: int):
         self.ctx._check(lib().mpcg_matrix_set_schedule(self.handle, int(fmt), int(sched), int(lanes)))
+
+    def ic0(self, out=None, stream=None):
+        """IC(0) factor in fp32 (mpcg_matrix_ic0); `out`: a float32 device tensor of nnz
+        elements that receives it, or None to only compute and keep it with the matrix."""
+        _check_dtype(out, "out", "float32")
+        self.ctx._check(lib().mpcg_matrix_ic0(self.ctx.handle, self.handle, _ptr(out), _stream(stream)))
+        return out
 
     def close(self):
         if getattr(self, "handle", None):
