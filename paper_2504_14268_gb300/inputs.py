@@ -26,6 +26,7 @@ import numpy as np
 __all__ = [
     "poisson2d", "diffusion_varcoef", "fem27_aniso", "fem27_spectrum", "banded_spd", "ba_laplacian",
     "rhs_from_xstar", "rng_for", "cfg_poisson32", "cfg_train_set", "cfg_batched", "random_spd_small",
+    "synth_bbt", "poisson_subdomain", "poisson_subdomain_system",
 ]
 
 
@@ -241,6 +242,96 @@ def hub_laplacian(n: int, hubs: int, deg_lo: int, deg_hi: int, shift: float, rng
     deg = np.asarray(Wm.sum(axis=1)).ravel()
     Lap = sp.diags(deg + shift) - Wm
     return _from_scipy(Lap)
+
+
+def synth_bbt(seed: int, n: int = 5000, pairs: int = 5000, ood: bool = False):
+    """Section 5.1's synthetic family: A = B B^T + beta I with B n x n holding `pairs` entries at
+    index pairs drawn uniformly with replacement (repeated pairs add up), values N(0, 1), and
+    beta ~ U[1e-4, 1e-2]; with ood the pair count is scaled by U[0.8, 1.2] (the paper's
+    out-of-distribution test set). READINGS: the paper's "about 1% nonzeros" contradicts its
+    5000 pairs in a 5000 x 5000 B (0.02%): the pair count is used; b ~ U[-1, 1] (the paper
+    draws b from a uniform distribution without giving its range). Returns (A, b)."""
+    import scipy.sparse as sp
+
+    rng = rng_for(51, seed)
+    npairs = int(round(pairs * rng.uniform(0.8, 1.2))) if ood else pairs
+    i = rng.integers(0, n, npairs)
+    j = rng.integers(0, n, npairs)
+    v = rng.standard_normal(npairs)
+    B = sp.coo_matrix((v, (i, j)), shape=(n, n)).tocsr()
+    beta = rng.uniform(1e-4, 1e-2)
+    A = (B @ B.T + beta * sp.identity(n, format="csr")).tocsr()
+    A.sum_duplicates()
+    A.sort_indices()
+    b = rng.uniform(-1.0, 1.0, n)
+    return _from_scipy(A), b
+
+
+def _edge_function(rng):
+    """A boundary function g(t), t in [0, 1] along an edge: constant, linear or sinusoidal with
+    uniform parameters (equal odds)."""
+    kind = int(rng.integers(0, 3))
+    if kind == 0:
+        c = rng.uniform(-1, 1)
+        return lambda t: np.full_like(t, c)
+    if kind == 1:
+        c0, c1 = rng.uniform(-1, 1, 2)
+        return lambda t: c0 + c1 * t
+    a, k = rng.uniform(-1, 1), rng.uniform(0.5, 3.0)
+    return lambda t: a * np.sin(k * np.pi * t)
+
+
+def _source_function(rng):
+    """A source f(x, y): zero, sinusoidal or a low-degree polynomial (equal odds)."""
+    kind = int(rng.integers(0, 3))
+    if kind == 0:
+        return lambda x, y: np.zeros_like(x)
+    if kind == 1:
+        a, kx, ky = rng.uniform(-10, 10), rng.uniform(0.5, 3.0), rng.uniform(0.5, 3.0)
+        return lambda x, y: a * np.sin(kx * np.pi * x) * np.sin(ky * np.pi * y)
+    c = rng.uniform(-5, 5, 6)
+    return lambda x, y: c[0] + c[1] * x + c[2] * y + c[3] * x * x + c[4] * x * y + c[5] * y * y
+
+
+def poisson_subdomain_system(ax, bx, ay, by, m, f, g_left, g_right, g_bottom, g_top):
+    """Five-point -lap u = f on [ax, bx] x [ay, by] with m x m interior points (h = (b - a) /
+    (m + 1) per direction) and Dirichlet data on the four edges (each g a function of the
+    edge coordinate t in [0, 1], left/right along y, bottom/top along x) moved into b.
+    Unknowns in x-fastest order. Returns (A, b)."""
+    import scipy.sparse as sp
+
+    hx, hy = (bx - ax) / (m + 1), (by - ay) / (m + 1)
+    T = sp.diags([-np.ones(m - 1), 2 * np.ones(m), -np.ones(m - 1)], [-1, 0, 1])
+    Im = sp.identity(m)
+    A = (sp.kron(Im, T / hx ** 2) + sp.kron(T / hy ** 2, Im)).tocsr()
+    A.sort_indices()
+    xs = ax + hx * np.arange(1, m + 1)
+    ys = ay + hy * np.arange(1, m + 1)
+    X, Y = np.meshgrid(xs, ys)  # X[j, i] = x_i: rows are y, so ravel() is x-fastest
+    b = np.asarray(f(X, Y), dtype=np.float64).copy()
+    ty = (ys - ay) / (by - ay)
+    tx = (xs - ax) / (bx - ax)
+    b[:, 0] += g_left(ty) / hx ** 2
+    b[:, -1] += g_right(ty) / hx ** 2
+    b[0, :] += g_bottom(tx) / hy ** 2
+    b[-1, :] += g_top(tx) / hy ** 2
+    return _from_scipy(A), b.ravel()
+
+
+def poisson_subdomain(seed: int, m: int = 80):
+    """Section 5.2's family: a random subdomain [ax, bx] x [ay, by] of [0, 2]^2 (ax ~ U[0, 1.9],
+    bx = ax + U[0.1, 2 - ax], the same for y), 80 x 80 interior points, Dirichlet data on each
+    edge constant, linear or sinusoidal, source zero, sinusoidal or polynomial (equal odds).
+    READING: the paper names the function classes, not their parameter ranges; the ranges
+    here are the generator's own. Returns (A, b)."""
+    rng = rng_for(52, seed)
+    ax = rng.uniform(0.0, 1.9)
+    bx = ax + rng.uniform(0.1, 2.0 - ax)
+    ay = rng.uniform(0.0, 1.9)
+    by = ay + rng.uniform(0.1, 2.0 - ay)
+    f = _source_function(rng)
+    gs = [_edge_function(rng) for _ in range(4)]
+    return poisson_subdomain_system(ax, bx, ay, by, m, f, *gs)
 
 
 def random_spd_small(n: int, rng: np.random.Generator, density: float = 0.3, shift: float = 0.5):
