@@ -268,6 +268,22 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def max_over_ranks(t_local: float, dist, device) -> float:
+    """The job's time: the slowest rank's (every rank solves its own replica)."""
+    if dist is None:
+        return t_local
+    import torch
+
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, t_job: float) -> float:
+    """Solves per second of the whole job: every rank's solves over the slowest rank's time."""
+    return world * steps / t_job
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -336,11 +352,7 @@ def main():
     if dist:
         dist.barrier()
     step_ms = [a.elapsed_time(c) for a, c in ev]
-    T = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([T], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        T = float(t.item())
+    T = max_over_ranks(sum(step_ms) / 1e3, dist, "cuda")
     r0 = results[0]
     h0 = hist[: r0["iters"] + 1][: len(hist)]
     h0 = hist[: min(MAX_ITER, max(1, r0["iters"]))]
@@ -398,7 +410,7 @@ def main():
         ah = np.array(r0["action_hist"])[:, :7]
         line = {
             "metric": "solves/s to true relative residual 1e-8 (RL-mixed CG), with time vs all-FP64 CG and SpMV % HBM",
-            "value": world * args.steps / T, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "value": whole_job_rate(world, args.steps, T), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+mixed", "data": "synthetic",
             "config": {"workload": f"fem27_aniso_{args.grid}^3", "n": n, "nnz": Z, "anisotropy": ANISO, "tau": TAU,
