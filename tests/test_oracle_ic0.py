@@ -132,3 +132,15 @@ def test_ic0_cuts_cg_iterations_on_poisson():
     # low-precision operations on top of the fp32 preconditioner still converge
     mixed = O.solve(O.Options(min_k=0, precond=2), A, b, 1e-6, 1000, fixed=(3, 1, 3, 3))
     assert mixed.outcome == O.CONVERGED
+
+
+def test_fp32_preconditioner_output_is_exact_in_fp32():
+    """M^-1 r is computed in fp32, so rounding it to fp32 (p2 = fp32) changes nothing: the
+    solve is bit-identical to p2 = fp64, while p2 = fp16 is not."""
+    A, b, xs = I.cfg_poisson32()
+    o = O.Options(min_k=0, precond=2)
+    a = O.solve(o, A, b, 1e-8, 300, fixed=(4, 4, 4, 4))
+    c = O.solve(o, A, b, 1e-8, 300, fixed=(4, 3, 4, 4))
+    assert a.iters == c.iters and np.array_equal(a.x, c.x) and np.array_equal(a.hist["rho"], c.hist["rho"])
+    d = O.solve(o, A, b, 1e-8, 300, fixed=(4, 0, 4, 4))
+    assert not np.array_equal(a.hist["rho"][: d.iters], d.hist["rho"][: a.iters][: d.iters])
