@@ -176,6 +176,11 @@ enum DevErr : unsigned { DERR_NONE = 0, DERR_TIMEOUT = 1, DERR_BAD_STATE = 2 };
 // Host entry points of the kernels (cg_kernel.cu, setup_kernels.cu).
 cudaError_t launch_cg(const Launch& L, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_cg_lockstep(const Launch& L, int grid, size_t smem, cudaStream_t s);
+// the IC(0) instantiations (cg_kernel_ic.cu)
+cudaError_t launch_cg_ic(const Launch& L, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_cg_lockstep_ic(const Launch& L, int grid, size_t smem, cudaStream_t s);
+cudaError_t cg_occupancy_ic(int* blocks_per_sm, size_t smem);
+cudaError_t cg_set_smem_limit_ic(size_t bytes);
 cudaError_t cg_occupancy(int* blocks_per_sm, size_t smem);
 size_t cg_static_smem();
 cudaError_t launch_validate(int n, long long nnz, const int* rp, const int* ci, const double* v,
