@@ -5,7 +5,8 @@
 
 `solve`: a fixed-format solve of the Q1-FEM 27-point anisotropic matrix on grid^3 (the
 bench's matrix family) for exactly `--iters` iterations (tolerance 1e-30), one launch of the
-persistent kernel, autotuned product schedules. `spmv`: one product of the same matrix in
+persistent kernel, autotuned product schedules; `--precond 2` runs the IC(0)
+instantiation (the factor is computed before the solve). `spmv`: one product of the same matrix in
 the given value format with the given schedule (two launches of the product kernel: a
 warm-up and a timed one; no other launch of that kernel).
 Prints the launch's iteration count and per-phase times (solve) or milliseconds (spmv).
@@ -26,6 +27,7 @@ def main():
     ap.add_argument("--iters", type=int, default=20)
     ap.add_argument("--sched", type=int, default=2)
     ap.add_argument("--lanes", type=int, default=1)
+    ap.add_argument("--precond", type=int, default=0, help="solve: 0 none, 1 Jacobi, 2 fp32 IC(0)")
     args = ap.parse_args()
 
     import torch
@@ -38,12 +40,14 @@ def main():
 
     A = I.fem27_aniso(args.grid, args.aniso)
     n, rp, ci, val = A
-    ctx = M.Context(0, M.Options(min_k=0))
+    ctx = M.Context(0, M.Options(min_k=0, precond=args.precond if args.what == "solve" else 0))
     mat = ctx.matrix((n, torch.as_tensor(rp).cuda(), torch.as_tensor(ci).cuda(), torch.as_tensor(val).cuda()))
     fm = tuple(int(v) for v in args.fmt.split(","))
     b = torch.as_tensor(I.rhs_from_xstar(A, np.random.default_rng(0))[1]).cuda()
     if args.what == "solve":
         mat.autotune(3)
+        if args.precond == 2:
+            mat.ic0()
         pol = ctx.policy_fixed(fm if len(fm) == 4 else fm * 4)
         x = torch.zeros_like(b)
         res, h = ctx.solve(mat, b, x, 1e-30, args.iters, pol, history_cap=args.iters + 1)
