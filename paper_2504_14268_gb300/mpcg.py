@@ -196,7 +196,7 @@ class Options:
     on_breakdown: int = 0
     mlp_hidden: int = 64
     batch_mode: int = 0
-    precond: int = 0
+    precond: int = 0  # 0: M = I; 1: Jacobi; 2: fp32 IC(0) (factor kept with the matrix)
 
     def c(self) -> COptions:
         o = COptions()
