@@ -216,6 +216,16 @@ mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, 
  * non-positive pivot (IC(0) exists for M-matrices, not for every SPD matrix) is INVALID_ARG
  * "breaks down". Synchronises `stream`. */
 mpcg_status mpcg_matrix_ic0(mpcg_ctx_t ctx, mpcg_matrix_t A, float* factor, void* stream);
+/* Dependency levels of the two triangular substitutions of a CSR pattern (host pointers,
+ * no device work; the scheduling analysis of the IC(0) substitutions): level_lower[i] =
+ * 0 for a row without stored columns j < i, else 1 + the largest level_lower[j] over them
+ * (rows of one level of L y = r are independent once the earlier levels are done);
+ * level_upper[i] the same over the columns j > i (for L^T w = y, rows taken from the last).
+ * depth[0], depth[1] receive the number of levels of each. The caller owns all arrays
+ * (level arrays of n int32). INVALID_ARG for n < 0, NULL arrays, a decreasing row_ptr or a
+ * column outside [0, n). */
+mpcg_status mpcg_csr_levels(int32_t n, const int32_t* row_ptr, const int32_t* col, int32_t* level_lower,
+                            int32_t* level_upper, int32_t* depth);
 /* Forces the SpMV schedule of value format `fmt` (sched: 0 = sub-warp vector CSR with
  * `lanes` lanes per row (1, 2, 4, 8, 16 or 32); 1 = staged stream CSR, shared-memory tiles
  * filled by bulk copies, `lanes` = 1, 2 or 4 lanes per row; 2 = one thread per row reading

@@ -845,6 +845,37 @@ mpcg_status mpcg_matrix_info(mpcg_matrix_t A, mpcg_matrix_stats* info) {
   return MPCG_OK;
 }
 
+mpcg_status mpcg_csr_levels(int32_t n, const int32_t* row_ptr, const int32_t* col, int32_t* level_lower,
+                            int32_t* level_upper, int32_t* depth) {
+  if (n < 0 || !depth || (n > 0 && (!row_ptr || !col || !level_lower || !level_upper))) return MPCG_ERR_INVALID_ARG;
+  depth[0] = depth[1] = 0;
+  if (n == 0) return MPCG_OK;
+  if (row_ptr[0] != 0) return MPCG_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < n; ++i) {
+    if (row_ptr[i + 1] < row_ptr[i]) return MPCG_ERR_INVALID_ARG;
+    for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+      if (col[e] < 0 || col[e] >= n) return MPCG_ERR_INVALID_ARG;
+  }
+  int32_t dl = 0, du = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t l = 0;
+    for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+      if (col[e] < i) l = std::max(l, level_lower[col[e]] + 1);
+    level_lower[i] = l;
+    dl = std::max(dl, l + 1);
+  }
+  for (int32_t i = n - 1; i >= 0; --i) {
+    int32_t l = 0;
+    for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+      if (col[e] > i) l = std::max(l, level_upper[col[e]] + 1);
+    level_upper[i] = l;
+    du = std::max(du, l + 1);
+  }
+  depth[0] = dl;
+  depth[1] = du;
+  return MPCG_OK;
+}
+
 mpcg_status mpcg_matrix_ic0(mpcg_ctx_t ctx, mpcg_matrix_t A, float* factor, void* stream) {
   if (!ctx || !A) return fail(ctx, MPCG_ERR_INVALID_ARG, "NULL argument");
   if (A->ctx != ctx) return fail(ctx, MPCG_ERR_INVALID_ARG, "matrix belongs to another context");

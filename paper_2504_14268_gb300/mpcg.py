@@ -90,6 +90,7 @@ SIGNATURES = {
     "mpcg_matrix_autotune": (_st, [_vp, _vp, _i32, _vp]),
     "mpcg_matrix_set_schedule": (_st, [_vp, _i32, _i32, _i32]),
     "mpcg_matrix_ic0": (_st, [_vp, _vp, _vp, _vp]),
+    "mpcg_csr_levels": (_st, [_i32, _vp, _vp, _vp, _vp, _vp]),
     "mpcg_spmv": (_st, [_vp, _vp, _i32, _vp, _vp, _i32, C.POINTER(_d), _vp]),
     "mpcg_policy_fixed": (_st, [_vp, C.POINTER(_i32), C.POINTER(_vp)]),
     "mpcg_policy_schedule": (_st, [_vp, _vp, _i32, C.POINTER(_vp)]),
@@ -507,3 +508,16 @@ class Graph:
 
 def mlp_nparams(hidden: int, nprec: int) -> int:
     return int(lib().mpcg_mlp_nparams(hidden, nprec))
+
+
+def csr_levels(A):
+    """mpcg_csr_levels on a host CSR (n, row_ptr, col, ...): the dependency levels of the
+    substitutions L y = r and L^T w = y over its pattern, and their depths."""
+    n, rp, ci = int(A[0]), np.ascontiguousarray(A[1], dtype=np.int32), np.ascontiguousarray(A[2], dtype=np.int32)
+    lo = np.zeros(max(n, 1), dtype=np.int32)
+    up = np.zeros(max(n, 1), dtype=np.int32)
+    depth = np.zeros(2, dtype=np.int32)
+    st = lib().mpcg_csr_levels(n, _ptr(rp), _ptr(ci), _ptr(lo), _ptr(up), _ptr(depth))
+    if st != 0:
+        raise MpcgError(st, "mpcg_csr_levels: invalid CSR")
+    return lo[:n], up[:n], (int(depth[0]), int(depth[1]))
