@@ -111,7 +111,9 @@ typedef struct {
   int32_t op_mask[4];      /* per operation, bitmask of the entries of precs the policy may
                               choose (bit a = precs[a]); 0 allows all. Section 5 notes the
                               precision set can be customised; a mask customises it per
-                              operation (greedy, exploration and fallback respect it)    */
+                              operation: greedy choice, exploration, the unvisited
+                              fallback and the bootstrap max of the Section 4.1 update
+                              (max over the operation's allowed entries) respect it     */
   int32_t on_breakdown;    /* 0: a breakdown ends the solve (paper); 1: inference solves
                               recompute r = b - A x in fp64, restart with p = r and finish
                               with every operation in fp64 (at most once per solve)     */
@@ -132,6 +134,11 @@ typedef struct {
                             * and the first and restart directions are p = L^-T L^-1 r.
                             * The factor is computed on the first such solve of a matrix
                             * and kept with it.                                          */
+  double edge_tol;         /* greedy decisions of a tabular policy taken at a residual rho_k
+                            * with |rho_k / theta_m - 1| <= edge_tol for a residual-bin
+                            * threshold theta_m (Section 4.1's bin edges) are counted in
+                            * mpcg_result.near_edge_count: there a rounding-level change of
+                            * rho can move the state to the next bin (5e-3)              */
 } mpcg_options;
 
 /* Result of one solve. */
@@ -143,6 +150,9 @@ typedef struct {
   int32_t n_true_checks;   /* residual recomputations during the solve                  */
   int32_t n_restarts;      /* fp64 restarts after a breakdown (option on_breakdown)      */
   int64_t action_hist[MPCG_NUM_OPS][MPCG_MAX_PREC]; /* iterations per (op, format)       */
+  int32_t near_edge_count; /* greedy tabular decisions taken within edge_tol of a residual-bin
+                              edge (options.edge_tol); 0 for other policies             */
+  int32_t reserved;
 } mpcg_result;
 
 /* One record per iteration k (80 bytes). rho is rho_{k+1} after the iteration (the true
@@ -315,11 +325,14 @@ mpcg_status mpcg_graph_destroy(mpcg_graph_t g);
  * 1,048,576 rows (about 29 MiB), which every GPU that loads the library holds until the
  * process exits. Systems with more rows are rejected with MPCG_ERR_INVALID_ARG. b and x must
  * be device pointers; the matrix and the policy are created beforehand with the calls
- * above. The first call on a device looks up the array's device address, so make that
- * first call before any stream capture. All calls share the one array: calls whose work
- * overlaps on the GPU (other streams, other host threads) race and must not be issued.
- * Contexts with precond = 2 (IC(0), whose factor and marks need memory) are rejected with
- * MPCG_ERR_INVALID_ARG. */
+ * above. Each call looks up the array's device address with the context's device current;
+ * the first lookup on a device loads the library's device code, so make the first call on
+ * a device before any stream capture. The call synchronises `stream` before it returns.
+ * All calls share the one array and it keeps the last call's contents (the barriers and
+ * status word are cleared by each call): calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must not be issued. The system always runs as one
+ * team of CTAs (options.batch_mode is ignored). Contexts with precond = 2 (IC(0), whose
+ * factor and marks need memory) are rejected with MPCG_ERR_INVALID_ARG. */
 mpcg_status mpcg_solve_noalloc(mpcg_ctx_t ctx, mpcg_matrix_t A, const double* b, double* x, double tol,
                                int32_t max_iter, mpcg_policy_t policy, mpcg_result* res, void* stream);
 
@@ -372,6 +385,15 @@ mpcg_status mpcg_mlp_loss_grad(mpcg_ctx_t ctx, const float* params, int64_t B, c
 mpcg_status mpcg_mlp_train(mpcg_ctx_t ctx, mpcg_policy_t mlp, const mpcg_transition* data, int64_t count,
                            int32_t steps, int32_t batch, float lr, int32_t target_sync, uint64_t seed,
                            float* loss_out, void* stream);
+
+/* One Adam step (Kingma & Ba, ICLR 2015; the optimiser of mpcg_mlp_train) on host arrays of
+ * mpcg_mlp_nparams(options.mlp_hidden, options.nprec) floats: m = 0.9 m + 0.1 g,
+ * v = 0.999 v + 0.001 g^2, params -= lr (m / (1 - 0.9^t)) / (sqrt(v / (1 - 0.999^t)) + 1e-8),
+ * in fp32 on the device with the kernel mpcg_mlp_train uses. params, m, v are updated in
+ * place; grad is read. t >= 1 is the step number. Errors: INVALID_ARG (NULL, t < 1), CUDA,
+ * OOM. */
+mpcg_status mpcg_mlp_adam(mpcg_ctx_t ctx, float* params, float* m, float* v, const float* grad, int32_t t, float lr,
+                          void* stream);
 
 /* The fitted-Q regression targets of the MLP Q-function (the one-step backup of the
  * Section 4.1 update with the table replaced by the network): y[b][j] = rew[b] +

@@ -113,6 +113,8 @@ def lib():
             L.orc_true_residual.restype = d
             L.orc_true_residual.argtypes = [i, vp, vp, vp, vp, vp, vp]
             L.orc_q_update.argtypes = [C.POINTER(Opts), vp, vp, vp]
+            L.orc_greedy_action.restype = i
+            L.orc_greedy_action.argtypes = [C.POINTER(Opts), vp, vp, i, d, vp]
             L.orc_run.restype = i
             L.orc_run.argtypes = [C.POINTER(Opts), i, vp, vp, vp, vp, vp, d, i, C.POINTER(Policy), i,
                                   u64, u64, d, vp, vp, vp, vp, C.POINTER(Result)]
@@ -416,6 +418,14 @@ def train_round(opts: Options, mats, bs, tau: float, t_max: int, e: int, E: int,
                           arr([c[3] for c in cs]), arr(bs), tau, t_max, e, E, _p(qt.Q), _p(qt.visits),
                           _p(iters))
     return iters
+
+
+def greedy_action(opts: Options, qt: QTable, k: int, rho: float):
+    """Algorithm 2's decision at iteration k with residual rho: (state, formats of ops 1-4)."""
+    o = opts.c()
+    act = np.zeros(4, dtype=np.int32)
+    s = lib().orc_greedy_action(C.byref(o), _p(qt.Q), _p(qt.visits), int(k), float(rho), _p(act))
+    return s, tuple(int(opts.precs[a]) for a in act)
 
 
 def q_update(opts: Options, qt: QTable, trans: np.ndarray):

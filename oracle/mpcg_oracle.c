@@ -250,10 +250,15 @@ static int random_allowed(const orc_opts* o, int j, uint32_t pick) {
   return 0;
 }
 
-static double max_row(const double* row, int nprec) {
-  double m = row[0];
-  for (int a = 1; a < nprec; ++a)
-    if (row[a] > m) m = row[a];
+/* max_{p in P_j} Q_j(s', p): the bootstrap term of the Section 4.1 update, taken over the
+ * entries operation j may choose. READING: Section 5 lets the precision set be customised;
+ * with a per-operation set P_j (op_mask) the update's max runs over P_j, the same set the
+ * greedy and exploring choices use (entries outside P_j are never updated and must not
+ * enter the target). */
+static double max_allowed(const orc_opts* o, int j, const double* row) {
+  double m = -INFINITY;
+  for (int a = 0; a < o->nprec; ++a)
+    if (allowed(o, j, a) && row[a] > m) m = row[a];
   return m;
 }
 
@@ -661,14 +666,32 @@ static int select_qtable(const orc_opts* o, const orc_policy* pol, int mode, int
   return argmax_allowed(o, j, row);
 }
 
-/* Q_j(s, a_j) += lr (R + gamma max_p Q_j(s', p) - Q_j(s, a_j))   (Section 4.1, Alg. 1 non-terminal)
- * Q_j(s, a_j) += lr (R - Q_j(s, a_j))                            (Alg. 1 terminal)             */
+/* Algorithm 2's decision at iteration k with residual rho_k: state s = (i_k, j_k) of
+ * Section 4.1, then per operation the greedy entry of Q_j(s, .) (first-index argmax over the
+ * allowed entries; a never-updated row takes the fallback). act[j] receives indices into
+ * precs. Returns s. */
+int orc_greedy_action(const orc_opts* o, const double* Q, const int32_t* visits, int k, double rho,
+                      int32_t act[4]) {
+  orc_policy pol;
+  memset(&pol, 0, sizeof(pol));
+  pol.kind = ORC_POL_QTABLE;
+  pol.Q = (double*)Q;
+  pol.visits = (int32_t*)visits;
+  int s = orc_state(o, k, rho);
+  int explored = 0;
+  for (int j = 0; j < 4; ++j) act[j] = select_qtable(o, &pol, ORC_MODE_INFER, j, s, 0.0, 0, 0, k, &explored);
+  return s;
+}
+
+/* Q_j(s, a_j) += lr (R + gamma max_{p in P_j} Q_j(s', p) - Q_j(s, a_j))   (Section 4.1, Alg. 1 non-terminal)
+ * Q_j(s, a_j) += lr (R - Q_j(s, a_j))                                    (Alg. 1 terminal)
+ * P_j is operation j's allowed set (all of P unless op_mask[j] restricts it). */
 void orc_q_update(const orc_opts* o, double* Q, int32_t* visits, const orc_transition* t) {
   int S = o->b_bins * o->r_bins;
   for (int j = 0; j < 4; ++j) {
     double* row = Q + ((int64_t)j * S + t->s) * o->nprec;
     double target = t->reward;
-    if (!t->terminal) target += o->gamma * max_row(Q + ((int64_t)j * S + t->s_next) * o->nprec, o->nprec);
+    if (!t->terminal) target += o->gamma * max_allowed(o, j, Q + ((int64_t)j * S + t->s_next) * o->nprec);
     row[t->act[j]] += o->lr * (target - row[t->act[j]]);
     if (visits) visits[(int64_t)j * S + t->s] += 1;
   }

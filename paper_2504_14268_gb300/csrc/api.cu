@@ -177,6 +177,7 @@ mpcg_status build_optview(mpcg_ctx_t ctx, const mpcg_options& o, OptView& v) {
   if (o.mlp_hidden < 1 || o.mlp_hidden > kMaxHidden) return fail(ctx, MPCG_ERR_INVALID_ARG, "mlp_hidden must be in [1, %d]", kMaxHidden);
   if (o.batch_mode < 0 || o.batch_mode > 2) return fail(ctx, MPCG_ERR_INVALID_ARG, "batch_mode must be 0, 1 or 2");
   if (o.precond < 0 || o.precond > 2) return fail(ctx, MPCG_ERR_INVALID_ARG, "precond must be 0, 1 or 2");
+  if (!(o.edge_tol >= 0.0 && o.edge_tol < 1.0)) return fail(ctx, MPCG_ERR_INVALID_ARG, "edge_tol must be in [0, 1)");
   for (int a = 0; a < o.nprec; ++a)
     if (!valid_fmt(o.precs[a])) return fail(ctx, MPCG_ERR_INVALID_ARG, "precs[%d] = %d is not a format code", a, o.precs[a]);
   if (o.unvisited_fallback != -1 && !valid_fmt(o.unvisited_fallback))
@@ -214,6 +215,7 @@ mpcg_status build_optview(mpcg_ctx_t ctx, const mpcg_options& o, OptView& v) {
   v.warm_start = o.warm_start;
   v.on_breakdown = o.on_breakdown;
   v.precond = o.precond;
+  v.edge_tol = o.edge_tol;
   for (int j = 0; j < 4; ++j) {
     const unsigned all = (1u << o.nprec) - 1u;
     const unsigned m = o.op_mask[j] ? ((unsigned)o.op_mask[j] & all) : all;
@@ -642,6 +644,7 @@ void mpcg_options_default(mpcg_options* o) {
   o->mlp_hidden = 64;
   o->batch_mode = 0;
   o->precond = 0;
+  o->edge_tol = 5e-3;
 }
 
 mpcg_status mpcg_create(mpcg_ctx_t* out, int device, const mpcg_options* opt) {
@@ -1372,6 +1375,14 @@ mpcg_status mpcg_graph_destroy(mpcg_graph_t g) {
   return MPCG_OK;
 }
 
+// The options' per-operation masks (bit p = entry p of precs; a 0 mask allows every entry).
+static OpMask op_masks(const mpcg_options& o) {
+  OpMask m;
+  const unsigned all = (1u << o.nprec) - 1u;
+  for (int j = 0; j < 4; ++j) m.m[j] = o.op_mask[j] ? ((unsigned)o.op_mask[j] & all) : all;
+  return m;
+}
+
 // ---- training -----------------------------------------------------------------------------
 
 mpcg_status mpcg_train_qtable(mpcg_ctx_t ctx, int32_t nsys, const mpcg_matrix_t* A, const double* const* b, double tol,
@@ -1417,7 +1428,7 @@ mpcg_status mpcg_train_qtable(mpcg_ctx_t ctx, int32_t nsys, const mpcg_matrix_t*
     st = enqueue_plan(ctx, pl, s);
     if (st != MPCG_OK) return st;
     CK(ctx, launch_qmerge(inout->Q.as<double>(), inout->visits.as<int>(), pl.trans.as<Transition>(),
-                          pl.st.as<SysState>(), nsys, t_max, S, o.nprec, o.lr, o.gamma, s));
+                          pl.st.as<SysState>(), nsys, t_max, S, o.nprec, o.lr, o.gamma, op_masks(o), s));
     if (iters_out || e == episodes) {
       st = finish_plan(ctx, pl, rr.data(), s);
       if (st != MPCG_OK) return st;
@@ -1490,14 +1501,6 @@ mpcg_status mpcg_collect(mpcg_ctx_t ctx, int32_t nsys, const mpcg_matrix_t* A, c
   }
   *count = c;
   return MPCG_OK;
-}
-
-// The options' per-operation masks with 0 meaning every entry of precs.
-static OpMask op_masks(const mpcg_options& o) {
-  OpMask m;
-  const unsigned all = (1u << o.nprec) - 1u;
-  for (int j = 0; j < 4; ++j) m.m[j] = o.op_mask[j] ? ((unsigned)o.op_mask[j] & all) : all;
-  return m;
 }
 
 mpcg_status mpcg_mlp_loss_grad(mpcg_ctx_t ctx, const float* params, int64_t B, const float* feats, const int32_t* acts,
@@ -1601,6 +1604,33 @@ mpcg_status mpcg_mlp_train(mpcg_ctx_t ctx, mpcg_policy_t P, const mpcg_transitio
   return MPCG_OK;
 }
 
+mpcg_status mpcg_mlp_adam(mpcg_ctx_t ctx, float* params, float* m, float* v, const float* grad, int32_t t, float lr,
+                          void* stream) {
+  if (!ctx || !params || !m || !v || !grad || t < 1) return fail(ctx, MPCG_ERR_INVALID_ARG, "bad Adam arguments");
+  ctx->err.clear();
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long np = mlp_nparams_dev(ctx->opt.mlp_hidden, ctx->opt.nprec);
+  const size_t bytes = sizeof(float) * (size_t)np;
+  DevBuf dw, dm, dv, dg;
+  CK(ctx, dw.ensure(bytes));
+  CK(ctx, dm.ensure(bytes));
+  CK(ctx, dv.ensure(bytes));
+  CK(ctx, dg.ensure(bytes));
+  CK(ctx, cudaMemcpyAsync(dw.p, params, bytes, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(dm.p, m, bytes, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(dv.p, v, bytes, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaMemcpyAsync(dg.p, grad, bytes, cudaMemcpyHostToDevice, s));
+  // the gradient is the single "partial" of the reduction; no gradient or loss output
+  CK(ctx, launch_mlp_reduce_adam(dg.as<float>(), 1, np, nullptr, dw.as<float>(), dm.as<float>(), dv.as<float>(), t, lr,
+                                 nullptr, nullptr, s));
+  CK(ctx, cudaMemcpyAsync(params, dw.p, bytes, cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaMemcpyAsync(m, dm.p, bytes, cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaMemcpyAsync(v, dv.p, bytes, cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  return MPCG_OK;
+}
+
 mpcg_status mpcg_mlp_targets(mpcg_ctx_t ctx, const float* target_params, int64_t B, const float* feats_next,
                              const float* rew, const int32_t* done, float* y, void* stream) {
   if (!ctx || !target_params || B < 1 || !feats_next || !rew || !done || !y)
@@ -1645,11 +1675,6 @@ constexpr size_t kNoAllocBytes = kNoAllocCtrl + 28 * (size_t)kNoAllocMaxRows + 4
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-namespace {
-// Device address of g_noalloc_scratch per device ordinal, looked up once per device.
-void* g_noalloc_ptr[64] = {nullptr};
-}  // namespace
-
 mpcg_status mpcg_solve_noalloc(mpcg_ctx_t ctx, mpcg_matrix_t A, const double* b, double* x, double tol,
                                int32_t max_iter, mpcg_policy_t policy, mpcg_result* res, void* stream) {
   if (!ctx || !A || !policy || !res) return fail(ctx, MPCG_ERR_INVALID_ARG, "NULL argument");
@@ -1666,17 +1691,16 @@ mpcg_status mpcg_solve_noalloc(mpcg_ctx_t ctx, mpcg_matrix_t A, const double* b,
     return fail(ctx, MPCG_ERR_INVALID_ARG, "the no-allocation solve does not run the incomplete Cholesky preconditioner");
   if (!(tol >= 0.0) || max_iter < 0) return fail(ctx, MPCG_ERR_INVALID_ARG, "tol must be >= 0 and max_iter >= 0");
   if (A->ctx != ctx || policy->ctx != ctx) return fail(ctx, MPCG_ERR_INVALID_ARG, "objects belong to another context");
-  if (ctx->device < 0 || ctx->device >= 64) return fail(ctx, MPCG_ERR_INVALID_ARG, "device ordinal out of range");
   cudaError_t ce = cudaSetDevice(ctx->device);
   if (ce != cudaSuccess) return fail(ctx, MPCG_ERR_CUDA, "cudaSetDevice failed: %s", cudaGetErrorString(ce));
-  if (!g_noalloc_ptr[ctx->device]) {
-    void* ptr = nullptr;
-    ce = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (ce != cudaSuccess || !ptr)
-      return fail(ctx, MPCG_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(ce));
-    g_noalloc_ptr[ctx->device] = ptr;
-  }
-  unsigned char* base = (unsigned char*)g_noalloc_ptr[ctx->device];
+  // The array's device address in the current context, looked up with the context's device
+  // current on every call (the first lookup on a device loads the library's device code; a
+  // cached address would go stale if the context were torn down and created again).
+  void* ptr = nullptr;
+  ce = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (ce != cudaSuccess || !ptr)
+    return fail(ctx, MPCG_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(ce));
+  unsigned char* base = (unsigned char*)ptr;
   cudaStream_t s = (cudaStream_t)stream;
   const bool stream_shape = uses_stream(A->dm);
   const int grid = ctx->nsm * (stream_shape ? ctx->occ_s : ctx->occ);
@@ -1758,7 +1782,8 @@ mpcg_status mpcg_solve_noalloc(mpcg_ctx_t ctx, mpcg_matrix_t A, const double* b,
   L.opt = ctx->ov;
   L.train = 0;
   L.stream_stage = stream_shape ? kStageBytes : 0;
-  L.timeout_cycles = kTimeoutCycles;
+  L.timeout_cycles = kTimeoutCycles;  // the same wait limit as mpcg_solve, with its override
+  if (const char* t = getenv("MPCG_TIMEOUT_CYCLES")) L.timeout_cycles = atoll(t);
   cudaGetLastError();
   CK(ctx, launch_cg(L, grid, stream_shape ? 2 * (size_t)kStageBytes : 0, s));
   unsigned herr = 0;

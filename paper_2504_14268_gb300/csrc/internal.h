@@ -101,6 +101,7 @@ struct SysState {
   int fp64_lock, n_restart;   // after a breakdown restart every operation runs in fp64
   unsigned long long t_last;  // globaltimer at the previous team barrier
   unsigned ns_a, ns_b;        // phase times of the current iteration
+  int near_edge, pad_ne;      // greedy tabular decisions taken near a residual-bin edge
   long long counts[4][8];
 };
 
@@ -131,6 +132,7 @@ struct OptView {
   int true_every, true_at_conv, warm_start, t_bin;
   int on_breakdown, precond;
   int op_mask[4];           // allowed action indices per operation (all bits set = no restriction)
+  double edge_tol;          // relative distance to a residual-bin threshold counted as near an edge
 };
 
 // Arguments of one launch of the persistent kernel.
@@ -169,6 +171,15 @@ struct Launch {
   int4* lk_seg;             // [grid][nsys + 1] slices of each CTA: (system, r0, r1, partial slot)
   int* lk_nseg;             // [grid] number of slices of each CTA
 };
+
+// max over the entries a of a Q-table row that bit a of `mask` allows (the bootstrap term
+// of the Section 4.1 update over an operation's customised precision set).
+__device__ __forceinline__ double row_max_allowed(const double* row, int n, unsigned mask) {
+  double m = -__longlong_as_double(0x7ff0000000000000ll);
+  for (int a = 0; a < n; ++a)
+    if (((mask >> a) & 1u) && row[a] > m) m = row[a];
+  return m;
+}
 
 // Device status word values.
 enum DevErr : unsigned { DERR_NONE = 0, DERR_TIMEOUT = 1, DERR_BAD_STATE = 2 };
@@ -220,6 +231,6 @@ cudaError_t spmv_occupancy(int* blocks_per_sm, size_t smem);
 cudaError_t set_smem_limits(size_t bytes);
 cudaError_t launch_qcopy(const double* Q, double* Qpriv, int nlanes, long long qsize, cudaStream_t s);
 cudaError_t launch_qmerge(double* Q, int* visits, const Transition* trans, const SysState* st, int nlanes, int cap,
-                          int S, int nprec, double lr, double gamma, cudaStream_t s);
+                          int S, int nprec, double lr, double gamma, OpMask mask, cudaStream_t s);
 
 }  // namespace mpcg

@@ -315,7 +315,7 @@ __global__ void qcopy_kernel(const double* __restrict__ Q, double* Qpriv, int nl
 // operation tables are independent, so one thread per table replays them in that order.
 __global__ void qmerge_kernel(double* Q, int* visits, const Transition* __restrict__ trans,
                               const SysState* __restrict__ st, int nlanes, int cap, int S, int nprec, double lr,
-                              double gamma, int use_smem) {
+                              double gamma, OpMask mask, int use_smem) {
   extern __shared__ double tab[];
   const long long tsize = (long long)S * nprec;
   double* T = use_smem ? tab : Q;
@@ -333,12 +333,9 @@ __global__ void qmerge_kernel(double* Q, int* visits, const Transition* __restri
         const Transition tr = trans[(long long)l * cap + t];
         double* row = Tj + (long long)tr.s * nprec;
         double target = tr.reward;
-        if (!tr.terminal) {
-          const double* nx = Tj + (long long)tr.s_next * nprec;
-          double mx = nx[0];
-          for (int a = 1; a < nprec; ++a) mx = nx[a] > mx ? nx[a] : mx;
-          target = __dadd_rn(target, __dmul_rn(gamma, mx));
-        }
+        if (!tr.terminal)  // max over the operation's allowed entries
+          target = __dadd_rn(target, __dmul_rn(gamma, row_max_allowed(Tj + (long long)tr.s_next * nprec, nprec,
+                                                                      mask.m[j])));
         const int a = tr.act[j];
         const double cur = row[a];
         row[a] = __dadd_rn(cur, __dmul_rn(lr, __dsub_rn(target, cur)));
@@ -458,11 +455,12 @@ cudaError_t launch_qcopy(const double* Q, double* Qpriv, int nlanes, long long q
 }
 
 cudaError_t launch_qmerge(double* Q, int* visits, const Transition* trans, const SysState* st, int nlanes, int cap,
-                          int S, int nprec, double lr, double gamma, cudaStream_t s) {
+                          int S, int nprec, double lr, double gamma, OpMask mask, cudaStream_t s) {
   const size_t bytes = sizeof(double) * 4 * (size_t)S * nprec;
   const int use_smem = bytes <= 48 * 1024 ? 1 : 0;
   cudaGetLastError();
-  qmerge_kernel<<<1, 128, use_smem ? bytes : 0, s>>>(Q, visits, trans, st, nlanes, cap, S, nprec, lr, gamma, use_smem);
+  qmerge_kernel<<<1, 128, use_smem ? bytes : 0, s>>>(Q, visits, trans, st, nlanes, cap, S, nprec, lr, gamma, mask,
+                                                     use_smem);
   return cudaGetLastError();
 }
 

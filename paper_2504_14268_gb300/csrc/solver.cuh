@@ -223,11 +223,6 @@ __device__ double reward_of(const OptView& o, double rho, const int* act, double
   return r;
 }
 
-__device__ __forceinline__ double row_max(const double* row, int n) {
-  double m = row[0];
-  for (int a = 1; a < n; ++a) m = row[a] > m ? row[a] : m;
-  return m;
-}
 
 // First-index argmax over the allowed entries (bit a of mask).
 __device__ __forceinline__ int row_argmax(const double* row, int n, unsigned mask) {
@@ -248,13 +243,16 @@ __device__ __forceinline__ int kth_allowed(unsigned mask, int k) {
   return 0;
 }
 
-// Q_j(s, a_j) += lr (R + gamma max_p Q_j(s', p) - Q_j(s, a_j)), terminal without the max term.
+// Q_j(s, a_j) += lr (R + gamma max_{p in P_j} Q_j(s', p) - Q_j(s, a_j)), terminal without the max
+// term; P_j = the entries operation j may choose (op_mask).
 __device__ void q_update(double* Q, const OptView& o, const Transition& t) {
   const int S = o.b_bins * o.r_bins;
   for (int j = 0; j < 4; ++j) {
     double* row = Q + ((long long)j * S + t.s) * o.nprec;
     double target = t.reward;
-    if (!t.terminal) target = __dadd_rn(target, __dmul_rn(o.gamma, row_max(Q + ((long long)j * S + t.s_next) * o.nprec, o.nprec)));
+    if (!t.terminal)
+      target = __dadd_rn(target, __dmul_rn(o.gamma, row_max_allowed(Q + ((long long)j * S + t.s_next) * o.nprec,
+                                                                     o.nprec, (unsigned)o.op_mask[j])));
     const double cur = row[t.act[j]];
     row[t.act[j]] = __dadd_rn(cur, __dmul_rn(o.lr, __dsub_rn(target, cur)));
   }
@@ -342,6 +340,11 @@ __device__ void choose_action(const Launch& L, const DevSys& S, SysState* st, in
           const double* Qsrc = L.train ? S.Qpriv : P.Q;
           const double* row = Qsrc + ((long long)j * (o.b_bins * o.r_bins) + s) * o.nprec;
           act = row_argmax(row, o.nprec, mask);
+          if (!L.train && j == 0) {  // one count per decision: rho within edge_tol of a bin edge
+            int near = 0;
+            for (int m = 1; m < o.r_bins; ++m) near |= fabs(rho / o.thr[m] - 1.0) <= o.edge_tol ? 1 : 0;
+            st->near_edge += near;
+          }
           if (!L.train && P.visits && o.fallback_fmt >= 0 && o.fallback_idx >= 0 && ((mask >> o.fallback_idx) & 1u) &&
               P.visits[j * (o.b_bins * o.r_bins) + s] == 0)
             act = o.fallback_idx;
@@ -610,6 +613,7 @@ __device__ void step_init(const Launch& L, const DevSys& S, SysState* st, double
     st->fp64_lock = 0;
     st->n_restart = 0;
     st->ns_a = st->ns_b = 0;
+    st->near_edge = 0;
     st->t_last = gtime();
     for (int j = 0; j < 4; ++j) {
       st->prev_act[j] = 0;
@@ -870,6 +874,8 @@ __device__ void step_final(const Launch& L, const DevSys& S, SysState* st, int s
   res.n_restarts = st->n_restart;
   for (int j = 0; j < 4; ++j)
     for (int f = 0; f < 8; ++f) res.action_hist[j][f] = st->counts[j][f];
+  res.near_edge_count = st->near_edge;
+  res.reserved = 0;
   L.res[sid] = res;
 }
 

@@ -46,13 +46,14 @@ class COptions(C.Structure):
         ("mlp_hidden", C.c_int32),
         ("batch_mode", C.c_int32),
         ("precond", C.c_int32),
+        ("edge_tol", C.c_double),
     ]
 
 
 class CResult(C.Structure):
     _fields_ = [("outcome", C.c_int32), ("iters", C.c_int32), ("rel_res_rec", C.c_double),
                 ("rel_res_true", C.c_double), ("n_true_checks", C.c_int32), ("n_restarts", C.c_int32),
-                ("action_hist", (C.c_int64 * 8) * 4)]
+                ("action_hist", (C.c_int64 * 8) * 4), ("near_edge_count", C.c_int32), ("reserved", C.c_int32)]
 
 
 class CStats(C.Structure):
@@ -114,6 +115,7 @@ SIGNATURES = {
     "mpcg_mlp_loss_grad": (_st, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, C.POINTER(_d), _vp]),
     "mpcg_mlp_train": (_st, [_vp, _vp, _vp, _i64, _i32, _i32, C.c_float, _i32, C.c_uint64, _vp, _vp]),
     "mpcg_mlp_targets": (_st, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]),
+    "mpcg_mlp_adam": (_st, [_vp, _vp, _vp, _vp, _vp, _i32, C.c_float, _vp]),
 }
 
 _LIB = None
@@ -198,6 +200,7 @@ class Options:
     mlp_hidden: int = 64
     batch_mode: int = 0
     precond: int = 0  # 0: M = I; 1: Jacobi; 2: fp32 IC(0) (factor kept with the matrix)
+    edge_tol: float = 5e-3  # greedy decisions this close (relative) to a residual-bin edge are counted
 
     def c(self) -> COptions:
         o = COptions()
@@ -222,7 +225,8 @@ class Options:
 
 def result_dict(r: CResult) -> dict:
     return dict(outcome=r.outcome, iters=r.iters, rel_res_rec=r.rel_res_rec, rel_res_true=r.rel_res_true,
-                n_true_checks=r.n_true_checks, n_restarts=r.n_restarts, action_hist=np.array([list(row) for row in r.action_hist]))
+                n_true_checks=r.n_true_checks, n_restarts=r.n_restarts,
+                action_hist=np.array([list(row) for row in r.action_hist]), near_edge_count=r.near_edge_count)
 
 
 class Context:
@@ -402,6 +406,15 @@ class Context:
         self._check(lib().mpcg_mlp_train(self.handle, policy.handle, _ptr(d), d.shape[0], int(steps), int(batch),
                                          float(lr), int(target_sync), int(seed), _ptr(losses), _stream(stream)))
         return losses
+
+    def mlp_adam(self, params, m, v, grad, t: int, lr: float = 1e-3, stream=None):
+        """mpcg_mlp_adam: one Adam step; params, m, v (float32 host arrays) updated in place."""
+        for a in (params, m, v):
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous):
+                raise TypeError("params, m and v must be C-contiguous float32 numpy arrays")
+        g = np.ascontiguousarray(grad, dtype=np.float32)
+        self._check(lib().mpcg_mlp_adam(self.handle, _ptr(params), _ptr(m), _ptr(v), _ptr(g), int(t), float(lr),
+                                        _stream(stream)))
 
     def spmv(self, A: "Matrix", fmt: int, x, y, reps: int = 1, stream=None) -> float:
         ms = C.c_double()

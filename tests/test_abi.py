@@ -39,9 +39,9 @@ def test_binding_covers_the_header():
 def test_struct_layouts():
     from paper_2504_14268_gb300 import mpcg
 
-    assert ctypes.sizeof(mpcg.CResult) == 288
+    assert ctypes.sizeof(mpcg.CResult) == 296
     assert mpcg.REC_DTYPE.itemsize == 80
-    assert ctypes.sizeof(mpcg.COptions) == 240
+    assert ctypes.sizeof(mpcg.COptions) == 248
     assert ctypes.sizeof(mpcg.Csr) == 40
 
 
@@ -57,6 +57,7 @@ def test_options_default_matches_paper(lib):
     assert (o.lr, o.gamma, o.eps0, o.eps_floor) == (0.1, 0.9, 1.0, 0.1)
     assert list(o.precs)[:5] == [0, 1, 2, 3, 4]
     assert list(o.cost)[:5] == [0.8, 0.6, 0.8, 1.0, 2.0]
+    assert o.edge_tol == 5e-3
     assert L.mpcg_mlp_nparams(64, 5) == 64 * 16 + 64 + 64 * 64 + 64 + 20 * 64 + 20
 
 

@@ -223,12 +223,13 @@ def test_greedy_qtable_matches_oracle(M):
     assert res["outcome"] == ref.outcome
 
 
-def _train_both(M, precs, cost, E=6, tmax=200, seed=5):
+def _train_both(M, precs, cost, E=6, tmax=200, seed=5, eps=None):
     A, b, xs = I.cfg_poisson32()
-    oo = _oopts(seed=seed, precs=precs, cost={p: c for p, c in zip(precs, cost)})
+    ek = {} if eps is None else dict(eps0=eps, eps_floor=eps)
+    oo = _oopts(seed=seed, precs=precs, cost={p: c for p, c in zip(precs, cost)}, **ek)
     qt = O.QTable.zeros(oo)
     it_o = O.train_sequential(oo, A, b, 1e-6, tmax, E, qt)
-    ctx = _ctx(M, seed=seed, precs=precs, cost=cost)
+    ctx = _ctx(M, seed=seed, precs=precs, cost=cost, **ek)
     mat = ctx.matrix(_dev(A))
     bd = torch.as_tensor(b).cuda()
     S = 100
@@ -248,13 +249,27 @@ def test_training_one_lane_matches_algorithm_1_fp32_fp64(M):
 
 
 def test_training_one_lane_matches_algorithm_1_full_set(M):
-    """Full precision set: episodes agree until the residual histories separate (an fp16 dot
-    rounded on either side of a tie is enough to split them, even in the first episode);
-    iteration counts stay close and the tables stay close."""
-    it_o, it_g, qt, Qg, vg = _train_both(M, (0, 1, 2, 3, 4), (0.8, 0.6, 0.8, 1.0, 2.0))
+    """Full precision set: episodes agree until the residual histories separate (a residual
+    within rounding of a bin edge, or an fp16 dot rounded on either side of a tie, is enough
+    to split them); iteration counts stay close. With a constant exploration rate a run of
+    E' episodes is the prefix of a longer run, so the tables are compared after every
+    prefix of episodes that both sides ran alike (same iteration counts and visits): there
+    they agree to the accuracy of the rewards (the 5e-3 relative residual tolerance moves
+    -log10 rho by about 2e-3 per update)."""
+    precs, cost = (0, 1, 2, 3, 4), (0.8, 0.6, 0.8, 1.0, 2.0)
+    it_o, it_g, qt, Qg, vg = _train_both(M, precs, cost)
     assert np.all(np.abs(np.asarray(it_o) - np.asarray(it_g)) <= np.maximum(3, np.asarray(it_o) // 10))
     # every iteration updates each operation's table once
     assert vg.sum() == 4 * int(np.sum(it_g)) and qt.visits.sum() == 4 * int(np.sum(it_o))
+    compared = 0
+    for E in range(1, 7):
+        it_o, it_g, qt, Qg, vg = _train_both(M, precs, cost, E=E, tmax=60, seed=8, eps=0.3)
+        if list(it_o) != list(it_g) or not np.array_equal(vg, qt.visits):
+            break
+        assert np.allclose(Qg, qt.Q, rtol=2e-2, atol=2e-2), (E, float(np.max(np.abs(Qg - qt.Q))))
+        compared = E
+    print(f"full-set training: tables compared after 1..{compared} episodes")
+    assert compared >= 1
 
 
 def test_training_one_lane_short_episodes_full_set(M):

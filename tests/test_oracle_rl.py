@@ -202,3 +202,64 @@ def test_operation_masks_restrict_greedy_and_exploration():
     cnt = np.array([np.sum(picks == a) for a in (1, 2, 4)])
     exp = len(picks) / 3
     assert np.sum((cnt - exp) ** 2 / exp) < 13.8  # chi-square, 2 dof, p ~ 0.001
+
+
+def test_bootstrap_max_runs_over_the_allowed_set():
+    """Section 4.1's update bootstraps on max over P; with a customised per-operation set
+    P_j (op_mask) the max runs over P_j. One update by hand: op j may choose only fp64
+    (index 4), Q_j(s', .) = (0, 0, 0, 0, -5) with the zeros never allowed, Q_j(s, fp64) = -2,
+    R = -1: target = -1 + 0.9 (-5) = -5.5 and Q_j(s, fp64) = -2 + 0.1 (-5.5 + 2) = -2.35
+    (an unrestricted max would bootstrap on 0 and give -1.9)."""
+    o = O.Options(op_mask=(0b10000,) * 4)
+    qt = O.QTable.zeros(o)
+    qt.Q[:, 7, 4] = -5.0
+    qt.Q[:, 3, 4] = -2.0
+    t = np.zeros(1, dtype=O.TRANS_DTYPE)
+    t[0]["s"], t[0]["s_next"], t[0]["reward"], t[0]["terminal"] = 3, 7, -1.0, 0
+    t[0]["act"] = [4, 4, 4, 4]
+    O.q_update(o, qt, t)
+    for j in range(4):
+        assert qt.Q[j, 3, 4] == pytest.approx(-2.35, abs=1e-15)
+        assert qt.Q[j, 7, 4] == -5.0 and not qt.Q[j, :, :4].any()
+    # a mix of allowed entries: op 0 may use fp32 and fp64 (indices 3, 4) with
+    # Q_0(s', .) = (9, 9, 9, -4, -6): target = -1 + 0.9 (-4) = -4.6, Q = -2 + 0.1 (-2.6)
+    o2 = O.Options(op_mask=(0b11000, 0, 0, 0))
+    q2 = O.QTable.zeros(o2)
+    q2.Q[0, 7] = [9.0, 9.0, 9.0, -4.0, -6.0]
+    q2.Q[0, 3, 4] = -2.0
+    t[0]["act"] = [4, 4, 4, 4]
+    O.q_update(o2, q2, t)
+    assert q2.Q[0, 3, 4] == pytest.approx(-2.26, abs=1e-15)
+    # operations without a mask keep the full set: op 1 bootstraps on max(0, ..., 0) = 0
+    assert q2.Q[1, 3, 4] == pytest.approx(-0.1, abs=1e-15)
+
+
+def test_masked_chain_reaches_the_restricted_bellman_fixed_point():
+    """Chain s0 -> s1 -> end with negative rewards (-1, -3), every operation restricted to
+    fp64: value iteration on the restricted MDP gives Q(s1, fp64) = -3 and Q(s0, fp64) =
+    -1 + 0.9 (-3) = -3.7. The never-allowed entries (still 0) must not lift Q(s0) to -1."""
+    o = O.Options(op_mask=(0b10000,) * 4)
+    qt = O.QTable.zeros(o)
+    chain = np.zeros(2, dtype=O.TRANS_DTYPE)
+    for t, (s, sn, r, term) in enumerate([(0, 1, -1.0, 0), (1, 1, -3.0, 1)]):
+        chain[t]["s"], chain[t]["s_next"], chain[t]["reward"], chain[t]["terminal"] = s, sn, r, term
+        chain[t]["act"] = [4, 4, 4, 4]
+    for _ in range(400):
+        O.q_update(o, qt, chain)
+    for j in range(4):
+        assert qt.Q[j, [0, 1], 4] == pytest.approx([-3.7, -3.0], rel=1e-9)
+
+
+def test_greedy_action_is_the_solvers_decision():
+    """orc_greedy_action (used to check GPU decisions on a replayed trajectory) gives the
+    action the oracle's own greedy solve takes at every iteration of that solve."""
+    A, b, _ = I.cfg_poisson32()
+    o = O.Options(seed=2, min_k=0, cost=dict(O.COST_C2))
+    qt = O.QTable.zeros(o)
+    O.train_sequential(o, A, b, 1e-6, 300, 15, qt)
+    out = O.solve(o, A, b, 1e-6, 300, qtable=qt)
+    rho = 1.0
+    for k, rec in enumerate(out.hist):
+        s, fm = O.greedy_action(o, qt, k, rho)
+        assert s == rec["state"] and fm == tuple(int(f) for f in rec["fmt"]), k
+        rho = rec["rho"]
