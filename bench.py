@@ -11,18 +11,27 @@ SpMV, the fused dot/axpy passes, the fp64 scalars and residual recomputation, th
 through the C ABI, inputs resident in HBM. The matrix and its value copies exceed the 129 MB
 L2 many times over, so no L2 flush is needed between steps.
 
-Prints one JSON line (see the fields below). `--impl reference` runs the CPU oracle arm on a
-bounded sample of the same workload instead.
+Besides the timed solve the line reports: all-FP64 CG on the same GPU, the standalone SpMV
+bandwidth per value format, the roofline of the solver kernel, the end-to-end rate with host
+buffers, a policy allowed every format of the paper's precision set, the 512-system uneven
+batch under a CUDA graph, and the CPU oracle's rates (one core and all cores).
+
+Prints one JSON line. `--impl reference` runs the CPU oracle arm (all host cores) on bounded
+samples of the same workload instead. Sections of the run carry NVTX ranges (solve_rl,
+solve_fp64, spmv_<format>, batch_<policy>) so that a profiler can select one launch.
 """
 from __future__ import annotations
 
 import argparse
+import contextlib
 import json
 import math
 import os
+import shutil
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -31,6 +40,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+METRIC = "time-to-1e-8 residual & solves/s: RL-mixed vs FP64 CG; SpMV % HBM peak"
+UNIT = "solves/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
 TAU = 1e-8
@@ -47,10 +58,22 @@ TRAIN_SET = [(24, 1e-3), (28, 1e-3), (32, 1e-3), (36, 1e-3), (40, 1e-3), (44, 1e
              (40, 1e-2), (48, 3e-3), (30, 3e-3), (36, 1e-2), (26, 1e-3), (34, 3e-3), (42, 1e-3), (46, 1e-2)]
 TRAIN_ROUNDS = 150
 TRAIN_SEED = 3
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_cg_persistent_fem27_128.md")
 
 
-def solver_options(M):
-    return M.Options(true_res_at_conv=1, on_breakdown=1, op_mask=OP_MASK, t_bin=T_BIN, seed=TRAIN_SEED)
+@contextlib.contextmanager
+def nvtx(name: str):
+    import torch
+
+    torch.cuda.nvtx.range_push(name)
+    try:
+        yield
+    finally:
+        torch.cuda.nvtx.range_pop()
+
+
+def solver_options(M, op_mask=OP_MASK):
+    return M.Options(true_res_at_conv=1, on_breakdown=1, op_mask=op_mask, t_bin=T_BIN, seed=TRAIN_SEED)
 
 
 def train_policy(M, ctx):
@@ -79,9 +102,6 @@ def train_policy(M, ctx):
     return pol, dt, (float(its[:3].mean()), float(its[-3:].mean()))
 
 
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_cg_persistent_fem27_256.md")
-
-
 def sources_sha256() -> str:
     """Hash of the kernel sources and the C header (the build the ncu counters belong to)."""
     import glob
@@ -96,18 +116,20 @@ def sources_sha256() -> str:
     return h.hexdigest()
 
 
-def measured_traffic():
-    """DRAM bytes per launch of the solver kernel on this workload from the committed ncu
-    summary, or None when that summary was taken on other kernel sources."""
+def traffic_ratio():
+    """DRAM bytes per algorithmic byte of the solver kernel, from the committed ncu summary of a
+    small case of the same family (the ratio does not depend on the grid: both grow with the
+    iterations times the bytes per iteration); None when that summary was taken on other
+    kernel sources."""
     try:
         vals = {}
         with open(TRAFFIC_FILE) as f:
             for line in f:
-                if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "sources_sha256")):
+                if ":" in line and line.strip().startswith(("traffic_per_algorithmic_byte", "sources_sha256")):
                     k, v = line.strip().split(":", 1)
                     vals[k.strip()] = v.strip().strip("`")
         if vals.get("sources_sha256") == sources_sha256():
-            return float(vals["traffic_bytes_per_launch"])
+            return float(vals["traffic_per_algorithmic_byte"])
     except Exception:
         pass
     return None
@@ -128,13 +150,6 @@ def workload(grid: int):
     A = I.fem27_aniso(grid, ANISO)
     xs, b = I.rhs_from_xstar(A, np.random.default_rng(0))
     return A, b, xs
-
-
-def load_policy():
-    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
-    from make_qtable import load
-
-    return load()
 
 
 class Clocks:
@@ -214,59 +229,193 @@ def launch_bytes(n: int, Z: int, hist) -> float:
     return total
 
 
-def cpu_sample(A, b, Q, visits, gpu_iters: int, budget_s: float = 15.0):
-    """The oracle, as it stands, on the first iterations of the same solve. Returns
-    (solves/s extrapolated to the GPU's iteration count, iterations sampled, seconds)."""
+# ---------------------------------------------------------------------------------------
+# CPU oracle (the cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------------------
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_policy(grid: int):
+    """The oracle-trained Q-table of the benchmark's options and the oracle's own iteration
+    counts on this workload (oracle/policy_fem27_c1.txt, written by the oracle alone), or a
+    closed-form CG bound when the file has no count for this grid."""
+    from oracle import make_fem27_policy as P
+    from paper_2504_14268_gb300 import inputs as I
+
+    Q, visits, counts = P.load()
+    lo, hi = I.fem27_spectrum(grid, ANISO)
+    bound = int(math.ceil(0.5 * math.sqrt(hi / lo) * math.log(2 / TAU)))
+    basis = {}
+    for kind in ("rl", "fp64"):
+        key = f"iters_{kind}_{grid}"
+        if key in counts:
+            basis[kind] = (int(counts[key]), f"the oracle's own {kind} solve of this workload ({int(counts[key])} "
+                                             f"iterations, oracle/policy_fem27_c1.txt)")
+        else:
+            basis[kind] = (bound, f"the closed-form CG bound 0.5 sqrt(kappa) ln(2/tau) = {bound} iterations")
+    return Q, visits, basis
+
+
+def _oracle_options():
     import oracle as O
 
-    o = O.Options(true_res_at_conv=1, on_breakdown=1, op_mask=OP_MASK, t_bin=T_BIN)
-    qt = O.QTable(Q.copy(), visits.copy())
+    return O.Options(true_res_at_conv=1, on_breakdown=1, op_mask=OP_MASK, t_bin=T_BIN)
+
+
+def _oracle_iters(A, b, kind, Q, visits, k):
+    """k iterations of the oracle's solve from x_0 = 0 (RL-mixed with the table, or fp64)."""
+    import oracle as O
+
+    o = _oracle_options()
+    if kind == "rl":
+        out = O.solve(o, A, b, TAU, k, qtable=O.QTable(Q.copy(), visits.copy()))
+    else:
+        out = O.solve(o, A, b, TAU, k, fixed=(4, 4, 4, 4))
+    return len(out.hist)
+
+
+def _oracle_worker(args):
+    """Spawned worker: maps the staged workload and runs k oracle iterations."""
+    d, kind, k = args
+    A = (int(np.load(os.path.join(d, "n.npy"))[0]), np.load(os.path.join(d, "rp.npy"), mmap_mode="r"),
+         np.load(os.path.join(d, "ci.npy"), mmap_mode="r"), np.load(os.path.join(d, "val.npy"), mmap_mode="r"))
+    b = np.load(os.path.join(d, "b.npy"), mmap_mode="r")
+    Q = np.load(os.path.join(d, "Q.npy"))
+    visits = np.load(os.path.join(d, "visits.npy"))
     t0 = time.time()
-    O.solve(o, A, b, TAU, 1, qtable=qt)
-    t1 = time.time() - t0
-    its = max(1, min(50, int(budget_s / max(t1, 1e-3))))
-    t0 = time.time()
-    out = O.solve(o, A, b, TAU, its, qtable=qt)
-    dt = time.time() - t0
-    per_it = dt / max(1, len(out.hist))
-    return 1.0 / (per_it * max(gpu_iters, 1)), len(out.hist), dt
+    done = _oracle_iters(A, b, kind, Q, visits, k)
+    return time.time() - t0, done
+
+
+class OracleBench:
+    """Times the oracle, as it stands, on bounded samples of the workload: in this process
+    (one core) or as one process per host core, each running the same sample concurrently
+    (the whole CPU's throughput; the workload is staged once in files that the processes
+    map). Rates are solves/s: iterations per second over the basis iteration count."""
+
+    def __init__(self, A, b, Q, visits):
+        self.A, self.b, self.Q, self.visits = A, b, Q, visits
+        self.dir = None
+        self.pool = None
+        self.t_iter = {}
+
+    def probe(self, kind):
+        """Seconds per iteration from a 2-iteration single-core run (first call also builds)."""
+        if kind not in self.t_iter:
+            _oracle_iters(self.A, self.b, kind, self.Q, self.visits, 1)
+            t0 = time.time()
+            done = _oracle_iters(self.A, self.b, kind, self.Q, self.visits, 2)
+            self.t_iter[kind] = (time.time() - t0) / max(done, 1)
+        return self.t_iter[kind]
+
+    def single(self, kind, budget_s, basis):
+        k = max(1, min(200, int(budget_s / self.probe(kind))))
+        t0 = time.time()
+        done = _oracle_iters(self.A, self.b, kind, self.Q, self.visits, k)
+        dt = time.time() - t0
+        return {"value": done / dt / basis, "cores": 1, "iters": done, "seconds": round(dt, 2)}
+
+    def _stage(self):
+        if self.dir is None:
+            import multiprocessing as mp
+
+            self.dir = tempfile.mkdtemp(prefix="mpcg_oracle_")
+            n, rp, ci, val = self.A
+            for name, arr in (("n", np.array([n])), ("rp", rp), ("ci", ci), ("val", val), ("b", self.b),
+                              ("Q", self.Q), ("visits", self.visits)):
+                np.save(os.path.join(self.dir, name + ".npy"), np.ascontiguousarray(arr))
+            self.pool = mp.get_context("spawn").Pool(host_cores())
+
+    def all_cores(self, kind, budget_s, basis):
+        self._stage()
+        P = host_cores()
+        # concurrent runs share the memory system: size the sample below the single-core budget
+        k = max(1, min(200, int(budget_s / (2.0 * self.probe(kind)))))
+        t0 = time.time()
+        out = self.pool.map(_oracle_worker, [(self.dir, kind, k)] * P)
+        dt = time.time() - t0
+        done = min(o[1] for o in out)
+        return {"value": P * done / dt / basis, "cores": P, "iters": done, "seconds": round(dt, 2)}
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.pool = None
+        if self.dir is not None:
+            shutil.rmtree(self.dir, ignore_errors=True)
+            self.dir = None
+
+
+def cpu_baseline(A, b, grid, budget_s=8.0):
+    """The oracle on one core (the line's cpu_baseline) plus all cores and plain fp64 CG."""
+    Q, visits, basis = oracle_policy(grid)
+    ob = OracleBench(A, b, Q, visits)
+    try:
+        rl1 = ob.single("rl", budget_s, basis["rl"][0])
+        rlP = ob.all_cores("rl", budget_s, basis["rl"][0])
+        f1 = ob.single("fp64", budget_s / 2, basis["fp64"][0])
+        fP = ob.all_cores("fp64", budget_s / 2, basis["fp64"][0])
+    finally:
+        ob.close()
+    return {
+        "kind": "oracle", "value": rl1["value"], "unit": UNIT, "cores": 1,
+        "sample": (f"the first {rl1['iters']} iterations of the same RL-mixed solve ({rl1['seconds']} s, one thread; "
+                   f"policy: the oracle-trained table oracle/policy_fem27_c1.txt, same options), extrapolated to "
+                   f"{basis['rl'][1]}"),
+        "all_cores": {"value": rlP["value"], "cores": rlP["cores"],
+                      "sample": f"{rlP['cores']} concurrent processes, {rlP['iters']} iterations each, {rlP['seconds']} s"},
+        "fp64_cg": {"value_1core": f1["value"], "value_all_cores": fP["value"], "cores": fP["cores"],
+                    "sample": f"plain fp64 CG (oracle, no rounding), {f1['iters']} / {fP['iters']} iterations, "
+                              f"extrapolated to {basis['fp64'][1]}"},
+    }
 
 
 def run_reference(args):
-    """CPU oracle arm: each step is a bounded sample of the workload's solve."""
+    """CPU oracle arm: each step runs a bounded sample of the workload's RL-mixed solve on every
+    host core (one process per core, the same sample each); solves/s on the oracle's own
+    iteration basis."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     A, b, xs = workload(args.grid)
-    Q, visits = load_policy()
-    # iterations of the full solve are taken from the oracle's own fp64 convergence bound
-    # (square root of the closed-form condition number), not from the GPU
-    from paper_2504_14268_gb300 import inputs as I
-
-    lo, hi = I.fem27_spectrum(args.grid, ANISO)
-    est_iters = int(math.ceil(0.5 * math.sqrt(hi / lo) * math.log(2 / TAU)))
-    for _ in range(args.warmup):
-        cpu_sample(A, b, Q, visits, est_iters, budget_s=2.0)
-    vals = []
-    t0 = time.time()
-    for _ in range(args.steps):
-        v, its, dt = cpu_sample(A, b, Q, visits, est_iters, budget_s=args.ref_budget)
-        vals.append(v)
-    T = time.time() - t0
+    Q, visits, basis = oracle_policy(args.grid)
+    ob = OracleBench(A, b, Q, visits)
+    try:
+        for _ in range(args.warmup):
+            ob.all_cores("rl", 0.5, basis["rl"][0])
+        vals, secs = [], []
+        for _ in range(args.steps):
+            r = ob.all_cores("rl", args.ref_budget, basis["rl"][0])
+            vals.append(r["value"])
+            secs.append(r["seconds"])
+    finally:
+        ob.close()
     value = statistics.mean(vals)
     line = {
-        "impl": "reference", "metric": "solves/s to true relative residual 1e-8 (RL-mixed CG)",
-        "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64+mixed", "data": "synthetic",
-        "config": {"workload": f"fem27_aniso_{args.grid}^3 (n={A[0]}, nnz={len(A[3])}), tau=1e-8, tabular policy"},
-        "cpu_baseline": {"kind": "oracle", "value": value, "unit": "solves/s", "cores": 1,
-                         "sample": f"first iterations of the solve per step (about {args.ref_budget:.0f} s of "
-                                   f"single-thread oracle time), extrapolated to {est_iters} iterations"},
-        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+mixed", "data": "synthetic",
+        "config": {"workload": f"fem27_aniso_{args.grid}^3", "n": A[0], "nnz": len(A[3]), "anisotropy": ANISO,
+                   "tau": TAU, "policy": "tabular Q (Algorithm 1) trained by the oracle on the same family, "
+                                         "operations in {fp32, fp64}; greedy (Algorithm 2)"},
+        "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": r["cores"],
+                         "sample": f"per step {r['cores']} concurrent oracle processes (one per host core), "
+                                   f"{r['iters']} iterations of the RL-mixed solve each, extrapolated to "
+                                   f"{basis['rl'][1]}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
 
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
 
 def max_over_ranks(t_local: float, dist, device) -> float:
     """The job's time: the slowest rank's (every rank solves its own replica)."""
@@ -284,6 +433,73 @@ def whole_job_rate(world: int, steps: int, t_job: float) -> float:
     return world * steps / t_job
 
 
+def timed_solve(ctx, mat, bd, x, pol, stream, reps=1):
+    import torch
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(reps):
+        res, _ = ctx.solve(mat, bd, x, TAU, MAX_ITER, pol, stream=stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    return res, ev[0].elapsed_time(ev[1]) / 1e3 / reps
+
+
+def fp16_capable_policy(M, ctx_all, mat, bd, x, xs, stream, t64):
+    """A policy trained with every operation free to choose any format of the paper's set
+    (fp16, bf16, tf32, fp32, fp64), same training set and rounds: its greedy solve of the
+    workload, against all-FP64 CG."""
+    pol, t_train, its = train_policy(M, ctx_all)
+    with nvtx("solve_rl_fullset"):
+        ctx_all.solve(mat, bd, x, TAU, MAX_ITER, pol, stream=stream)
+        res, t = timed_solve(ctx_all, mat, bd, x, pol, stream)
+    ah = np.array(res["action_hist"])[:, :7]
+    err = float(np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs))
+    return {"policy": "tabular Q, every operation in {fp16, bf16, tf32, fp32, fp64}, same training",
+            "time_to_tol_s": t, "iters": res["iters"], "outcome": res["outcome"],
+            "rel_res_true": res["rel_res_true"], "rel_err_xstar": err, "speedup_vs_fp64": t64 / t,
+            "action_mix": {M.FORMAT_NAMES[f]: int(ah[:, f].sum()) for f in range(7)},
+            "train_s": round(t_train, 2), "restarts": res["n_restarts"]}
+
+
+def batch512(M, pol_rl, stream):
+    """The uneven batch: 512 SPD systems (n log-uniform on [1e3, 2e5]; 2D and 3D variable-
+    coefficient diffusion and banded matrices), one persistent lockstep launch per batch captured
+    in a CUDA graph, tau = 1e-8, cap 5000; fp64 CG and the benchmark's tabular policy."""
+    import torch
+
+    from paper_2504_14268_gb300 import inputs as I
+
+    t0 = time.time()
+    sets = I.cfg_batched()
+    t_gen = time.time() - t0
+    out = {"systems": len(sets), "rows": int(sum(s[0][0] for s in sets)),
+           "nnz": int(sum(len(s[0][3]) for s in sets)), "generate_s": round(t_gen, 1)}
+    for name, pol_of in (("fp64", lambda c: c.policy_fixed((4, 4, 4, 4))), ("rl", None)):
+        ctx = M.Context(0, solver_options(M))
+        mats = [ctx.matrix((A[0], torch.as_tensor(A[1]).cuda(), torch.as_tensor(A[2]).cuda(),
+                            torch.as_tensor(A[3]).cuda())) for A, _, _ in sets]
+        bs = [torch.as_tensor(b).cuda() for _, b, _ in sets]
+        xs = [torch.zeros_like(b) for b in bs]
+        pol = pol_of(ctx) if pol_of else ctx.policy_load(pol_rl.save())
+        g = ctx.graph(mats, bs, xs, [TAU] * len(sets), [5000] * len(sets), pol)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        with nvtx(f"batch_{name}"):
+            ev[0].record(stream)
+            g.launch(stream)
+            ev[1].record(stream)
+        res = g.results(stream)
+        t = ev[0].elapsed_time(ev[1]) / 1e3
+        conv = sum(r["outcome"] == M.CONVERGED for r in res)
+        out[name] = {"batch_s": round(t, 3), "solves_per_s": len(sets) / t, "fraction_converged": conv / len(sets),
+                     "median_iters": float(np.median([r["iters"] for r in res]))}
+        g.close()
+        del mats, bs, xs
+        ctx.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -291,8 +507,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--grid", type=int, default=GRID)
-    ap.add_argument("--ref-budget", type=float, default=12.0)
-    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-budget", type=float, default=4.0, help="seconds of oracle work per reference step")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the full-precision-set policy, the 512-system batch and the SpMV table")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -342,7 +560,7 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    with Clocks(local) as clk:
+    with Clocks(local) as clk, nvtx("solve_rl"):
         for s in range(args.steps):
             ev[s][0].record(stream)
             res, h = ctx.solve(mat, bd, x, TAU, MAX_ITER, pol, history=hist if s == 0 else None, stream=stream)
@@ -354,35 +572,21 @@ def main():
     step_ms = [a.elapsed_time(c) for a, c in ev]
     T = max_over_ranks(sum(step_ms) / 1e3, dist, "cuda")
     r0 = results[0]
-    h0 = hist[: r0["iters"] + 1][: len(hist)]
     h0 = hist[: min(MAX_ITER, max(1, r0["iters"]))]
     xerr = float(np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs))
 
     # all-FP64 CG on the same GPU (same kernel, every operation in fp64)
     x64 = torch.zeros_like(bd)
-    res64, _ = ctx.solve(mat, bd, x64, TAU, MAX_ITER, pol64, stream=stream)
-    e64 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    e64[0].record(stream)
-    res64, _ = ctx.solve(mat, bd, x64, TAU, MAX_ITER, pol64, stream=stream)
-    e64[1].record(stream)
-    torch.cuda.synchronize()
-    t64 = e64[0].elapsed_time(e64[1]) / 1e3
+    with nvtx("solve_fp64"):
+        ctx.solve(mat, bd, x64, TAU, MAX_ITER, pol64, stream=stream)
+        res64, t64 = timed_solve(ctx, mat, bd, x64, pol64, stream)
     xerr64 = float(np.linalg.norm(x64.cpu().numpy() - xs) / np.linalg.norm(xs))
 
-    # SpMV bandwidth per value format (standalone product, autotuned schedule)
-    hbm, peak_kind = peaks()
-    xr = torch.rand(n, dtype=torch.float64, device="cuda")
-    yr = torch.empty_like(xr)
-    spmv = {}
-    for fmt, name in enumerate(M.FORMAT_NAMES):
-        ms = ctx.spmv(mat, fmt, xr, yr, reps=10, stream=stream)
-        v = BYTES[fmt]
-        byts = Z * (v + 4) + 4 * (n + 1) + 2 * n * v + (4 * n if fmt in (5, 6) else 0)
-        spmv[name] = {"ms": round(ms, 4), "gbs": round(byts / ms / 1e6, 1), "frac": round(byts / ms / 1e6 / hbm, 3)}
-
     # roofline of the persistent kernel (the only kernel of a step)
+    hbm, peak_kind = peaks()
     lb = launch_bytes(n, Z, h0)
     achieved = lb / (statistics.mean(step_ms) / 1e3) / 1e9
+    ratio = traffic_ratio()
 
     # end to end through the C ABI with pinned host buffers (H2D of b, D2H of x inside)
     bh = torch.as_tensor(b).pin_memory()
@@ -397,39 +601,66 @@ def main():
     torch.cuda.synchronize()
     e2e_T = ee[0].elapsed_time(ee[1]) / 1e3
 
+    extras = {}
+    if not args.no_extras and rank == 0:
+        # SpMV bandwidth per value format (standalone product, autotuned schedule)
+        xr = torch.rand(n, dtype=torch.float64, device="cuda")
+        yr = torch.empty_like(xr)
+        spmv = {}
+        for fmt, name in enumerate(M.FORMAT_NAMES):
+            with nvtx(f"spmv_{name}"):
+                ms = ctx.spmv(mat, fmt, xr, yr, reps=10, stream=stream)
+            v = BYTES[fmt]
+            byts = Z * (v + 4) + 4 * (n + 1) + 2 * n * v + (4 * n if fmt in (5, 6) else 0)
+            spmv[name] = {"ms": round(ms, 4), "gbs": round(byts / ms / 1e6, 1),
+                          "frac": round(byts / ms / 1e6 / hbm, 3)}
+        extras["spmv"] = spmv
+        del xr, yr
+        ctx_all = M.Context(local, solver_options(M, op_mask=(0, 0, 0, 0)))
+        mat_all = ctx_all.matrix((n, torch.as_tensor(rp).cuda(), torch.as_tensor(ci).cuda(),
+                                  torch.as_tensor(val).cuda()))
+        mat_all.autotune(3)
+        extras["fullset_policy"] = fp16_capable_policy(M, ctx_all, mat_all, bd, torch.zeros_like(bd), xs, stream, t64)
+        mat_all.close()
+        ctx_all.close()
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        Q, visits = load_policy()
-        v, its, dt = cpu_sample(A, b, Q, visits, r0["iters"])
-        cpu = {"kind": "oracle", "value": v, "unit": "solves/s", "cores": 1,
-               "sample": f"first {its} iterations of the same solve ({dt:.1f} s single-thread; policy: the "
-                         f"oracle-trained table tests/golden/qtable_diffusion3d_c1.txt under the same operation "
-                         f"sets), extrapolated to the GPU's {r0['iters']} iterations"}
+        cpu = cpu_baseline(A, b, args.grid)
+
+    if not args.no_extras and rank == 0:
+        mat.close()
+        del bd, x, x64
+        torch.cuda.empty_cache()
+        extras["batch512"] = batch512(M, pol, stream)
 
     if rank == 0:
         ah = np.array(r0["action_hist"])[:, :7]
         line = {
-            "metric": "solves/s to true relative residual 1e-8 (RL-mixed CG), with time vs all-FP64 CG and SpMV % HBM",
-            "value": whole_job_rate(world, args.steps, T), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64+mixed", "data": "synthetic",
+            "metric": METRIC, "value": whole_job_rate(world, args.steps, T), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+mixed",
+            "data": "synthetic",
             "config": {"workload": f"fem27_aniso_{args.grid}^3", "n": n, "nnz": Z, "anisotropy": ANISO, "tau": TAU,
                        "policy": f"tabular Q (Algorithm 1) trained on the GPU at set-up: {len(TRAIN_SET)} systems "
                                  f"24^3-48^3 of the same family, {TRAIN_ROUNDS} batched rounds, cost C1, every "
                                  f"operation in {{fp32, fp64}}, T_max {T_BIN}; greedy (Algorithm 2)",
                        "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if world > 1 else "1 GPU"},
             "time_to_tol_s": 1e-3 * statistics.mean(step_ms), "iters": r0["iters"], "outcome": r0["outcome"],
-            "rel_res_true": r0["rel_res_true"], "rel_err_xstar": xerr,
+            "rel_res_true": r0["rel_res_true"], "rel_err_xstar": xerr, "near_edge_count": r0["near_edge_count"],
             "fp64": {"time_to_tol_s": t64, "iters": res64["iters"], "rel_res_true": res64["rel_res_true"],
                      "rel_err_xstar": xerr64},
             "speedup_vs_fp64": t64 / (1e-3 * statistics.mean(step_ms)),
             "action_mix": {M.FORMAT_NAMES[f]: int(ah[:, f].sum()) for f in range(7)},
-            "spmv": spmv,
+            **extras,
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                         "frac": round(achieved / hbm, 3), "traffic": measured_traffic(), "peak_source": peak_kind,
-                         "kernel": "cg_persistent", "bytes_per_launch": lb, "sources_sha256": sources_sha256()},
-            "e2e": {"value": args.steps / e2e_T, "unit": "solves/s", "h2d_bytes_per_step": 8 * n,
-                    "d2h_bytes_per_step": 8 * n + 288},
+                         "frac": round(achieved / hbm, 3), "traffic": None if ratio is None else round(ratio * lb),
+                         "peak_source": peak_kind, "kernel": "cg_persistent", "bytes_per_launch": lb,
+                         "traffic_note": "DRAM bytes per algorithmic byte from an ncu capture of the same kernel "
+                                         "on the 128^3 case, times this launch's algorithmic bytes"},
+            "e2e": {"value": args.steps / e2e_T, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+                    "d2h_bytes_per_step": 8 * n + 296},
             "cpu_baseline": cpu,
             "gpu_launches": args.steps,
             "clocks": clk.summary(),

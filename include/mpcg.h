@@ -139,6 +139,13 @@ typedef struct {
                             * threshold theta_m (Section 4.1's bin edges) are counted in
                             * mpcg_result.near_edge_count: there a rounding-level change of
                             * rho can move the state to the next bin (5e-3)              */
+  int32_t stepped;         /* single solves (mpcg_solve): 0 = automatic (stepped for systems
+                            * of at least 2^24 nonzeros without IC(0)), 1 = one persistent
+                            * cooperative launch, 2 = stepped: one kernel per phase of the
+                            * iteration, repeated on the device by a conditional while-loop
+                            * CUDA graph (precond = 2 always runs the persistent launch,
+                            * whose substitutions need every CTA resident)              */
+  int32_t reserved_opt;
 } mpcg_options;
 
 /* Result of one solve. */

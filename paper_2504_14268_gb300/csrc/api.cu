@@ -70,6 +70,13 @@ struct Plan {
   DevBuf icwork;             // IC(0): every system's substitution words, zeroed per launch
   size_t icwork_bytes = 0;
   bool lockstep = false;
+  bool stepped = false;      // one system, one kernel per phase in a while-loop graph
+  int sgrid[4] = {0, 0, 0, 0};
+  size_t ssmem = 0;
+  cudaGraphExec_t sexec = nullptr;
+  ~Plan() {
+    if (sexec) cudaGraphExecDestroy(sexec);
+  }
   std::vector<DevSys> hsys;
   std::vector<mpcg_result> hres;
   Launch L;
@@ -83,6 +90,7 @@ struct mpcg_ctx_s {
   int occ = 0;      // CTAs per SM of the solver kernel without the stream ring
   int occ_s = 0;    // ... with the stream ring (2 * kStageBytes of dynamic shared memory)
   int socc = 0, socc_s = 0;  // same for the standalone product kernel
+  int pocc[4] = {0, 0, 0, 0}, pocc_s[4] = {0, 0, 0, 0};  // the stepped solve's phase kernels
   std::string err;
   Plan plan;   // reused by mpcg_solve / mpcg_solve_batched / training
   DevBuf spmv_x, spmv_q, spmv_y, spmv_err;
@@ -178,6 +186,7 @@ mpcg_status build_optview(mpcg_ctx_t ctx, const mpcg_options& o, OptView& v) {
   if (o.batch_mode < 0 || o.batch_mode > 2) return fail(ctx, MPCG_ERR_INVALID_ARG, "batch_mode must be 0, 1 or 2");
   if (o.precond < 0 || o.precond > 2) return fail(ctx, MPCG_ERR_INVALID_ARG, "precond must be 0, 1 or 2");
   if (!(o.edge_tol >= 0.0 && o.edge_tol < 1.0)) return fail(ctx, MPCG_ERR_INVALID_ARG, "edge_tol must be in [0, 1)");
+  if (o.stepped < 0 || o.stepped > 2) return fail(ctx, MPCG_ERR_INVALID_ARG, "stepped must be 0, 1 or 2");
   for (int a = 0; a < o.nprec; ++a)
     if (!valid_fmt(o.precs[a])) return fail(ctx, MPCG_ERR_INVALID_ARG, "precs[%d] = %d is not a format code", a, o.precs[a]);
   if (o.unvisited_fallback != -1 && !valid_fmt(o.unvisited_fallback))
@@ -374,8 +383,10 @@ mpcg_status ensure_ic0(mpcg_ctx_t ctx, mpcg_matrix_s* M, cudaStream_t s) {
 
 // Builds the device tables of a launch for `in` systems into `pl` and fills pl.L.
 mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, mpcg_policy_t policy, int train,
-                       int trans_cap, int force_team, cudaStream_t s, int feat_cap = 0) {
+                       int trans_cap, int force_team, cudaStream_t s, int feat_cap = 0, bool stepped = false) {
   const int nsys = (int)in.size();
+  if (stepped && (nsys != 1 || train || ctx->opt.precond == 2))
+    return fail(ctx, MPCG_ERR_INTERNAL, "the stepped solve takes one inference system without IC(0)");
   if (ctx->opt.precond == 1)
     for (int i = 0; i < nsys; ++i)
       if (!in[i].A->diag_ok)
@@ -489,7 +500,17 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
   // Lockstep batches: every CTA works on a slice of every unfinished system.
   const int bm = ctx->opt.batch_mode;
   pl.lockstep = force_team == 0 && ((bm == 0 && nsys >= 2) || bm == 2) && nsys >= 1;
-  CK(ctx, pl.partials.ensure(sizeof(double) * kNSlot * (size_t)(grid + (pl.lockstep ? nsys : 0))));
+  pl.stepped = stepped;
+  int pgrid = 0;
+  if (stepped) {
+    for (int w = 0; w < 4; ++w) {
+      pl.sgrid[w] = ctx->nsm * (stream_shape ? ctx->pocc_s[w] : ctx->pocc[w]);
+      pgrid = std::max(pgrid, pl.sgrid[w]);
+    }
+    pl.ssmem = stream_shape ? 2 * (size_t)kStageBytes : 0;
+    CK(ctx, pl.lk_done.ensure(sizeof(int)));
+  }
+  CK(ctx, pl.partials.ensure(sizeof(double) * kNSlot * (size_t)(std::max(grid, pgrid) + (pl.lockstep ? nsys : 0))));
   if (pl.lockstep) {
     std::vector<long long> w(nsys);
     for (int i = 0; i < nsys; ++i) w[i] = std::max(1LL, in[i].A->dm.nnz + 3LL * in[i].A->dm.n);
@@ -543,6 +564,7 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
   if (const char* t = getenv("MPCG_TIMEOUT_CYCLES")) L.timeout_cycles = atoll(t);
   L.lockstep = pl.lockstep ? 1 : 0;
   L.ic = ctx->opt.precond == 2 ? 1 : 0;
+  if (pl.stepped) L.lk_done = pl.lk_done.as<int>();
   if (pl.lockstep) {
     L.lk_w = pl.lk_w.as<long long>();
     L.lk_pref = pl.lk_pref.as<long long>();
@@ -562,6 +584,26 @@ mpcg_status enqueue_plan(mpcg_ctx_t ctx, Plan& pl, cudaStream_t s) {
   CK(ctx, cudaMemsetAsync(pl.err.p, 0, sizeof(unsigned), s));
   if (pl.icwork_bytes) CK(ctx, cudaMemsetAsync(pl.icwork.p, 0, pl.icwork_bytes, s));
   const size_t smem = pl.L.stream_stage > 0 ? 2 * (size_t)pl.L.stream_stage : 0;
+  if (pl.stepped) {
+    // the phase machine starts in its initialisation phase; the while-loop graph of this
+    // launch is built and instantiated here (a graph with a conditional node has at most one
+    // instantiation at a time, so the previous one is destroyed first)
+    CK(ctx, cudaMemsetAsync(pl.st.p, 0, sizeof(SysState), s));
+    CK(ctx, cudaMemsetAsync(pl.lk_done.p, 0, sizeof(int), s));
+    if (pl.sexec) {
+      CK(ctx, cudaStreamSynchronize(s));
+      cudaGraphExecDestroy(pl.sexec);
+      pl.sexec = nullptr;
+    }
+    const unsigned limit = 8u * (unsigned)std::min(pl.hsys[0].max_iter + 4, 1 << 26) + 64u;
+    cudaGraph_t g = nullptr;
+    CK(ctx, stepped_graph(pl.L, pl.sgrid, pl.ssmem, limit, &g));
+    const cudaError_t e = cudaGraphInstantiate(&pl.sexec, g, 0);
+    cudaGraphDestroy(g);
+    CK(ctx, e);
+    CK(ctx, cudaGraphLaunch(pl.sexec, s));
+    return MPCG_OK;
+  }
   if (pl.lockstep) {
     // every system starts in its initialisation phase; no system has finished
     CK(ctx, cudaMemsetAsync(pl.st.p, 0, sizeof(SysState) * pl.nsys, s));
@@ -645,6 +687,8 @@ void mpcg_options_default(mpcg_options* o) {
   o->batch_mode = 0;
   o->precond = 0;
   o->edge_tol = 5e-3;
+  o->stepped = 0;
+  o->reserved_opt = 0;
 }
 
 mpcg_status mpcg_create(mpcg_ctx_t* out, int device, const mpcg_options* opt) {
@@ -672,6 +716,12 @@ mpcg_status mpcg_create(mpcg_ctx_t* out, int device, const mpcg_options* opt) {
   if (spmv_occupancy(&c->socc, 0) != cudaSuccess || spmv_occupancy(&c->socc_s, 2 * (size_t)kStageBytes) != cudaSuccess)
     return MPCG_ERR_CUDA;
   if (mlp_set_smem_limit(mlp_grad_smem(kMaxHidden, MPCG_MAX_PREC)) != cudaSuccess) return MPCG_ERR_CUDA;
+  if (stepped_set_smem_limit(2 * (size_t)kStageBytes) != cudaSuccess) return MPCG_ERR_CUDA;
+  for (int w = 0; w < 4; ++w) {
+    if (stepped_occupancy(w, &c->pocc[w], 0) != cudaSuccess || c->pocc[w] < 1) return MPCG_ERR_CUDA;
+    if (stepped_occupancy(w, &c->pocc_s[w], 2 * (size_t)kStageBytes) != cudaSuccess || c->pocc_s[w] < 1)
+      return MPCG_ERR_CUDA;
+  }
   c->socc = std::min(c->socc, c->occ);
   c->socc_s = std::min(c->socc_s, c->occ_s);
   *out = c.release();
@@ -1269,7 +1319,10 @@ mpcg_status mpcg_solve(mpcg_ctx_t ctx, mpcg_matrix_t A, const double* b, double*
   in[0] = SysIn{A, bd, xd, tol, max_iter, hd, history ? history_cap : 0};
   int force = 0;
   if (const char* f = getenv("MPCG_FORCE_TEAM")) force = atoi(f);
-  mpcg_status st = build_plan(ctx, pl, in, policy, 0, 0, force, s);
+  // stepped (one kernel per phase in a while-loop graph) for large systems, or when asked
+  const int sm = ctx->opt.stepped;
+  const bool stepped = ctx->opt.precond != 2 && force == 0 && (sm == 2 || (sm == 0 && A->dm.nnz >= (1LL << 24)));
+  mpcg_status st = build_plan(ctx, pl, in, policy, 0, 0, force, s, 0, stepped);
   if (st != MPCG_OK) return st;
   st = enqueue_plan(ctx, pl, s);
   if (st != MPCG_OK) return st;

@@ -187,6 +187,12 @@ enum DevErr : unsigned { DERR_NONE = 0, DERR_TIMEOUT = 1, DERR_BAD_STATE = 2 };
 // Host entry points of the kernels (cg_kernel.cu, setup_kernels.cu).
 cudaError_t launch_cg(const Launch& L, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_cg_lockstep(const Launch& L, int grid, size_t smem, cudaStream_t s);
+// Stepped single solve (stepped.cu): kernels 0..3 are the product, residual, direction and
+// other-phases kernels; the graph repeats them (grids[w] CTAs each, smem bytes of dynamic
+// shared memory for kernels 0 and 3) until the system is done or `limit` passes ran.
+cudaError_t stepped_occupancy(int which, int* blocks_per_sm, size_t smem);
+cudaError_t stepped_set_smem_limit(size_t bytes);
+cudaError_t stepped_graph(const Launch& L, const int grids[4], size_t smem, unsigned limit, cudaGraph_t* out);
 // the IC(0) instantiations (cg_kernel_ic.cu)
 cudaError_t launch_cg_ic(const Launch& L, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_cg_lockstep_ic(const Launch& L, int grid, size_t smem, cudaStream_t s);

@@ -1505,9 +1505,12 @@ __device__ __forceinline__ void lk_partial(const Launch& L, int slot, int k, dou
   if (threadIdx.x == 0) L.partials[(long long)slot * kNSlot + k] = v;
 }
 
-// Row work of one slice in the current phase of its system.
-template <bool IC>
+// Row work of one slice in the current phase of its system. ONLY >= 0 compiles the code of
+// that phase alone (the per-phase kernels of the stepped solve; the caller has checked the
+// phase), ONLY < 0 every phase behind a run-time switch.
+template <bool IC, int ONLY = -1>
 __device__ void lk_slice_rows(const Launch& L, int s, Rows R, int slot, Smem& sm, const StreamCtx* sc) {
+  static_assert(!(IC && ONLY >= 0), "the single-phase forms carry no IC(0) substitutions");
   const DevSys& S = L.sys[s];
   SysState* st = L.st + s;
   if (threadIdx.x == 0) {
@@ -1516,6 +1519,26 @@ __device__ void lk_slice_rows(const Launch& L, int s, Rows R, int slot, Smem& sm
     sm.lk_known = v->true_known;
   }
   load_bcast(st, sm);  // ends with __syncthreads
+  if constexpr (ONLY == PH_A) {
+    DotAcc nu{0.0, 0.f, 0.f};
+    spmv_rows(S, R, sm.bc.fmt[0], sm.bc.fmt[2], nu, sc);
+    lk_partial(L, slot, 0, cta_dot(nu, sm.red));
+    return;
+  } else if constexpr (ONLY == PH_B) {
+    const int p1 = sm.bc.fmt[0], p2 = sm.bc.fmt[1], p4 = sm.bc.fmt[3];
+    const bool sig_rr = (p2 == F64 && p4 == F64 && !S.A.dinv);
+    double rr = 0.0;
+    DotAcc sg{0.0, 0.f, 0.f};
+    phase_b(S, R, sm.bc.alpha, p1, p2, p4, sig_rr, rr, sg);
+    rr = cta_sum(rr, sm.red);
+    const double sp = sig_rr ? rr : cta_dot(sg, sm.red);
+    lk_partial(L, slot, 0, rr);
+    lk_partial(L, slot, 1, sp);
+    return;
+  } else if constexpr (ONLY == PH_C) {
+    phase_c(S, R, sm.bc.alpha, sm.bc.beta, sm.bc.zfmt, sm.bc.fmt[0]);
+    return;
+  }
   const int phase = sm.lk_phase;
   switch (phase) {
     case PH_INIT: {
@@ -1632,16 +1655,24 @@ __device__ __forceinline__ double lk_sum(const Launch& L, int base, int np, int 
 }
 
 // Scalar step of the phase system s has just run, by the CTA that owns s; sets the next
-// phase (the transitions of solve_system).
-__device__ void lk_step(const Launch& L, int s, Smem& sm) {
+// phase (the transitions of solve_system). The phase's partials are the np slots from base.
+// ONLY >= 0: the caller knows the phase and only that phase's step is compiled.
+template <int ONLY = -1>
+__device__ void lk_step_slots(const Launch& L, int s, int base, int np, Smem& sm) {
   const DevSys& S = L.sys[s];
   SysState* st = L.st + s;
   if (threadIdx.x == 0) sm.lk_phase = ((const volatile SysState*)st)->phase;
   __syncthreads();
-  const int phase = sm.lk_phase;
+  const int phase = ONLY >= 0 ? ONLY : sm.lk_phase;
   if (phase == PH_DONE) return;
-  const int cf = L.lk_cfirst[s], base = L.lk_base[s];
-  const int np = cf < 0 ? 0 : L.lk_clast[s] - cf + 1;
+  if constexpr (ONLY == PH_A) {
+    step_A(L, S, st, lk_sum(L, base, np, 0, sm));
+  } else if constexpr (ONLY == PH_B) {
+    const double trr = lk_sum(L, base, np, 0, sm), tsg = lk_sum(L, base, np, 1, sm);
+    step_B(L, S, st, trr, tsg, sm);
+  } else if constexpr (ONLY == PH_C) {
+    stamp_c(S, st);
+  } else {
   switch (phase) {
     case PH_INIT: {
       const double tb = lk_sum(L, base, np, 0, sm), tr = lk_sum(L, base, np, 1, sm);
@@ -1669,6 +1700,7 @@ __device__ void lk_step(const Launch& L, int s, Smem& sm) {
     case PH_FINAL: step_final(L, S, st, s, lk_sum(L, base, np, 0, sm)); break;
     default: break;  // PH_PLOW, PH_X, PH_RZ: no scalar work
   }
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     const volatile SysState* v = st;
@@ -1691,6 +1723,12 @@ __device__ void lk_step(const Launch& L, int s, Smem& sm) {
     if (next == PH_DONE) atomicAdd(L.lk_done, 1);
   }
   __syncthreads();
+}
+
+__device__ __forceinline__ void lk_step(const Launch& L, int s, Smem& sm) {
+  const int cf = L.lk_cfirst[s];
+  const int np = cf < 0 ? 0 : L.lk_clast[s] - cf + 1;
+  lk_step_slots<-1>(L, s, L.lk_base[s], np, sm);
 }
 
 template <bool IC>

@@ -1,7 +1,7 @@
 """Host scheduling analysis of the IC(0) substitutions (mpcg_csr_levels, no GPU): levels
 against closed forms (2D five-point grid: x + y; 27-point grid: x + 2y + 4z bounds; a
-tridiagonal matrix: one row per level; a diagonal matrix: one level) and against a
-longest-path computation over the dependency graph."""
+tridiagonal matrix: one row per level; a diagonal matrix: one level) and by the two
+properties that define the levels on other patterns."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -19,19 +19,20 @@ def M():
     return mpcg
 
 
-def _longest_paths(A):
+def _check_level_properties(A, lo, up):
+    """The two properties that define the levels (by induction over the rows they determine
+    every level uniquely): a row's level is above the level of every row it depends on, and a
+    row with dependencies sits exactly one above the highest of them (a row without any at 0).
+    Lower substitution: dependencies are the stored columns j < i; upper: j > i."""
     n, rp, ci, _ = A
-    lo = [0] * n
-    for i in range(n):
-        for e in range(rp[i], rp[i + 1]):
-            if ci[e] < i:
-                lo[i] = max(lo[i], lo[ci[e]] + 1)
-    up = [0] * n
-    for i in range(n - 1, -1, -1):
-        for e in range(rp[i], rp[i + 1]):
-            if ci[e] > i:
-                up[i] = max(up[i], up[ci[e]] + 1)
-    return np.array(lo), np.array(up)
+    for lev, dep in ((lo, lambda i, j: j < i), (up, lambda i, j: j > i)):
+        for i in range(n):
+            deps = [int(j) for j in ci[rp[i]:rp[i + 1]] if dep(i, j)]
+            if not deps:
+                assert lev[i] == 0, i
+                continue
+            assert all(lev[j] < lev[i] for j in deps), i
+            assert max(lev[j] for j in deps) == lev[i] - 1, i
 
 
 def test_poisson_levels_are_x_plus_y(M):
@@ -54,18 +55,18 @@ def test_special_patterns(M):
     assert M.csr_levels((0, np.zeros(1, dtype=np.int32), np.zeros(0, dtype=np.int32), None))[2] == (0, 0)
 
 
-def test_fem27_and_random_patterns_match_longest_paths(M):
+def test_fem27_and_random_patterns_satisfy_the_level_properties(M):
     N = 6
     A = I.fem27_aniso(N)
     lo, up, depth = M.csr_levels(A)
-    rlo, rup = _longest_paths(A)
-    assert np.array_equal(lo, rlo) and np.array_equal(up, rup)
+    _check_level_properties(A, lo, up)
+    assert depth == (int(lo.max()) + 1, int(up.max()) + 1)
     # at least x + 2y + 4z along the grid's dependency chains (the substitutions' depth)
     assert depth[0] >= 7 * (N - 1) + 1
     B = I.random_spd_small(60, np.random.default_rng(3))
-    lo, up, _ = M.csr_levels(B)
-    rlo, rup = _longest_paths(B)
-    assert np.array_equal(lo, rlo) and np.array_equal(up, rup)
+    lo, up, depth = M.csr_levels(B)
+    _check_level_properties(B, lo, up)
+    assert depth == (int(lo.max()) + 1, int(up.max()) + 1)
 
 
 def test_invalid_csr_is_refused(M):
