@@ -48,7 +48,7 @@ TAU = 1e-8
 GRID = 256
 ANISO = 1e-3
 MAX_ITER = 20000
-BYTES = {0: 2, 1: 2, 2: 4, 3: 4, 4: 8, 5: 2, 6: 2}
+BYTES = {0: 2, 1: 2, 2: 4, 3: 4, 4: 8, 5: 2, 6: 2, 7: 1}
 # policy training: formats with u <= sqrt(tau) for every operation (fp32, fp64), iteration
 # bins over the training horizon T_max = 5000 (so the state is in effect the residual bin),
 # 16 systems of the workload's family, 150 rounds of batched episodes
@@ -203,15 +203,19 @@ class Clocks:
 
 
 def iter_bytes(n: int, Z: int, fmt: tuple, flags: int, next_p1: int) -> float:
-    """Algorithmic HBM bytes of one iteration of the persistent kernel (each array touched
-    once): phase A reads the p1 value copy and the columns (Z (v + 4)), row_ptr (4n), p once
-    in its p1 copy (n v) and in fp64 for nu (8n, shared with the gather when p1 = fp64), and
-    writes q (n v); phase B reads q (plus the fp32 row scale for row-scaled formats) and r,
+    """Algorithmic HBM bytes of one iteration of the solver (each array touched once): phase A
+    reads the p1 value copy and the columns (Z (v + 4)), row_ptr (4n), p once in its p1 copy
+    (n v) and in fp64 for nu (8n; none when p1 = fp64 or when nu's format is p1's, whose
+    rounding of p is the low copy itself), and writes q (n v); phase B reads q (plus the fp32 row scale for row-scaled formats) and r,
     writes r; phase C reads p, x, r and writes x, p and p's copy in the next format; a
     residual recomputation reads the fp64 values, columns, row_ptr, x, b and writes r."""
-    p1 = fmt[0]
+    p1, p3 = fmt[0], fmt[2]
     v = BYTES[p1]
-    a = Z * (v + 4) + 4 * (n + 1) + n * v + (0 if p1 == 4 else 8 * n) + n * v
+    base = {5: 1, 6: 0}
+    # nu reads p in fp64 unless the product is fp64 (the gather reads it) or nu's format is the
+    # product's (then fl_p3(p) is p's low copy, which the gather reads)
+    nu_from_low = p3 != 4 and base.get(p3, p3) == base.get(p1, p1) and p1 not in (5, 6)
+    a = Z * (v + 4) + 4 * (n + 1) + n * v + (0 if p1 == 4 or nu_from_low else 8 * n) + n * v
     bb = n * v + (4 * n if p1 in (5, 6) else 0) + 16 * n
     c = 48 * n + (0 if next_p1 == 4 else BYTES[next_p1] * n)
     t = (Z * 12 + 4 * (n + 1) + 24 * n) if flags & 4 else 0
@@ -276,27 +280,37 @@ def _oracle_iters(A, b, kind, Q, visits, k):
         out = O.solve(o, A, b, TAU, k, qtable=O.QTable(Q.copy(), visits.copy()))
     else:
         out = O.solve(o, A, b, TAU, k, fixed=(4, 4, 4, 4))
-    return len(out.hist)
+    return len(out.hist) if k > 0 else 0
+
+
+def _timed_iters(A, b, kind, Q, visits, k):
+    """(seconds of a solve with no iteration -- the initial and closing fp64 residuals --,
+    seconds of a solve with k iterations, iterations done)."""
+    t0 = time.time()
+    _oracle_iters(A, b, kind, Q, visits, 0)
+    t1 = time.time()
+    done = _oracle_iters(A, b, kind, Q, visits, k)
+    return t1 - t0, time.time() - t1, done
 
 
 def _oracle_worker(args):
-    """Spawned worker: maps the staged workload and runs k oracle iterations."""
+    """Spawned worker: maps the staged workload and times k oracle iterations."""
     d, kind, k = args
     A = (int(np.load(os.path.join(d, "n.npy"))[0]), np.load(os.path.join(d, "rp.npy"), mmap_mode="r"),
          np.load(os.path.join(d, "ci.npy"), mmap_mode="r"), np.load(os.path.join(d, "val.npy"), mmap_mode="r"))
     b = np.load(os.path.join(d, "b.npy"), mmap_mode="r")
     Q = np.load(os.path.join(d, "Q.npy"))
     visits = np.load(os.path.join(d, "visits.npy"))
-    t0 = time.time()
-    done = _oracle_iters(A, b, kind, Q, visits, k)
-    return time.time() - t0, done
+    return _timed_iters(A, b, kind, Q, visits, k)
 
 
 class OracleBench:
     """Times the oracle, as it stands, on bounded samples of the workload: in this process
     (one core) or as one process per host core, each running the same sample concurrently
     (the whole CPU's throughput; the workload is staged once in files that the processes
-    map). Rates are solves/s: iterations per second over the basis iteration count."""
+    map). A sample's iteration time is the time of k iterations minus that of a solve with
+    none (the initial and closing fp64 residuals, which a solve pays once). Rates are
+    solves/s: iterations per second over the basis iteration count."""
 
     def __init__(self, A, b, Q, visits):
         self.A, self.b, self.Q, self.visits = A, b, Q, visits
@@ -305,20 +319,18 @@ class OracleBench:
         self.t_iter = {}
 
     def probe(self, kind):
-        """Seconds per iteration from a 2-iteration single-core run (first call also builds)."""
+        """Seconds per iteration from a one-iteration single-core run (first call also builds)."""
         if kind not in self.t_iter:
-            _oracle_iters(self.A, self.b, kind, self.Q, self.visits, 1)
-            t0 = time.time()
-            done = _oracle_iters(self.A, self.b, kind, self.Q, self.visits, 2)
-            self.t_iter[kind] = (time.time() - t0) / max(done, 1)
+            t0, t1, done = _timed_iters(self.A, self.b, kind, self.Q, self.visits, 1)
+            self.t_iter[kind] = max(t1 - t0, 1e-3) / max(done, 1)
         return self.t_iter[kind]
 
     def single(self, kind, budget_s, basis):
         k = max(1, min(200, int(budget_s / self.probe(kind))))
-        t0 = time.time()
-        done = _oracle_iters(self.A, self.b, kind, self.Q, self.visits, k)
-        dt = time.time() - t0
-        return {"value": done / dt / basis, "cores": 1, "iters": done, "seconds": round(dt, 2)}
+        t0, tk, done = _timed_iters(self.A, self.b, kind, self.Q, self.visits, k)
+        per_it = max(tk - t0, 1e-6) / max(done, 1)
+        return {"value": 1.0 / (per_it * basis), "cores": 1, "iters": done, "seconds": round(tk, 2),
+                "fixed_s": round(t0, 2)}
 
     def _stage(self):
         if self.dir is None:
@@ -339,8 +351,9 @@ class OracleBench:
         t0 = time.time()
         out = self.pool.map(_oracle_worker, [(self.dir, kind, k)] * P)
         dt = time.time() - t0
-        done = min(o[1] for o in out)
-        return {"value": P * done / dt / basis, "cores": P, "iters": done, "seconds": round(dt, 2)}
+        per_it = max(max(o[1] - o[0], 1e-6) / max(o[2], 1) for o in out)  # the slowest process
+        done = min(o[2] for o in out)
+        return {"value": P / (per_it * basis), "cores": P, "iters": done, "seconds": round(dt, 2)}
 
     def close(self):
         if self.pool is not None:
@@ -365,9 +378,9 @@ def cpu_baseline(A, b, grid, budget_s=8.0):
         ob.close()
     return {
         "kind": "oracle", "value": rl1["value"], "unit": UNIT, "cores": 1,
-        "sample": (f"the first {rl1['iters']} iterations of the same RL-mixed solve ({rl1['seconds']} s, one thread; "
-                   f"policy: the oracle-trained table oracle/policy_fem27_c1.txt, same options), extrapolated to "
-                   f"{basis['rl'][1]}"),
+        "sample": (f"the first {rl1['iters']} iterations of the same RL-mixed solve ({rl1['seconds']} s, one thread, "
+                   f"less {rl1['fixed_s']} s of a solve with no iteration; policy: the oracle-trained table "
+                   f"oracle/policy_fem27_c1.txt, same options), extrapolated to {basis['rl'][1]}"),
         "all_cores": {"value": rlP["value"], "cores": rlP["cores"],
                       "sample": f"{rlP['cores']} concurrent processes, {rlP['iters']} iterations each, {rlP['seconds']} s"},
         "fp64_cg": {"value_1core": f1["value"], "value_all_cores": fP["value"], "cores": fP["cores"],
@@ -453,12 +466,12 @@ def fp16_capable_policy(M, ctx_all, mat, bd, x, xs, stream, t64):
     with nvtx("solve_rl_fullset"):
         ctx_all.solve(mat, bd, x, TAU, MAX_ITER, pol, stream=stream)
         res, t = timed_solve(ctx_all, mat, bd, x, pol, stream)
-    ah = np.array(res["action_hist"])[:, :7]
+    ah = np.array(res["action_hist"])[:, :8]
     err = float(np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs))
     return {"policy": "tabular Q, every operation in {fp16, bf16, tf32, fp32, fp64}, same training",
             "time_to_tol_s": t, "iters": res["iters"], "outcome": res["outcome"],
             "rel_res_true": res["rel_res_true"], "rel_err_xstar": err, "speedup_vs_fp64": t64 / t,
-            "action_mix": {M.FORMAT_NAMES[f]: int(ah[:, f].sum()) for f in range(7)},
+            "action_mix": {M.FORMAT_NAMES[f]: int(ah[:, f].sum()) for f in range(8)},
             "train_s": round(t_train, 2), "restarts": res["n_restarts"]}
 
 
@@ -636,7 +649,7 @@ def main():
         extras["batch512"] = batch512(M, pol, stream)
 
     if rank == 0:
-        ah = np.array(r0["action_hist"])[:, :7]
+        ah = np.array(r0["action_hist"])[:, :8]
         line = {
             "metric": METRIC, "value": whole_job_rate(world, args.steps, T), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
@@ -652,7 +665,7 @@ def main():
             "fp64": {"time_to_tol_s": t64, "iters": res64["iters"], "rel_res_true": res64["rel_res_true"],
                      "rel_err_xstar": xerr64},
             "speedup_vs_fp64": t64 / (1e-3 * statistics.mean(step_ms)),
-            "action_mix": {M.FORMAT_NAMES[f]: int(ah[:, f].sum()) for f in range(7)},
+            "action_mix": {M.FORMAT_NAMES[f]: int(ah[:, f].sum()) for f in range(8)},
             **extras,
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 3), "traffic": None if ratio is None else round(ratio * lb),

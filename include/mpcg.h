@@ -50,7 +50,10 @@ typedef struct mpcg_policy_s* mpcg_policy_t; /* FIXED | SCHEDULE | QTABLE | MLP 
  * ties (first index wins). fp16/bf16/fp32/fp64 follow Table 1; tf32 (not in Table 1) is
  * read as 11 significand digits with the fp32 exponent range. BF16R / FP16R store the
  * matrix values of row i as fl(a_ij / s_i) with s_i = 2^floor(log2 max_j |a_ij|) (an
- * extension: power-of-two row scaling); for ops 2-4 they round like BF16 / FP16. */
+ * extension: power-of-two row scaling); for ops 2-4 they round like BF16 / FP16. Q52 is
+ * Table 1's quarter precision (u = 2^-3: 3 significand digits, e_min = -14, e_max = 15,
+ * x_max = 57344), stored in one byte (the fp8 E5M2 layout); it is not in Section 5's set
+ * and is offered as an extra action. */
 typedef enum {
   MPCG_FP16 = 0,
   MPCG_BF16 = 1,
@@ -58,9 +61,10 @@ typedef enum {
   MPCG_FP32 = 3,
   MPCG_FP64 = 4,
   MPCG_BF16R = 5,
-  MPCG_FP16R = 6
+  MPCG_FP16R = 6,
+  MPCG_Q52 = 7
 } mpcg_prec;
-#define MPCG_NUM_FORMATS 7
+#define MPCG_NUM_FORMATS 8
 #define MPCG_NUM_OPS 4
 #define MPCG_MAX_PREC 8
 

@@ -16,7 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 OBJ_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libmpcg.so")
-SOURCES = ["cg_kernel.cu", "cg_kernel_ic.cu", "stepped.cu", "setup_kernels.cu", "mlp_kernels.cu", "api.cu"]
+SOURCES = ["cg_kernel.cu", "cg_kernel_ic.cu", "cg_lockstep.cu", "cg_lockstep_ic.cu", "stepped.cu", "setup_kernels.cu",
+           "mlp_kernels.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

@@ -99,7 +99,7 @@ struct mpcg_ctx_s {
 struct mpcg_matrix_s {
   mpcg_ctx_t ctx = nullptr;
   DevMatrix dm;
-  DevBuf rp, ci, v64, v32, vtf, v16, vbf, v16r, vbfr, rexp, dinv;
+  DevBuf rp, ci, v64, v32, vtf, v16, vbf, v16r, vbfr, v8, rexp, dinv;
   bool diag_ok = false;             // every row has a positive diagonal entry (Jacobi defined)
   DevBuf icf, icd;                  // IC(0) factor (fp32, one value per stored entry), diagonal positions
   unsigned ic_fail = 0;             // 0: not factored or factored fine; else the factorization's error bits
@@ -772,9 +772,10 @@ mpcg_status mpcg_matrix_create(mpcg_ctx_t ctx, const mpcg_csr* A, mpcg_matrix_t*
   CK(ctx, M->vbf.ensure(sizeof(__nv_bfloat16) * pn));
   CK(ctx, M->v16r.ensure(sizeof(__half) * pn));
   CK(ctx, M->vbfr.ensure(sizeof(__nv_bfloat16) * pn));
+  CK(ctx, M->v8.ensure(sizeof(q52_t) * pn));
   CK(ctx, M->rexp.ensure(sizeof(short) * ((size_t)n + 8)));
   M->bytes = (long long)(M->rp.cap + M->ci.cap + M->v64.cap + M->v32.cap + M->vtf.cap + M->v16.cap + M->vbf.cap +
-                         M->v16r.cap + M->vbfr.cap + M->rexp.cap);
+                         M->v16r.cap + M->vbfr.cap + M->v8.cap + M->rexp.cap);
   CK(ctx, cudaMemcpyAsync(M->rp.p, A->row_ptr, sizeof(int) * ((size_t)n + 1), kind, s));
   CK(ctx, cudaMemsetAsync(M->ci.p, 0, sizeof(int) * pn, s));
   CK(ctx, cudaMemsetAsync(M->v64.p, 0, sizeof(double) * pn, s));
@@ -811,9 +812,10 @@ mpcg_status mpcg_matrix_create(mpcg_ctx_t ctx, const mpcg_csr* A, mpcg_matrix_t*
   d.vbf = M->vbf.as<__nv_bfloat16>();
   d.v16r = M->v16r.as<__half>();
   d.vbfr = M->vbfr.as<__nv_bfloat16>();
+  d.v8 = M->v8.as<q52_t>();
   d.rexp = M->rexp.as<short>();
   CK(ctx, launch_convert(d, M->v32.as<float>(), M->vtf.as<float>(), M->v16.as<__half>(), M->vbf.as<__nv_bfloat16>(),
-                         M->v16r.as<__half>(), M->vbfr.as<__nv_bfloat16>(), M->rexp.as<short>(), s));
+                         M->v16r.as<__half>(), M->vbfr.as<__nv_bfloat16>(), M->v8.as<q52_t>(), M->rexp.as<short>(), s));
   // Jacobi: fp64 reciprocals of the diagonal, and whether every row has a positive one.
   {
     DevBuf bad;

@@ -9,20 +9,33 @@
 
 namespace mpcg {
 
-enum Fmt : int { F16 = 0, BF16 = 1, TF32 = 2, F32 = 3, F64 = 4, BF16R = 5, F16R = 6, NFMT = 7 };
+// Q52: Table 1's quarter precision, 3 significand digits with the fp16 exponent range
+// (e_min = -14, e_max = 15; the fp8 E5M2 layout).
+enum Fmt : int { F16 = 0, BF16 = 1, TF32 = 2, F32 = 3, F64 = 4, BF16R = 5, F16R = 6, Q52 = 7, NFMT = 8 };
 
 // Storage of a format's value and vector arrays.
-enum Store : int { ST_HALF = 0, ST_BF16 = 1, ST_FLOAT = 2, ST_DOUBLE = 3 };
+enum Store : int { ST_HALF = 0, ST_BF16 = 1, ST_FLOAT = 2, ST_DOUBLE = 3, ST_Q52 = 4 };
 
 __host__ __device__ constexpr int store_of(int f) {
   return (f == F16 || f == F16R) ? ST_HALF
          : (f == BF16 || f == BF16R) ? ST_BF16
          : (f == F64) ? ST_DOUBLE
+         : (f == Q52) ? ST_Q52
                       : ST_FLOAT;
 }
 __host__ __device__ constexpr int bytes_of(int f) {
-  return store_of(f) == ST_DOUBLE ? 8 : store_of(f) == ST_FLOAT ? 4 : 2;
+  return store_of(f) == ST_DOUBLE ? 8 : store_of(f) == ST_FLOAT ? 4 : store_of(f) == ST_Q52 ? 1 : 2;
 }
+
+// One stored q52 value: sign, 5 exponent bits and 2 fraction bits, the same fields as the
+// upper byte of an fp16 number (same exponent bias), so a q52 value is exactly the fp16
+// number whose lower byte is zero.
+struct q52_t {
+  unsigned char b;
+};
+struct q52x2_t {
+  q52_t x, y;
+};
 __host__ __device__ constexpr bool row_scaled(int f) { return f == BF16R || f == F16R; }
 // The row-scaled formats round vectors like their base format.
 __host__ __device__ constexpr int base_fmt(int f) { return f == BF16R ? BF16 : f == F16R ? F16 : f; }
@@ -70,6 +83,7 @@ __device__ __forceinline__ double round_fmt(double x, int f) {
     case BF16: return round_to<8, -126, 127>(x);
     case TF32: return round_to<11, -126, 127>(x);
     case F32: return round_to<24, -126, 127>(x);
+    case Q52: return round_to<3, -14, 15>(x);
     default: return x;
   }
 }
@@ -84,18 +98,8 @@ __device__ __forceinline__ float round_tf32(float v) {
   return __uint_as_float(u);
 }
 
-// Rounding of an fp32 accumulator onto the output format of the product (op 1). The fp16
-// and bf16 conversions are the CUDA round-to-nearest-even intrinsics (one rounding).
-__device__ __forceinline__ float round_acc(float acc, int f) {
-  switch (base_fmt(f)) {
-    case F16: return __half2float(__float2half_rn(acc));
-    case BF16: return __bfloat162float(__float2bfloat16_rn(acc));
-    case TF32: return round_tf32(acc);
-    default: return acc;
-  }
-}
-
 // Loads of stored values as the accumulator type.
+__device__ __forceinline__ float to_acc(q52_t v) { return __half2float(__ushort_as_half((unsigned short)(v.b << 8))); }
 __device__ __forceinline__ float to_acc(__half v) { return __half2float(v); }
 __device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
 __device__ __forceinline__ float to_acc(float v) { return v; }
@@ -110,9 +114,15 @@ __device__ __forceinline__ void store_exact(__nv_bfloat16* p, long long i, doubl
 __device__ __forceinline__ void store_exact(float* p, long long i, double v) { p[i] = (float)v; }
 __device__ __forceinline__ void store_exact(double* p, long long i, double v) { p[i] = v; }
 
+// A q52 value given as fp32 (exact) in storage: the upper byte of its fp16 pattern.
+__device__ __forceinline__ q52_t q52_from_exact(float v) {
+  return q52_t{(unsigned char)(__half_as_ushort(__float2half_rn(v)) >> 8)};
+}
+
 // Reads element i of a vector stored in format f, as fp64 (exact).
 __device__ __forceinline__ double load_fmt(const void* p, long long i, int f) {
   switch (store_of(f)) {
+    case ST_Q52: return (double)to_acc(((const q52_t*)p)[i]);
     case ST_HALF: return (double)__half2float(((const __half*)p)[i]);
     case ST_BF16: return (double)__bfloat162float(((const __nv_bfloat16*)p)[i]);
     case ST_FLOAT: return (double)((const float*)p)[i];
@@ -124,6 +134,7 @@ __device__ __forceinline__ double load_fmt(const void* p, long long i, int f) {
 __device__ __forceinline__ void store_fmt(void* p, long long i, double v, int f) {
   const double r = round_fmt(v, f);
   switch (store_of(f)) {
+    case ST_Q52: ((q52_t*)p)[i] = q52_from_exact((float)r); break;
     case ST_HALF: store_exact((__half*)p, i, r); break;
     case ST_BF16: store_exact((__nv_bfloat16*)p, i, r); break;
     case ST_FLOAT: store_exact((float*)p, i, r); break;
@@ -215,13 +226,18 @@ __device__ __forceinline__ bool d2f_rn(double x, float& out) {
   return false;
 }
 
-// fl_f(v) of an fp32 value (one rounding) for f in {fp16, bf16, tf32, fp32} (and the
+// fl_q52(v) of an fp32 value: the exact fp64 form rounded on its bit pattern (round to
+// nearest even, gradual underflow below 2^-14, overflow beyond 57344 to infinity).
+__device__ __forceinline__ float round_q52(float v) { return (float)round_to<3, -14, 15>(f2d(v)); }
+
+// fl_f(v) of an fp32 value (one rounding) for f in {fp16, bf16, tf32, fp32, q52} (and the
 // row-scaled variants).
 __device__ __forceinline__ float round_f2f(float v, int f) {
   switch (base_fmt(f)) {
     case F16: return __half2float(__float2half_rn(v));
     case BF16: return __bfloat162float(__float2bfloat16_rn(v));
     case TF32: return round_tf32(v);
+    case Q52: return round_q52(v);
     default: return v;
   }
 }
@@ -243,7 +259,8 @@ __device__ __forceinline__ float round_d2f(double x, int f) {
 __host__ __device__ constexpr bool contains_fmt(int a, int b) {
   return base_fmt(a) == F64 || base_fmt(a) == base_fmt(b) ||
          (base_fmt(a) == F32 && base_fmt(b) != F64) ||
-         (base_fmt(a) == TF32 && (base_fmt(b) == F16 || base_fmt(b) == BF16));
+         (base_fmt(a) == TF32 && (base_fmt(b) == F16 || base_fmt(b) == BF16 || base_fmt(b) == Q52)) ||
+         ((base_fmt(a) == F16 || base_fmt(a) == BF16) && base_fmt(b) == Q52);
 }
 
 // s + t = a + b exactly (Knuth's TwoSum), fp32, without contraction.

@@ -37,6 +37,7 @@ struct DevMatrix {
   const __nv_bfloat16* vbf;
   const __half* v16r;
   const __nv_bfloat16* vbfr;
+  const q52_t* v8;          // q52 values (Table 1's quarter precision)
   const short* rexp;        // e_i of the row scales s_i = 2^e_i of the row-scaled formats
   int sched[8];             // SpMV schedule per format
   int lanes[8];             // lanes per row per format
@@ -198,12 +199,17 @@ cudaError_t launch_cg_ic(const Launch& L, int grid, size_t smem, cudaStream_t s)
 cudaError_t launch_cg_lockstep_ic(const Launch& L, int grid, size_t smem, cudaStream_t s);
 cudaError_t cg_occupancy_ic(int* blocks_per_sm, size_t smem);
 cudaError_t cg_set_smem_limit_ic(size_t bytes);
+// the lockstep kernels (cg_lockstep.cu, cg_lockstep_ic.cu)
+cudaError_t lockstep_occupancy(int* blocks_per_sm, size_t smem);
+cudaError_t lockstep_occupancy_ic(int* blocks_per_sm, size_t smem);
+cudaError_t lockstep_set_smem_limit(size_t bytes);
+cudaError_t lockstep_set_smem_limit_ic(size_t bytes);
 cudaError_t cg_occupancy(int* blocks_per_sm, size_t smem);
 size_t cg_static_smem();
 cudaError_t launch_validate(int n, long long nnz, const int* rp, const int* ci, const double* v,
                             unsigned* flags, int* bad_row, cudaStream_t s);
 cudaError_t launch_convert(const DevMatrix& A, float* v32, float* vtf, __half* v16, __nv_bfloat16* vbf,
-                           __half* v16r, __nv_bfloat16* vbfr, short* rexp, cudaStream_t s);
+                           __half* v16r, __nv_bfloat16* vbfr, q52_t* v8, short* rexp, cudaStream_t s);
 long long mlp_nparams_dev(int H, int nprec);
 size_t mlp_grad_smem(int H, int nprec);
 cudaError_t mlp_set_smem_limit(size_t bytes);

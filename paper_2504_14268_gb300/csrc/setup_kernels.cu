@@ -65,7 +65,7 @@ __global__ void validate_rows(int n, const int* __restrict__ rp, const int* __re
 // once from fp64.
 __global__ void convert_values(int n, const int* __restrict__ rp, const double* __restrict__ v64, float* v32,
                                float* vtf, __half* v16, __nv_bfloat16* vbf, __half* v16r, __nv_bfloat16* vbfr,
-                               short* rexp) {
+                               q52_t* v8, short* rexp) {
   const int lane = threadIdx.x & 31;
   for (long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; row < n;
        row += ((long long)gridDim.x * blockDim.x) >> 5) {
@@ -85,6 +85,7 @@ __global__ void convert_values(int n, const int* __restrict__ rp, const double* 
       vtf[e] = (float)round_to<11, -126, 127>(a);
       v16[e] = __double2half(round_to<11, -14, 15>(a));
       vbf[e] = __double2bfloat16(round_to<8, -126, 127>(a));
+      v8[e] = q52_from_exact((float)round_to<3, -14, 15>(a));
       const double as = (a * s1) * s2;
       v16r[e] = __double2half(round_to<11, -14, 15>(as));
       vbfr[e] = __double2bfloat16(round_to<8, -126, 127>(as));
@@ -132,6 +133,7 @@ __global__ void to_format(const double* __restrict__ x, void* xlow, int n, int f
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float r = round_d2f(x[i], f);
     switch (store_of(f)) {
+      case ST_Q52: ((q52_t*)xlow)[i] = q52_from_exact(r); break;
       case ST_HALF: ((__half*)xlow)[i] = __float2half_rn(r); break;
       case ST_BF16: ((__nv_bfloat16*)xlow)[i] = __float2bfloat16_rn(r); break;
       default: ((float*)xlow)[i] = r; break;
@@ -374,11 +376,11 @@ cudaError_t launch_validate(int n, long long nnz, const int* rp, const int* ci, 
 }
 
 cudaError_t launch_convert(const DevMatrix& A, float* v32, float* vtf, __half* v16, __nv_bfloat16* vbf,
-                           __half* v16r, __nv_bfloat16* vbfr, short* rexp, cudaStream_t s) {
+                           __half* v16r, __nv_bfloat16* vbfr, q52_t* v8, short* rexp, cudaStream_t s) {
   if (A.n == 0) return cudaSuccess;
   cudaGetLastError();
   convert_values<<<grid_for((long long)A.n * 32, kThreads), kThreads, 0, s>>>(A.n, A.rp, A.v64, v32, vtf, v16, vbf,
-                                                                             v16r, vbfr, rexp);
+                                                                             v16r, vbfr, v8, rexp);
   return cudaGetLastError();
 }
 

@@ -445,6 +445,7 @@ __device__ __noinline__ void ic_phase(const Launch& L, const DevSys& S, Rows R, 
 __device__ __forceinline__ double load_q(const DevSys& S, int i, int p1) {
   double v;
   switch (store_of(p1)) {
+    case ST_Q52: v = f2d(to_acc(((const q52_t*)S.q)[i])); break;
     case ST_HALF: v = f2d(__half2float(((const __half*)S.q)[i])); break;
     case ST_BF16: v = f2d(__bfloat162float(((const __nv_bfloat16*)S.q)[i])); break;
     case ST_FLOAT: v = f2d(((const float*)S.q)[i]); break;
@@ -457,6 +458,7 @@ __device__ __forceinline__ double load_q(const DevSys& S, int i, int p1) {
 __device__ __forceinline__ void store_low(void* plow, int i, double v, int f) {
   const float r = round_d2f(v, f);
   switch (store_of(f)) {
+    case ST_Q52: ((q52_t*)plow)[i] = q52_from_exact(r); break;
     case ST_HALF: ((__half*)plow)[i] = __float2half_rn(r); break;
     case ST_BF16: ((__nv_bfloat16*)plow)[i] = __float2bfloat16_rn(r); break;
     default: ((float*)plow)[i] = r; break;
@@ -925,6 +927,8 @@ template <>
 __device__ __forceinline__ __half to_storage<__half>(float v) { return __float2half_rn(v); }
 template <>
 __device__ __forceinline__ __nv_bfloat16 to_storage<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ q52_t to_storage<q52_t>(float v) { return q52_from_exact(v); }
 
 // Phase B rows: r -= alpha q (fp64), ||r||^2 (fp64) and, unless sigma is ||r||^2 itself,
 // the sigma terms. QT: storage of q; SCALED: q carries the row scale 2^e_i.
@@ -999,6 +1003,7 @@ template <> struct PairOf<double> { using type = double2; };
 template <> struct PairOf<float> { using type = float2; };
 template <> struct PairOf<__half> { using type = __half2; };
 template <> struct PairOf<__nv_bfloat16> { using type = __nv_bfloat162; };
+template <> struct PairOf<q52_t> { using type = q52x2_t; };
 
 constexpr int kPairs = 2;  // row pairs per thread in flight
 
@@ -1147,6 +1152,7 @@ __device__ __noinline__ void phase_b(const DevSys& S, Rows R, double alpha, int 
       case F16: phase_b_pairs<__half, false>(S, R, alpha, p2, p4, sig_rr, rr, sg); return;
       case BF16: phase_b_pairs<__nv_bfloat16, false>(S, R, alpha, p2, p4, sig_rr, rr, sg); return;
       case F16R: phase_b_pairs<__half, true>(S, R, alpha, p2, p4, sig_rr, rr, sg); return;
+      case Q52: phase_b_pairs<q52_t, false>(S, R, alpha, p2, p4, sig_rr, rr, sg); return;
       default: phase_b_pairs<__nv_bfloat16, true>(S, R, alpha, p2, p4, sig_rr, rr, sg); return;
     }
   }
@@ -1157,6 +1163,7 @@ __device__ __noinline__ void phase_b(const DevSys& S, Rows R, double alpha, int 
     case F16: phase_b_rows<__half, false>(S, R, alpha, p2, p4, sig_rr, rr, sg); break;
     case BF16: phase_b_rows<__nv_bfloat16, false>(S, R, alpha, p2, p4, sig_rr, rr, sg); break;
     case F16R: phase_b_rows<__half, true>(S, R, alpha, p2, p4, sig_rr, rr, sg); break;
+    case Q52: phase_b_rows<q52_t, false>(S, R, alpha, p2, p4, sig_rr, rr, sg); break;
     default: phase_b_rows<__nv_bfloat16, true>(S, R, alpha, p2, p4, sig_rr, rr, sg); break;
   }
 }
@@ -1167,6 +1174,7 @@ __device__ __noinline__ void phase_c(const DevSys& S, Rows R, double alpha, doub
       case ST_DOUBLE: phase_c_pairs<double>(S, R, alpha, beta, p2, p1n); return;
       case ST_FLOAT: phase_c_pairs<float>(S, R, alpha, beta, p2, p1n); return;
       case ST_HALF: phase_c_pairs<__half>(S, R, alpha, beta, p2, p1n); return;
+      case ST_Q52: phase_c_pairs<q52_t>(S, R, alpha, beta, p2, p1n); return;
       default: phase_c_pairs<__nv_bfloat16>(S, R, alpha, beta, p2, p1n); return;
     }
   }
@@ -1174,6 +1182,7 @@ __device__ __noinline__ void phase_c(const DevSys& S, Rows R, double alpha, doub
     case ST_DOUBLE: phase_c_rows<double>(S, R, alpha, beta, p2, p1n); break;
     case ST_FLOAT: phase_c_rows<float>(S, R, alpha, beta, p2, p1n); break;
     case ST_HALF: phase_c_rows<__half>(S, R, alpha, beta, p2, p1n); break;
+    case ST_Q52: phase_c_rows<q52_t>(S, R, alpha, beta, p2, p1n); break;
     default: phase_c_rows<__nv_bfloat16>(S, R, alpha, beta, p2, p1n); break;
   }
 }

@@ -14,6 +14,14 @@ struct Rows {
   int r0, r1;
 };
 
+// Read-only load of a stored value (the q52 byte through its unsigned char form).
+template <typename VT>
+__device__ __forceinline__ VT ldg_val(const VT* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ q52_t ldg_val<q52_t>(const q52_t* p) {
+  return q52_t{__ldg(reinterpret_cast<const unsigned char*>(p))};
+}
+
 // First row of part c of S parts of equal nonzero count (rows [part(c), part(c+1)) ).
 __device__ __forceinline__ int part_row(const int* rp, int n, long long nnz, int c, int S) {
   if (c <= 0) return 0;
@@ -46,12 +54,25 @@ __device__ __forceinline__ double pow2(int e) {
   return __longlong_as_double((long long)((unsigned long long)(e + 1023) << 52));
 }
 
+// p_i for the row's nu term: when nu's format is the product's (not row-scaled), fl_p3(p_i) is
+// the element of p's low copy that the product reads anyway (fl_p1(p_i)), so the fp64 p is not
+// read; otherwise p_i in fp64.
+template <typename VT>
+__device__ __forceinline__ double nu_input(const DevSys& S, const VT* xin, int row, int p1, int nu_fmt) {
+  if (nu_fmt < 0) return 0.0;
+  if constexpr (sizeof(VT) < 8) {
+    if (nu_fmt != F64 && base_fmt(nu_fmt) == base_fmt(p1) && !row_scaled(p1)) return f2d(to_acc(xin[row]));
+  }
+  return S.p[row];
+}
+
 // Row finished with q_i = qf already rounded onto p1: stored in p1's storage; then the row's
 // nu term fl_p3(p_i) fl_p3(q_i) (q_i includes the row scale 2^e_i of the row-scaled formats).
 // `pi` = p_i in fp64 (read by the caller, ahead of the row when it can).
 __device__ __forceinline__ void finish_row_low(const DevSys& S, int row, float qf, int p1, int nu_fmt, double pi,
                                                DotAcc& nu) {
   switch (store_of(p1)) {
+    case ST_Q52: ((q52_t*)S.q)[row] = q52_from_exact(qf); break;
     case ST_HALF: ((__half*)S.q)[row] = __float2half_rn(qf); break;
     case ST_BF16: ((__nv_bfloat16*)S.q)[row] = __float2bfloat16_rn(qf); break;
     default: ((float*)S.q)[row] = qf; break;
@@ -80,10 +101,10 @@ __device__ __forceinline__ void finish_row_64(const DevSys& S, int row, double t
 }
 
 // Half the distance from fl_f(v) = r to its neighbours in format f, below and above
-// (conservative at binade edges), as fp32; f is fp16, bf16 or tf32.
+// (conservative at binade edges), as fp32; f is fp16, bf16, tf32 or q52.
 __device__ __forceinline__ void half_gaps(float r, int f, float& below, float& above) {
-  const int t = base_fmt(f) == BF16 ? 8 : 11;
-  const int emin = base_fmt(f) == F16 ? -14 : -126;
+  const int t = base_fmt(f) == BF16 ? 8 : base_fmt(f) == Q52 ? 3 : 11;
+  const int emin = (base_fmt(f) == F16 || base_fmt(f) == Q52) ? -14 : -126;
   int e = (int)((__float_as_uint(r) >> 23) & 0xff) - 127;
   if (r == 0.f || e < emin) e = emin;
   const float ulp = __uint_as_float((unsigned)(e - t + 1 + 127) << 23);
@@ -301,7 +322,7 @@ __device__ void long_pass(LongRows& lr, const DevSys& S, const VT* __restrict__ 
     const int row = lr.rows[i];
     const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
     RowAcc<VT, COMP> acc;
-    for (int e = e0 + threadIdx.x; e < e1; e += kThreads) acc.add(__ldg(vals + e), xin[__ldg(ci + e)]);
+    for (int e = e0 + threadIdx.x; e < e1; e += kThreads) acc.add(ldg_val(vals + e), xin[__ldg(ci + e)]);
     acc.template reduce<32>(kFull);
     if ((threadIdx.x & 31) == 0) {
       lr.part[0][threadIdx.x >> 5] = acc.s;
@@ -311,8 +332,8 @@ __device__ void long_pass(LongRows& lr, const DevSys& S, const VT* __restrict__ 
     __syncthreads();
     if (threadIdx.x == 0) {
       for (int w = 1; w < kThreads / 32; ++w) acc.merge(lr.part[0][w], lr.part[1][w], lr.part[2][w]);
-      finish_row<VT, COMP>(S, row, e0, e1, acc, p1, nu_fmt, nu_fmt >= 0 ? S.p[row] : 0.0, nu,
-                           [&](int e) { return __ldg(vals + e); }, [&](int e) { return __ldg(ci + e); }, xin);
+      finish_row<VT, COMP>(S, row, e0, e1, acc, p1, nu_fmt, nu_input(S, xin, row, p1, nu_fmt), nu,
+                           [&](int e) { return ldg_val(vals + e); }, [&](int e) { return __ldg(ci + e); }, xin);
     }
     __syncthreads();
   }
@@ -339,11 +360,11 @@ __device__ void spmv_vec(const DevSys& S, const VT* __restrict__ vals, const VT*
       if (__shfl_sync(mask, queued, (threadIdx.x & 31) & ~(K - 1))) continue;
     }
     RowAcc<VT, COMP> acc;
-    for (int e = e0 + lane; e < e1; e += K) acc.add(__ldg(vals + e), xin[__ldg(ci + e)]);
+    for (int e = e0 + lane; e < e1; e += K) acc.add(ldg_val(vals + e), xin[__ldg(ci + e)]);
     acc.template reduce<K>(mask);
     if (lane == 0)
-      finish_row<VT, COMP>(S, row, e0, e1, acc, p1, nu_fmt, nu_fmt >= 0 ? S.p[row] : 0.0, nu,
-                           [&](int e) { return __ldg(vals + e); }, [&](int e) { return __ldg(ci + e); }, xin);
+      finish_row<VT, COMP>(S, row, e0, e1, acc, p1, nu_fmt, nu_input(S, xin, row, p1, nu_fmt), nu,
+                           [&](int e) { return ldg_val(vals + e); }, [&](int e) { return __ldg(ci + e); }, xin);
   }
   long_pass<VT, COMP>(lr, S, vals, xin, p1, nu_fmt, nu);
 }
@@ -355,6 +376,10 @@ __device__ __forceinline__ unsigned word_of(const int4& q, int w) {
 }
 template <typename VT>
 __device__ __forceinline__ VT lane_of(const int4& q, int k);
+template <>
+__device__ __forceinline__ q52_t lane_of<q52_t>(const int4& q, int k) {
+  return q52_t{(unsigned char)(word_of(q, k >> 2) >> (8 * (k & 3)))};
+}
 template <>
 __device__ __forceinline__ __half lane_of<__half>(const int4& q, int k) {
   return __ushort_as_half((unsigned short)(word_of(q, k >> 1) >> (16 * (k & 1))));
@@ -373,14 +398,14 @@ __device__ __forceinline__ double lane_of<double>(const int4& q, int k) {
 }
 
 // One thread per row with 16-byte loads: the row's column indices and values are read in
-// aligned groups of G elements (G = 8 for 16-bit values, 4 otherwise; group starts rounded
+// aligned groups of G elements (G = 16 for 8-bit values, 8 for 16-bit, 4 otherwise; group starts rounded
 // down to a multiple of G, the arrays are padded so the last group stays in bounds), so a
 // thread issues one load per 4 columns and per 16 bytes of values instead of one per
 // element; elements of a group outside the row are skipped. Long rows go to the CTA queue.
 template <typename VT, bool COMP>
 __device__ void spmv_vload(const DevSys& S, const VT* __restrict__ vals, const VT* xin, Rows R, int p1, int nu_fmt,
                            DotAcc& nu) {
-  constexpr int G = sizeof(VT) == 2 ? 8 : 4;
+  constexpr int G = sizeof(VT) == 1 ? 16 : sizeof(VT) == 2 ? 8 : 4;
   constexpr int NV = G * (int)sizeof(VT) / 16;  // 16-byte value loads per group
   const int* __restrict__ rp = S.A.rp;
   const int* __restrict__ ci = S.A.ci;
@@ -391,7 +416,7 @@ __device__ void spmv_vload(const DevSys& S, const VT* __restrict__ vals, const V
   if (row < R.r1) {
     ne0 = __ldg(rp + row);
     ne1 = __ldg(rp + row + 1);
-    if (nu_fmt >= 0) npi = S.p[row];
+    npi = nu_input(S, xin, row, p1, nu_fmt);
   }
   LongRows& lr = long_rows();
   long_begin(lr);
@@ -401,7 +426,7 @@ __device__ void spmv_vload(const DevSys& S, const VT* __restrict__ vals, const V
     if (row + kThreads < R.r1) {
       ne0 = __ldg(rp + row + kThreads);
       ne1 = __ldg(rp + row + kThreads + 1);
-      if (nu_fmt >= 0) npi = S.p[row + kThreads];
+      npi = nu_input(S, xin, row + kThreads, p1, nu_fmt);
     }
     if (e1 - e0 > kLongRow && long_queue(lr, row)) continue;
     RowAcc<VT, COMP> acc;
@@ -431,7 +456,7 @@ __device__ void spmv_vload(const DevSys& S, const VT* __restrict__ vals, const V
       for (int j = 0; j < G; ++j)
         if (g + j >= e0 && g + j < e1) acc.add(v[j], xv[j]);
     }
-    finish_row<VT, COMP>(S, row, e0, e1, acc, p1, nu_fmt, pi, nu, [&](int e) { return __ldg(vals + e); },
+    finish_row<VT, COMP>(S, row, e0, e1, acc, p1, nu_fmt, pi, nu, [&](int e) { return ldg_val(vals + e); },
                          [&](int e) { return __ldg(ci + e); }, xin);
   }
   long_pass<VT, COMP>(lr, S, vals, xin, p1, nu_fmt, nu);
@@ -490,7 +515,7 @@ __device__ void spmv_stream(const DevSys& S, const VT* __restrict__ vals, const 
       for (int e = rs + lane; e < re; e += K) acc.add(sv[e], xin[scol[e]]);
       acc.template reduce<K>(mask);
       if (lane == 0)
-        finish_row<VT, COMP>(S, row, rs, re, acc, p1, nu_fmt, nu_fmt >= 0 ? S.p[row] : 0.0, nu,
+        finish_row<VT, COMP>(S, row, rs, re, acc, p1, nu_fmt, nu_input(S, xin, row, p1, nu_fmt), nu,
                              [&](int e) { return sv[e]; }, [&](int e) { return scol[e]; }, xin);
     }
     __syncthreads();
@@ -537,6 +562,7 @@ __device__ void spmv_rows(const DevSys& S, Rows R, int p1, int nu_fmt, DotAcc& n
     case BF16: spmv_dispatch_k<__nv_bfloat16, true>(S, S.A.vbf, (const __nv_bfloat16*)S.plow, R, p1, nu_fmt, nu, sc);
       break;
     case F16R: spmv_dispatch_k<__half, true>(S, S.A.v16r, (const __half*)S.plow, R, p1, nu_fmt, nu, sc); break;
+    case Q52: spmv_dispatch_k<q52_t, true>(S, S.A.v8, (const q52_t*)S.plow, R, p1, nu_fmt, nu, sc); break;
     default: spmv_dispatch_k<__nv_bfloat16, true>(S, S.A.vbfr, (const __nv_bfloat16*)S.plow, R, p1, nu_fmt, nu, sc);
       break;
   }

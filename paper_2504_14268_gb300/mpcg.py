@@ -17,8 +17,8 @@ import numpy as np
 
 from . import build as _build
 
-FP16, BF16, TF32, FP32, FP64, BF16R, FP16R = range(7)
-FORMAT_NAMES = ["fp16", "bf16", "tf32", "fp32", "fp64", "bf16r", "fp16r"]
+FP16, BF16, TF32, FP32, FP64, BF16R, FP16R, Q52 = range(8)
+FORMAT_NAMES = ["fp16", "bf16", "tf32", "fp32", "fp64", "bf16r", "fp16r", "q52"]
 CONVERGED, MAX_ITER, BREAKDOWN = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "BAD_POLICY", 5: "TIMEOUT", 6: "INTERNAL"}
 SCHED_VECTOR, SCHED_STREAM = 0, 1
@@ -59,7 +59,7 @@ class CResult(C.Structure):
 
 class CStats(C.Structure):
     _fields_ = [("n", C.c_int32), ("nnz", C.c_int64), ("mean_row_nnz", C.c_double), ("max_row_nnz", C.c_double),
-                ("cv_row_nnz", C.c_double), ("spmv_sched", C.c_int32 * 7), ("spmv_lanes", C.c_int32 * 7),
+                ("cv_row_nnz", C.c_double), ("spmv_sched", C.c_int32 * 8), ("spmv_lanes", C.c_int32 * 8),
                 ("device_bytes", C.c_int64), ("static_features", C.c_double * 5)]
 
 

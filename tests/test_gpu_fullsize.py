@@ -76,7 +76,7 @@ def test_fullsize_spmv_sampled_rows(big, sched, lanes):
     xd = torch.as_tensor(x).cuda()
     yd = torch.empty_like(xd)
     # orc_spmv over the sampled rows reads the full vector through their column indices
-    for fmt in range(7):
+    for fmt in range(8):
         try:
             mat.set_schedule(fmt, sched, lanes)
         except M.MpcgError:
@@ -84,7 +84,7 @@ def test_fullsize_spmv_sampled_rows(big, sched, lanes):
         ctx.spmv(mat, fmt, xd, yd)
         y = yd.cpu().numpy()[rows]
         ref = _oracle_rows(sub, fmt, x)
-        base = fmt if fmt < 5 else (1 if fmt == 5 else 0)
+        base = fmt if fmt < 5 or fmt == 7 else (1 if fmt == 5 else 0)
         absref = _oracle_rows(absub, 4, np.abs(O.chop(x, base)))
         _check_rows(fmt, y, ref, absref)
         mat.set_schedule(fmt, 0, 1)

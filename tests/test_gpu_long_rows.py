@@ -43,7 +43,7 @@ def _check_products(M, A, fmts, schedules, seed):
     tried = 0
     for fmt in fmts:
         ref = O.spmv(A, fmt, x)
-        mag = O.spmv(absA, 4, np.abs(O.chop(x, fmt if fmt < 5 else (0 if fmt == 6 else 1))))
+        mag = O.spmv(absA, 4, np.abs(O.chop(x, fmt if fmt < 5 or fmt == 7 else (0 if fmt == 6 else 1))))
         for sched, lanes in schedules:
             try:
                 mat.set_schedule(fmt, sched, lanes)
@@ -61,7 +61,7 @@ def _check_products(M, A, fmts, schedules, seed):
                 bound = np.abs(ref) * 2.0 ** -23 + (lens + 64) * 2.0 ** -24 * mag * 2
                 assert np.all(np.abs(y - ref) <= bound), (fmt, sched, lanes, np.max(np.abs(y - ref) - bound))
             else:
-                # 16-bit and tf32 formats: the correctly rounded row sum
+                # 16-bit, tf32 and q52 formats: the correctly rounded row sum
                 bad = np.flatnonzero(y != ref)
                 assert bad.size == 0, (fmt, sched, lanes, bad[:5], lens[bad[:5]])
     mat.close()
@@ -71,7 +71,7 @@ def _check_products(M, A, fmts, schedules, seed):
 def test_hub_rows_every_format_and_schedule(M):
     A = I.hub_laplacian(60000, 24, 1100, 20000, 1.0, np.random.default_rng(2))
     assert np.diff(A[1]).max() > 10000
-    assert _check_products(M, A, range(7), SCHEDULES, seed=3) >= 7 * 5
+    assert _check_products(M, A, range(8), SCHEDULES, seed=3) >= 8 * 5
 
 
 def test_long_row_queue_overflow(M):
@@ -107,7 +107,7 @@ def test_solve_on_hub_graph_matches_oracle(M, fmts, tol, sched):
     xs, b = I.rhs_from_xstar(A, np.random.default_rng(7))
     ctx = M.Context(0, M.Options(min_k=0))
     mat = ctx.matrix(_dev(A))
-    for f in range(7):
+    for f in range(8):
         mat.set_schedule(f, *sched)
     bd = torch.as_tensor(b).cuda()
     x = torch.zeros_like(bd)

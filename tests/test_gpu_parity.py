@@ -73,6 +73,11 @@ def _edge_values():
     for grid in (f16, bf):
         vals += list(0.5 * (grid[:-1] + grid[1:]))  # midpoints: ties to even
         vals += list(grid[:-1] + 0.25 * (grid[1:] - grid[:-1]))
+    # q52 (3 significand digits, fp16 exponent range): every value, midpoints and quarter
+    # points between neighbours, the overflow edge x_max + ulp / 2 = 57344 + 4096
+    q8 = (np.arange(1, 0x7C, dtype=np.uint16) << 8).view(np.float16).astype(np.float64)
+    vals += list(0.5 * (q8[:-1] + q8[1:])) + list(q8[:-1] + 0.25 * (q8[1:] - q8[:-1])) + list(q8)
+    vals += [57344.0, 61439.99, 61440.0, 2.0 ** -16, 2.0 ** -17, 3 * 2.0 ** -18]
     vals += [65504.0, 65519.99, 65520.0, 3.4028235677973366e38, 2.0 ** -24, 3 * 2.0 ** -26, 2.0 ** -149,
              2.0 ** -136 * 1.5, 1e-300, 1e300]
     return np.array([v for v in vals if v != 0.0 and math.isfinite(v)])
@@ -89,7 +94,7 @@ def test_format_copies_are_bit_exact(M):
     x = np.tile([0.0, 1.0], A[0] // 2)
     xd = torch.as_tensor(x).cuda()
     yd = torch.empty_like(xd)
-    for fmt in range(7):
+    for fmt in range(8):
         ctx.spmv(mat, fmt, xd, yd)
         y = yd.cpu().numpy()
         ref = O.spmv(A, fmt, x)
@@ -115,9 +120,9 @@ def test_spmv_every_format_and_lane_count(M, which):
     xd = torch.as_tensor(x).cuda()
     yd = torch.empty_like(xd)
     absA = (n, rp, ci, np.abs(val))
-    for fmt in range(7):
+    for fmt in range(8):
         ref = O.spmv(A, fmt, x)
-        mag = O.spmv(absA, 4, np.abs(O.chop(x, fmt if fmt < 5 else (0 if fmt == 6 else 1))))
+        mag = O.spmv(absA, 4, np.abs(O.chop(x, fmt if fmt < 5 or fmt == 7 else (0 if fmt == 6 else 1))))
         for sched, lanes in SCHEDULES:
             try:
                 mat.set_schedule(fmt, sched, lanes)
@@ -135,7 +140,7 @@ def test_spmv_every_format_and_lane_count(M, which):
                 bound = ulp + 64 * 2.0 ** -24 * mag * 2
                 assert np.all(np.abs(y - ref) <= bound), (fmt, sched, lanes, np.max(np.abs(y - ref) - bound))
             else:
-                # 16-bit and tf32 formats: the correctly rounded row sum, as the oracle's
+                # 16-bit, tf32 and q52 formats: the correctly rounded row sum, as the oracle's
                 # (exact products summed in fp64, then rounded once)
                 assert np.array_equal(y, ref), (fmt, sched, lanes, np.flatnonzero(y != ref)[:5])
 
@@ -148,6 +153,9 @@ def test_spmv_every_format_and_lane_count(M, which):
     ((1, 1, 1, 1), 1e-2, 200),
     ((6, 0, 3, 4), 1e-3, 200),
     ((5, 4, 4, 3), 1e-2, 200),
+    ((7, 4, 4, 4), 1e-3, 200),
+    ((7, 7, 7, 7), 1e-3, 200),
+    ((4, 4, 7, 7), 1e-3, 200),
 ])
 def test_fixed_policy_history_matches_oracle(M, fmts, tol, maxit):
     A, b, xs = I.cfg_poisson32()

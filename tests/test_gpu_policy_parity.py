@@ -157,7 +157,10 @@ def test_training_round_with_four_lanes_matches_oracle(M):
     xs, b = I.rhs_from_xstar(A, np.random.default_rng(43))
     sets.append((A, b, xs))
     precs, cost = (O.FP32, O.FP64), (1.0, 2.0)
-    oo = O.Options(seed=9, min_k=0, precs=precs, cost={O.FP32: 1.0, O.FP64: 2.0})
+    # the product stays in fp64 (its fp32 form accumulates in fp32 on the GPU, so histories
+    # drift apart by about 1e-5 over an episode); z and the two dots choose from {fp32, fp64}
+    # and round alike on both sides, so the replay order is checked to rounding accuracy
+    oo = O.Options(seed=9, min_k=0, precs=precs, cost={O.FP32: 1.0, O.FP64: 2.0}, op_mask=(0b10, 0b11, 0b11, 0b11))
     E, tmax = 8, 300
     qt = O.QTable.zeros(oo)
     it_o = np.array([O.train_round(oo, [s[0] for s in sets], [s[1] for s in sets], 1e-6, tmax, e, E, qt)
@@ -203,9 +206,11 @@ def test_adam_step_matches_oracle(M):
         w_before = w.copy()
         ctx.mlp_adam(w, m, v, g, t, lr)
         O.adam(wo, mo, vo, g.astype(np.float64), t, lr=lr)
-        # moments to fp32 accuracy, the step to a few fp32 units of lr
-        assert np.allclose(m, mo, rtol=1e-5, atol=1e-12)
-        assert np.allclose(v, vo, rtol=1e-5, atol=1e-20)
+        # the kernel works in fp32 with beta1 = 0.9 and beta2 = 0.999 rounded to fp32: 1 - beta2
+        # is then 1.3e-5 (relative) away from the oracle's fp64 value, so the moments agree to
+        # 1e-4 relative; the steps (a ratio of the moments) to a small fraction of lr
+        assert np.allclose(m, mo, rtol=1e-4, atol=1e-12)
+        assert np.allclose(v, vo, rtol=1e-4, atol=1e-20)
         step_g = w.astype(np.float64) - w_before
         step_o = wo - w_before.astype(np.float64)
         assert np.all(np.abs(step_g - step_o) <= 1e-4 * lr + 2e-7 * np.abs(wo)), t
