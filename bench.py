@@ -222,6 +222,16 @@ def iter_bytes(n: int, Z: int, fmt: tuple, flags: int, next_p1: int) -> float:
     return a + bb + c + t
 
 
+def product_bytes(n: int, Z: int, fmt: tuple) -> float:
+    """Algorithmic bytes of phase A alone (the product kernel): values and columns, row_ptr,
+    p's low copy, p in fp64 for nu when needed, q written."""
+    p1, p3 = fmt[0], fmt[2]
+    v = BYTES[p1]
+    base = {5: 1, 6: 0}
+    nu_from_low = p3 != 4 and base.get(p3, p3) == base.get(p1, p1) and p1 not in (5, 6)
+    return Z * (v + 4) + 4 * (n + 1) + n * v + (0 if p1 == 4 or nu_from_low else 8 * n) + n * v
+
+
 def launch_bytes(n: int, Z: int, hist) -> float:
     """Bytes of one persistent launch: initialisation (b read, x, r, p written), every
     iteration of the history, and the closing fp64 residual."""
@@ -524,6 +534,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the full-precision-set policy, the 512-system batch and the SpMV table")
+    ap.add_argument("--history-out", default=None,
+                    help="write the first timed solve's per-iteration records (numpy .npy) to this path")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -600,6 +612,17 @@ def main():
     lb = launch_bytes(n, Z, h0)
     achieved = lb / (statistics.mean(step_ms) / 1e3) / 1e9
     ratio = traffic_ratio()
+    if args.history_out:
+        np.save(args.history_out, h0)
+    # the product kernel alone (phase A of every iteration): its algorithmic bytes over its
+    # device time, the globaltimer span from the previous phase's end to the product's end
+    # (launch gap included) recorded in the history of the first timed solve
+    pa_bytes = sum(product_bytes(n, Z, tuple(int(f) for f in h0["fmt"][k])) for k in range(len(h0)))
+    pa_s = float(np.sum(h0["ns_a"].astype(np.float64))) / 1e9
+    prod = {"kernel": "cg_phase<A> (product and nu)", "achieved": round(pa_bytes / pa_s / 1e9, 1), "peak": hbm,
+            "unit": "GB/s", "frac": round(pa_bytes / pa_s / 1e9 / hbm, 3), "share_of_step":
+            round(pa_s / (step_ms[0] / 1e3), 3), "source": "per-phase device time (globaltimer) of the first timed "
+                                                          "solve's iteration records"}
 
     # end to end through the C ABI with pinned host buffers (H2D of b, D2H of x inside)
     bh = torch.as_tensor(b).pin_memory()
@@ -669,9 +692,12 @@ def main():
             **extras,
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 3), "traffic": None if ratio is None else round(ratio * lb),
-                         "peak_source": peak_kind, "kernel": "cg_persistent", "bytes_per_launch": lb,
-                         "traffic_note": "DRAM bytes per algorithmic byte from an ncu capture of the same kernel "
+                         "peak_source": peak_kind, "kernel": "solve step", "bytes_per_launch": lb,
+                         "kernel_note": "the whole step: one launch of the solve (the stepped graph's phase "
+                                        "kernels, or the persistent kernel), CUDA events around it",
+                         "traffic_note": "DRAM bytes per algorithmic byte from an ncu capture of the same kernels "
                                          "on the 128^3 case, times this launch's algorithmic bytes"},
+            "roofline_product": prod,
             "e2e": {"value": args.steps / e2e_T, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                     "d2h_bytes_per_step": 8 * n + 296},
             "cpu_baseline": cpu,

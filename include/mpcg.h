@@ -149,7 +149,18 @@ typedef struct {
                             * iteration, repeated on the device by a conditional while-loop
                             * CUDA graph (precond = 2 always runs the persistent launch,
                             * whose substitutions need every CTA resident)              */
-  int32_t reserved_opt;
+  int32_t variant;         /* 0: the CG of Section 3 (three reductions per iteration); 1: the
+                            * single-reduction iteration of Chronopoulos and Gear (an
+                            * extension, equal to CG in exact arithmetic): u = fl_p2(M^-1 r),
+                            * w = fl_p1(A fl_p1(u)), gamma = fl_p4(r^T u) (op 4),
+                            * delta = fl_p3(w^T u) (op 3), beta = gamma / gamma_prev,
+                            * alpha = gamma / (delta - beta gamma / alpha_prev), p = u + beta p,
+                            * s = w + beta s, x += alpha p, r -= alpha s, and ||r_{k+1}||^2
+                            * expanded from inner products of the same pass, so that one
+                            * reduction serves an iteration. Runs in the lockstep and
+                            * stepped kernels (every launch with variant 1 uses them), with
+                            * M = I or Jacobi (precond 2 is refused); mpcg_solve_noalloc
+                            * refuses it                                                  */
 } mpcg_options;
 
 /* Result of one solve. */

@@ -56,6 +56,7 @@ class Opts(C.Structure):
         ("gamma", C.c_double), ("eps0", C.c_double), ("eps_floor", C.c_double), ("seed", C.c_uint64),
         ("unvisited_fallback", C.c_int), ("true_res_every", C.c_int), ("true_res_at_conv", C.c_int),
         ("op_mask", C.c_int * 4), ("on_breakdown", C.c_int), ("mlp_hidden", C.c_int), ("precond", C.c_int),
+        ("variant", C.c_int),
     ]
 
 
@@ -170,12 +171,13 @@ class Options:
     on_breakdown: int = 0
     mlp_hidden: int = 64
     precond: int = 0
+    variant: int = 0  # 0: the CG of Section 3; 1: the single-reduction iteration (orc_run_sr)
 
     def c(self) -> Opts:
         o = Opts()
         for name in ("b_bins", "r_bins", "t_bin", "min_k", "eps_min", "w1", "w2", "w3", "lr", "gamma",
                      "eps0", "eps_floor", "seed", "unvisited_fallback", "true_res_every",
-                     "true_res_at_conv", "on_breakdown", "mlp_hidden", "precond"):
+                     "true_res_at_conv", "on_breakdown", "mlp_hidden", "precond", "variant"):
             setattr(o, name, getattr(self, name))
         for j in range(4):
             o.op_mask[j] = int(self.op_mask[j])
@@ -371,6 +373,7 @@ _PRECOND_ERRORS = {
     -2: "incomplete Cholesky breaks down (a non-positive pivot)",
     -3: "incomplete Cholesky needs a diagonal entry in every row, strictly increasing columns "
         "and a symmetric pattern",
+    -4: "the single-reduction iteration runs with M = I or Jacobi",
 }
 
 

@@ -154,6 +154,8 @@ typedef struct {
                              2: IC(0) in fp32 (orc_ic0): z = fl_p2(L^-T L^-1 r) with
                              the solves in fp32, the initial and restart directions
                              z = L^-T L^-1 r unrounded beyond fp32                      */
+  int variant;            /* 0: the CG of Section 3 (orc_run); 1: the single-reduction
+                             iteration of orc_run_sr (M = I or Jacobi)                  */
 } orc_opts;
 
 enum { ORC_POL_FIXED = 0, ORC_POL_SCHEDULE = 1, ORC_POL_QTABLE = 2, ORC_POL_MLP = 3 };
@@ -705,6 +707,286 @@ static void learn_step(const orc_opts* o, orc_policy* pol, const orc_transition*
   if (trans) trans[(*ntrans)++] = *t;
 }
 
+/* The action of iteration k in state s (Algorithm 1's epsilon-greedy choice in training,
+ * Algorithm 2's greedy choice in inference, or the fixed / replayed formats): fmt[j] the
+ * format of operation j, act[j] its index in P (-1 when the format is not in P). f holds the
+ * MLP policy's features; h1, h2, qout are its work arrays. */
+static void choose_formats(const orc_opts* o, const orc_policy* pol, int mode, int k, int s, double eps,
+                           uint64_t ep, uint64_t lane, int locked, const double* f, int H, int nout,
+                           double* h1, double* h2, double* qout, int fmt[4], int act[4], int* explored) {
+  if (locked) {
+    for (int j = 0; j < 4; ++j) fmt[j] = ORC_FP64;
+  } else if (pol->kind == ORC_POL_FIXED) {
+    for (int j = 0; j < 4; ++j) fmt[j] = pol->fixed[j];
+  } else if (pol->kind == ORC_POL_SCHEDULE) {
+    int row = k < pol->sched_len ? k : pol->sched_len - 1;
+    for (int j = 0; j < 4; ++j) fmt[j] = pol->sched[(int64_t)row * 4 + j];
+  } else if (pol->kind == ORC_POL_QTABLE) {
+    for (int j = 0; j < 4; ++j) {
+      int ex = 0;
+      act[j] = select_qtable(o, pol, mode, j, s, eps, ep, lane, k, &ex);
+      *explored |= ex;
+      fmt[j] = o->precs[act[j]];
+    }
+  } else {
+    /* Learned policy: greedy per operation on the MLP's Q-values (same tie rule). */
+    orc_mlp_forward(pol->mlp, H, nout, f, h1, h2, qout);
+    for (int j = 0; j < 4; ++j) {
+      act[j] = argmax_allowed(o, j, qout + j * o->nprec);
+      if (mode == ORC_MODE_TRAIN) {
+        double u;
+        uint32_t pick;
+        orc_draw(o->seed, ep, lane, (uint64_t)k, (uint64_t)j, &u, &pick);
+        if (u < eps) {
+          act[j] = random_allowed(o, j, pick);
+          *explored = 1;
+        }
+      }
+      fmt[j] = o->precs[act[j]];
+    }
+  }
+  if (locked || pol->kind == ORC_POL_FIXED || pol->kind == ORC_POL_SCHEDULE)
+    for (int j = 0; j < 4; ++j) act[j] = index_of(o, fmt[j]);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Single-reduction variant of the iteration (a widening beyond the paper).    */
+/* ------------------------------------------------------------------------- */
+
+/* Chronopoulos and Gear's form of CG (J. Comput. Appl. Math. 25, 1989), identical to the CG
+ * of Section 3 in exact arithmetic, in which every inner product of an iteration is formed
+ * from vectors that exist at the same time, so that one global reduction serves a whole
+ * iteration. The four operations of Section 4.2 keep their roles:
+ *   u_k = fl_p2(M^-1 r_k)                                   (op 2, z of Section 3)
+ *   w_k = fl_p1(A fl_p1(u_k))                               (op 1, the product)
+ *   gamma_k = fl_p4(sum fl_p4(r_i) fl_p4(u_i))              (op 4, sigma)
+ *   delta_k = fl_p3(sum fl_p3(w_i) fl_p3(u_i))              (op 3, the curvature product)
+ *   beta_k = gamma_k / gamma_{k-1},  nu_k = delta_k - beta_k gamma_k / alpha_{k-1}
+ *     (at k = 0 and after r was replaced: beta_k = 0, nu_k = delta_k)
+ *   alpha_k = gamma_k / nu_k                                (fp64 scalars)
+ *   p_k = u_k + beta_k p_{k-1},  s_k = w_k + beta_k s_{k-1} (s_k = A p_k in exact arithmetic)
+ *   x_{k+1} = x_k + alpha_k p_k,  r_{k+1} = r_k - alpha_k s_k        (fp64)
+ * READING (what the variant stops on): the residual norm of the next state comes from the
+ * same reduction, expanding ||r_k - alpha_k s_k||^2 with s_k = w_k + beta_k s_{k-1}:
+ *   rr_{k+1} = rr_k - 2 alpha_k (r_k.w_k + beta_k r_k.s_{k-1})
+ *            + alpha_k^2 (w_k.w_k + 2 beta_k w_k.s_{k-1} + beta_k^2 s_{k-1}.s_{k-1}),
+ * with every inner product in fp64 and rr_k = r_k.r_k formed directly, clamped at 0; rho_{k+1} =
+ * sqrt(rr_{k+1}) / ||b|| drives the stopping test, the reward and the next state. The
+ * breakdown rules, the residual replacement (which restarts the recurrence: beta = 0) and the
+ * fp64 restart follow orc_run. Parity unpinned beyond the equality with orc_run's CG in fp64
+ * and the step-by-step recomputation of its first iterations (tests). */
+int orc_run_sr(const orc_opts* o, int n, const int32_t* rp, const int32_t* ci, const double* val,
+               const double* b, double* x, double tau, int max_iter, orc_policy* pol, int mode,
+               uint64_t ep, uint64_t lane, double eps, orc_transition* trans, int32_t* ntrans,
+               orc_rec* hist, double* feat_out, orc_result* res) {
+  size_t nb = sizeof(double) * (size_t)(n > 0 ? n : 1);
+  double* r = malloc(nb);
+  double* u = malloc(nb);
+  double* w = malloc(nb);
+  double* p = calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double* sv = calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double* rt = malloc(nb);
+  double* dinv = malloc(nb);
+  int nout = 4 * o->nprec;
+  int H = o->mlp_hidden > 0 ? o->mlp_hidden : 1;
+  double* h1 = malloc(sizeof(double) * H);
+  double* h2 = malloc(sizeof(double) * H);
+  double* qout = malloc(sizeof(double) * nout);
+  orc_feat_state fs;
+  memset(&fs, 0, sizeof(fs));
+  if (ntrans) *ntrans = 0;
+  for (int i = 0; i < n; ++i) dinv[i] = 1.0;
+  if (o->precond == 1) {
+    for (int i = 0; i < n; ++i) {
+      double d = 0.0;
+      for (int e = rp[i]; e < rp[i + 1]; ++e)
+        if (ci[e] == i) d = val[e];
+      if (!(d > 0.0)) {
+        free(r); free(u); free(w); free(p); free(sv); free(rt); free(dinv); free(h1); free(h2); free(qout);
+        return -1;
+      }
+      dinv[i] = 1.0 / d;
+    }
+  } else if (o->precond != 0) {
+    free(r); free(u); free(w); free(p); free(sv); free(rt); free(dinv); free(h1); free(h2); free(qout);
+    return -4;
+  }
+  double bb = 0.0;
+  for (int i = 0; i < n; ++i) bb += b[i] * b[i];
+  double bnorm = sqrt(bb);
+  double rr = orc_true_residual(n, rp, ci, val, b, x, r);
+  double rho = bnorm > 0 ? sqrt(rr) / bnorm : 0.0;
+  int outcome = ORC_MAX_ITER, iters = max_iter, nrec = 0;
+  if (n == 0 || bnorm == 0.0) {
+    for (int i = 0; i < n; ++i) x[i] = 0.0;
+    outcome = ORC_CONVERGED;
+    iters = 0;
+    rho = 0.0;
+    max_iter = 0;
+  }
+  fs.rho_hist[0] = rho;
+  int locked = 0, restart = 1;
+  double gamma_prev = 0.0, alpha_prev = 0.0;
+  double fstat[5] = {0, 0, 0, 0, 0};
+  if (pol->feat_static) memcpy(fstat, pol->feat_static, sizeof(fstat));
+
+  for (int k = 0; k < max_iter; ++k) {
+    int s = orc_state(o, k, rho);
+    int fmt[4], act[4], explored = 0;
+    double f[ORC_NFEAT];
+    for (int j = 0; j < 5; ++j) f[j] = fstat[j];
+    orc_dynamic_features(o, k, &fs, f);
+    if (feat_out) memcpy(feat_out + (int64_t)k * ORC_NFEAT, f, sizeof(f));
+    choose_formats(o, pol, mode, k, s, eps, ep, lane, locked, f, H, nout, h1, h2, qout, fmt, act, &explored);
+    int learn = mode == ORC_MODE_TRAIN && act[0] >= 0 && act[1] >= 0 && act[2] >= 0 && act[3] >= 0;
+    orc_rec rec;
+    memset(&rec, 0, sizeof(rec));
+    rec.k = k;
+    rec.state = s;
+    for (int j = 0; j < 4; ++j) { rec.fmt[j] = fmt[j]; rec.act[j] = act[j]; }
+    rec.flags = explored ? 8 : 0;
+    rec.rho = rho;
+
+    /* u_k = fl_p2(M^-1 r_k); w_k = fl_p1(A fl_p1(u_k)); gamma_k, delta_k */
+    for (int i = 0; i < n; ++i) u[i] = orc_chop(o->precond == 1 ? r[i] * dinv[i] : r[i], fmt[1]);
+    orc_spmv(n, rp, ci, val, fmt[0], u, w);
+    double gamma = orc_dot(n, r, u, fmt[3]);
+    double delta = orc_dot(n, w, u, fmt[2]);
+    double beta = restart ? 0.0 : gamma / gamma_prev;
+    double nu = restart ? delta : delta - beta * gamma / alpha_prev;
+    double alpha = gamma / nu;
+    rec.nu = nu;
+    rec.alpha = alpha;
+    rec.sigma = gamma;
+    rec.beta = beta;
+    int stop = 0;
+    orc_transition t = {s, s, {act[0], act[1], act[2], act[3]}, 0.0, 1, 0};
+    if (!(nu > 0.0) || !isfinite(nu) || !isfinite(alpha) || !isfinite(beta)) {
+      if (rho < tau && isfinite(nu)) {
+        outcome = ORC_CONVERGED;
+        iters = k;
+        rec.flags |= 1;
+        t.reward = learn ? orc_reward(o, rho, act, tau) : 0.0;
+      } else {
+        outcome = ORC_BREAKDOWN;
+        iters = k;
+        rec.flags |= 2;
+        t.reward = learn ? orc_reward_breakdown(o, act) : 0.0;
+      }
+      stop = 1;
+    } else {
+      /* the inner products of the norm recurrence (fp64, the vectors before the update) */
+      double rr_k = 0.0, rw = 0.0, rs = 0.0, ww = 0.0, ws = 0.0, ss = 0.0;
+      for (int i = 0; i < n; ++i) {
+        rr_k += r[i] * r[i];
+        rw += r[i] * w[i];
+        rs += r[i] * sv[i];
+        ww += w[i] * w[i];
+        ws += w[i] * sv[i];
+        ss += sv[i] * sv[i];
+      }
+      double rr_next = rr_k - 2.0 * alpha * (rw + beta * rs) + alpha * alpha * (ww + 2.0 * beta * ws + beta * beta * ss);
+      if (rr_next < 0.0) rr_next = 0.0;
+      double rho_rec = sqrt(rr_next) / bnorm;
+      /* p_k, s_k, x_{k+1}, r_{k+1} (fp64) */
+      for (int i = 0; i < n; ++i) {
+        p[i] = u[i] + beta * p[i];
+        sv[i] = w[i] + beta * sv[i];
+        x[i] = x[i] + alpha * p[i];
+        r[i] = r[i] - alpha * sv[i];
+      }
+      double rho_new = rho_rec;
+      int check = (o->true_res_every > 0 && (k + 1) % o->true_res_every == 0) ||
+                  (o->true_res_at_conv && rho_rec < tau && k >= o->min_k);
+      int replaced = 0;
+      if (check && isfinite(rho_rec)) {
+        double nt = orc_true_residual(n, rp, ci, val, b, x, rt);
+        for (int i = 0; i < n; ++i) r[i] = rt[i];
+        double rho_t = sqrt(nt) / bnorm;
+        fs.gap_log = (rho_t > 0 && rho_rec > 0) ? log10(rho_t / rho_rec) : 0.0;
+        rho_new = rho_t;
+        rec.flags |= 4;
+        replaced = 1;
+      }
+      rec.rho = rho_new;
+      if (!isfinite(rho_new)) {
+        outcome = ORC_BREAKDOWN;
+        iters = k + 1;
+        rec.flags |= 2;
+        t.reward = learn ? orc_reward_breakdown(o, act) : 0.0;
+        stop = 1;
+      } else if (rho_new < tau && k >= o->min_k) {
+        outcome = ORC_CONVERGED;
+        iters = k + 1;
+        rec.flags |= 1;
+        t.reward = learn ? orc_reward(o, rho_new, act, tau) : 0.0;
+        rho = rho_new;
+        stop = 1;
+      } else {
+        t.reward = learn ? orc_reward(o, rho_new, act, tau) : 0.0;
+        t.s_next = orc_state(o, k + 1, rho_new);
+        t.terminal = 0;
+        gamma_prev = gamma;
+        alpha_prev = alpha;
+        restart = replaced;
+        for (int h = 8; h > 0; --h) fs.rho_hist[h] = fs.rho_hist[h - 1];
+        fs.rho_hist[0] = rho_new;
+        fs.alpha_prev = alpha;
+        fs.beta_prev = beta;
+        fs.have_prev = 1;
+        for (int j = 0; j < 4; ++j) fs.prev_act[j] = act[j] >= 0 ? act[j] : 0;
+        rho = rho_new;
+      }
+    }
+    if (stop && outcome == ORC_BREAKDOWN && mode == ORC_MODE_INFER && o->on_breakdown && !locked) {
+      /* fp64 restart from the current x (as orc_run): r = b - A x, the recurrence restarts */
+      double nt = orc_true_residual(n, rp, ci, val, b, x, r);
+      for (int i = 0; i < n; ++i) p[i] = sv[i] = 0.0;
+      rho = sqrt(nt) / bnorm;
+      locked = 1;
+      restart = 1;
+      rec.flags |= 16;
+      for (int h = 8; h > 0; --h) fs.rho_hist[h] = fs.rho_hist[h - 1];
+      fs.rho_hist[0] = rho;
+      stop = 0;
+      outcome = ORC_MAX_ITER;
+      iters = max_iter;
+      if (!isfinite(rho)) {
+        outcome = ORC_BREAKDOWN;
+        iters = k + 1;
+        stop = 1;
+      } else if (rho < tau && k >= o->min_k) {
+        outcome = ORC_CONVERGED;
+        iters = k + 1;
+        stop = 1;
+      }
+    }
+    rec.reward = t.reward;
+    if (learn) learn_step(o, pol, &t, trans, ntrans);
+    if (hist) hist[k] = rec;
+    nrec = k + 1;
+    if (stop) break;
+  }
+  if (feat_out && outcome != ORC_CONVERGED && outcome != ORC_BREAKDOWN && max_iter > 0) {
+    double f[ORC_NFEAT];
+    for (int j = 0; j < 5; ++j) f[j] = fstat[j];
+    orc_dynamic_features(o, max_iter, &fs, f);
+    memcpy(feat_out + (int64_t)max_iter * ORC_NFEAT, f, sizeof(f));
+  }
+  if (res) {
+    res->outcome = outcome;
+    res->iters = iters;
+    res->nrec = nrec;
+    double nt = orc_true_residual(n, rp, ci, val, b, x, rt);
+    res->rho_true = bnorm > 0 ? sqrt(nt) / bnorm : 0.0;
+    double r2 = 0.0;
+    for (int i = 0; i < n; ++i) r2 += r[i] * r[i];
+    res->rho_rec = bnorm > 0 ? sqrt(r2) / bnorm : 0.0;
+  }
+  free(r); free(u); free(w); free(p); free(sv); free(rt); free(dinv); free(h1); free(h2); free(qout);
+  return outcome;
+}
+
 /* Runs one CG solve with the given policy.
  *   mode INFER: Algorithm 2. mode TRAIN: Algorithm 1's episode body with epsilon-greedy
  *   selection; a QTABLE policy's tables are updated online after every iteration
@@ -716,6 +998,9 @@ int orc_run(const orc_opts* o, int n, const int32_t* rp, const int32_t* ci, cons
             const double* b, double* x, double tau, int max_iter, orc_policy* pol, int mode,
             uint64_t ep, uint64_t lane, double eps, orc_transition* trans, int32_t* ntrans,
             orc_rec* hist, double* feat_out, orc_result* res) {
+  if (o->variant == 1)
+    return orc_run_sr(o, n, rp, ci, val, b, x, tau, max_iter, pol, mode, ep, lane, eps, trans, ntrans, hist,
+                      feat_out, res);
   size_t nb = sizeof(double) * (size_t)(n > 0 ? n : 1);
   double* r = malloc(nb);
   double* p = malloc(nb);
@@ -792,39 +1077,7 @@ int orc_run(const orc_opts* o, int n, const int32_t* rp, const int32_t* ci, cons
     for (int j = 0; j < 5; ++j) f[j] = fstat[j];
     orc_dynamic_features(o, k, &fs, f);
     if (feat_out) memcpy(feat_out + (int64_t)k * ORC_NFEAT, f, sizeof(f));
-    if (locked) {
-      for (int j = 0; j < 4; ++j) fmt[j] = ORC_FP64;
-    } else if (pol->kind == ORC_POL_FIXED) {
-      for (int j = 0; j < 4; ++j) fmt[j] = pol->fixed[j];
-    } else if (pol->kind == ORC_POL_SCHEDULE) {
-      int row = k < pol->sched_len ? k : pol->sched_len - 1;
-      for (int j = 0; j < 4; ++j) fmt[j] = pol->sched[(int64_t)row * 4 + j];
-    } else if (pol->kind == ORC_POL_QTABLE) {
-      for (int j = 0; j < 4; ++j) {
-        int ex = 0;
-        act[j] = select_qtable(o, pol, mode, j, s, eps, ep, lane, k, &ex);
-        explored |= ex;
-        fmt[j] = o->precs[act[j]];
-      }
-    } else {
-      /* Learned policy: greedy per operation on the MLP's Q-values (same tie rule). */
-      orc_mlp_forward(pol->mlp, H, nout, f, h1, h2, qout);
-      for (int j = 0; j < 4; ++j) {
-        act[j] = argmax_allowed(o, j, qout + j * o->nprec);
-        if (mode == ORC_MODE_TRAIN) {
-          double u;
-          uint32_t pick;
-          orc_draw(o->seed, ep, lane, (uint64_t)k, (uint64_t)j, &u, &pick);
-          if (u < eps) {
-            act[j] = random_allowed(o, j, pick);
-            explored = 1;
-          }
-        }
-        fmt[j] = o->precs[act[j]];
-      }
-    }
-    if (locked || pol->kind == ORC_POL_FIXED || pol->kind == ORC_POL_SCHEDULE)
-      for (int j = 0; j < 4; ++j) act[j] = index_of(o, fmt[j]);
+    choose_formats(o, pol, mode, k, s, eps, ep, lane, locked, f, H, nout, h1, h2, qout, fmt, act, &explored);
     int learn = mode == ORC_MODE_TRAIN && act[0] >= 0 && act[1] >= 0 && act[2] >= 0 && act[3] >= 0;
 
     orc_rec rec;

@@ -71,7 +71,7 @@ struct Plan {
   size_t icwork_bytes = 0;
   bool lockstep = false;
   bool stepped = false;      // one system, one kernel per phase in a while-loop graph
-  int sgrid[4] = {0, 0, 0, 0};
+  int sgrid[kPhaseKernels] = {0, 0, 0, 0, 0, 0};
   size_t ssmem = 0;
   cudaGraphExec_t sexec = nullptr;
   ~Plan() {
@@ -90,7 +90,7 @@ struct mpcg_ctx_s {
   int occ = 0;      // CTAs per SM of the solver kernel without the stream ring
   int occ_s = 0;    // ... with the stream ring (2 * kStageBytes of dynamic shared memory)
   int socc = 0, socc_s = 0;  // same for the standalone product kernel
-  int pocc[4] = {0, 0, 0, 0}, pocc_s[4] = {0, 0, 0, 0};  // the stepped solve's phase kernels
+  int pocc[kPhaseKernels] = {}, pocc_s[kPhaseKernels] = {};  // the stepped solve's phase kernels
   std::string err;
   Plan plan;   // reused by mpcg_solve / mpcg_solve_batched / training
   DevBuf spmv_x, spmv_q, spmv_y, spmv_err;
@@ -187,6 +187,9 @@ mpcg_status build_optview(mpcg_ctx_t ctx, const mpcg_options& o, OptView& v) {
   if (o.precond < 0 || o.precond > 2) return fail(ctx, MPCG_ERR_INVALID_ARG, "precond must be 0, 1 or 2");
   if (!(o.edge_tol >= 0.0 && o.edge_tol < 1.0)) return fail(ctx, MPCG_ERR_INVALID_ARG, "edge_tol must be in [0, 1)");
   if (o.stepped < 0 || o.stepped > 2) return fail(ctx, MPCG_ERR_INVALID_ARG, "stepped must be 0, 1 or 2");
+  if (o.variant < 0 || o.variant > 1) return fail(ctx, MPCG_ERR_INVALID_ARG, "variant must be 0 or 1");
+  if (o.variant == 1 && o.precond == 2)
+    return fail(ctx, MPCG_ERR_INVALID_ARG, "the single-reduction iteration runs with precond 0 or 1");
   for (int a = 0; a < o.nprec; ++a)
     if (!valid_fmt(o.precs[a])) return fail(ctx, MPCG_ERR_INVALID_ARG, "precs[%d] = %d is not a format code", a, o.precs[a]);
   if (o.unvisited_fallback != -1 && !valid_fmt(o.unvisited_fallback))
@@ -225,6 +228,7 @@ mpcg_status build_optview(mpcg_ctx_t ctx, const mpcg_options& o, OptView& v) {
   v.on_breakdown = o.on_breakdown;
   v.precond = o.precond;
   v.edge_tol = o.edge_tol;
+  v.variant = o.variant;
   for (int j = 0; j < 4; ++j) {
     const unsigned all = (1u << o.nprec) - 1u;
     const unsigned m = o.op_mask[j] ? ((unsigned)o.op_mask[j] & all) : all;
@@ -433,7 +437,8 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
   // Work vectors: r, p, q (8 bytes per row each) and p's low-precision copy (4 bytes).
   // IC(0) adds one 64-bit word per row (value and mark of the substitutions).
   size_t wbytes = 0, mbytes = 0;
-  for (int i = 0; i < nsys; ++i) wbytes += 28 * (size_t)in[i].A->dm.n + 4 * 256;
+  const bool sr = ctx->opt.variant == 1;  // single-reduction iteration: u in fp64 possible, and s
+  for (int i = 0; i < nsys; ++i) wbytes += (sr ? 40 : 28) * (size_t)in[i].A->dm.n + 5 * 256;
   for (int i = 0; i < nsys; ++i) mbytes += ic ? 8 * (size_t)in[i].A->dm.n : 0;
   CK(ctx, pl.work.ensure(wbytes));
   pl.icwork_bytes = mbytes;
@@ -466,7 +471,8 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
     d.r = (double*)take(8 * (size_t)n);
     d.p = (double*)take(8 * (size_t)n);
     d.q = take(8 * (size_t)n);
-    d.plow = take(4 * (size_t)n);
+    d.plow = take((sr ? 8 : 4) * (size_t)n);
+    d.sv = sr ? (double*)take(8 * (size_t)n) : nullptr;
     if (ic) {
       d.icw = icw_next;
       icw_next += n;
@@ -499,11 +505,13 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
   CK(ctx, pl.bars.ensure(sizeof(unsigned) * kBarStride * nteams_all));
   // Lockstep batches: every CTA works on a slice of every unfinished system.
   const int bm = ctx->opt.batch_mode;
-  pl.lockstep = force_team == 0 && ((bm == 0 && nsys >= 2) || bm == 2) && nsys >= 1;
+  // the single-reduction iteration runs in the lockstep (or stepped) kernels only
+  if (sr && force_team > 0) return fail(ctx, MPCG_ERR_INVALID_ARG, "the single-reduction iteration runs without teams");
+  pl.lockstep = !stepped && force_team == 0 && ((bm == 0 && nsys >= 2) || bm == 2 || sr) && nsys >= 1;
   pl.stepped = stepped;
   int pgrid = 0;
   if (stepped) {
-    for (int w = 0; w < 4; ++w) {
+    for (int w = 0; w < kPhaseKernels; ++w) {
       pl.sgrid[w] = ctx->nsm * (stream_shape ? ctx->pocc_s[w] : ctx->pocc[w]);
       pgrid = std::max(pgrid, pl.sgrid[w]);
     }
@@ -688,7 +696,7 @@ void mpcg_options_default(mpcg_options* o) {
   o->precond = 0;
   o->edge_tol = 5e-3;
   o->stepped = 0;
-  o->reserved_opt = 0;
+  o->variant = 0;
 }
 
 mpcg_status mpcg_create(mpcg_ctx_t* out, int device, const mpcg_options* opt) {
@@ -717,7 +725,7 @@ mpcg_status mpcg_create(mpcg_ctx_t* out, int device, const mpcg_options* opt) {
     return MPCG_ERR_CUDA;
   if (mlp_set_smem_limit(mlp_grad_smem(kMaxHidden, MPCG_MAX_PREC)) != cudaSuccess) return MPCG_ERR_CUDA;
   if (stepped_set_smem_limit(2 * (size_t)kStageBytes) != cudaSuccess) return MPCG_ERR_CUDA;
-  for (int w = 0; w < 4; ++w) {
+  for (int w = 0; w < kPhaseKernels; ++w) {
     if (stepped_occupancy(w, &c->pocc[w], 0) != cudaSuccess || c->pocc[w] < 1) return MPCG_ERR_CUDA;
     if (stepped_occupancy(w, &c->pocc_s[w], 2 * (size_t)kStageBytes) != cudaSuccess || c->pocc_s[w] < 1)
       return MPCG_ERR_CUDA;
@@ -1744,6 +1752,8 @@ mpcg_status mpcg_solve_noalloc(mpcg_ctx_t ctx, mpcg_matrix_t A, const double* b,
     return fail(ctx, MPCG_ERR_INVALID_ARG, "Jacobi preconditioning needs a positive diagonal entry in every row");
   if (ctx->opt.precond == 2)
     return fail(ctx, MPCG_ERR_INVALID_ARG, "the no-allocation solve does not run the incomplete Cholesky preconditioner");
+  if (ctx->opt.variant != 0)
+    return fail(ctx, MPCG_ERR_INVALID_ARG, "the no-allocation solve runs the CG of Section 3 only (variant 0)");
   if (!(tol >= 0.0) || max_iter < 0) return fail(ctx, MPCG_ERR_INVALID_ARG, "tol must be >= 0 and max_iter >= 0");
   if (A->ctx != ctx || policy->ctx != ctx) return fail(ctx, MPCG_ERR_INVALID_ARG, "objects belong to another context");
   cudaError_t ce = cudaSetDevice(ctx->device);

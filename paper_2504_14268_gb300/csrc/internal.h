@@ -15,7 +15,7 @@ namespace mpcg {
 constexpr int kThreads = 256;       // threads per CTA of every kernel
 constexpr int kMaxRBins = 32;       // residual bins supported by the device policy
 constexpr int kMaxBBins = 64;       // iteration bins
-constexpr int kNSlot = 4;           // partial sums per CTA and phase
+constexpr int kNSlot = 8;           // partial sums per CTA and phase
 constexpr int kNFeat = 16;          // MLP input features
 constexpr int kMaxHidden = 128;     // MLP hidden width bound
 constexpr int kBarStride = 32;      // uint32 words between team barriers (128 bytes)
@@ -81,6 +81,8 @@ struct DevSys {
   float* feat_log;          // when set: the 16 features of every visited state, [k][16]
   unsigned long long* icw;  // IC(0): the substitutions' work vector [n], per row the fp32 value
                             // (y_i, then w_i = (M^-1 r)_i) in the low word and its mark above
+  double* sv;               // single-reduction iteration: s = A p by recurrence (nullptr otherwise);
+                            // plow then holds u = fl_p2(M^-1 r) in the product's format, fp64 included
 };
 
 // Per-system state that persists across phases; written only by the CTA that arrives
@@ -103,6 +105,9 @@ struct SysState {
   unsigned long long t_last;  // globaltimer at the previous team barrier
   unsigned ns_a, ns_b;        // phase times of the current iteration
   int near_edge, pad_ne;      // greedy tabular decisions taken near a residual-bin edge
+  double sr_gamma, sr_alpha;  // single-reduction iteration: gamma and alpha of the last iteration
+  int restart_sr;             // single-reduction iteration: 1 = the next iteration restarts (beta = 0)
+  int wfmt;                   // single-reduction iteration: product format of the finished iteration
   long long counts[4][8];
 };
 
@@ -134,6 +139,8 @@ struct OptView {
   int on_breakdown, precond;
   int op_mask[4];           // allowed action indices per operation (all bits set = no restriction)
   double edge_tol;          // relative distance to a residual-bin threshold counted as near an edge
+  int variant;              // 0: the CG of Section 3; 1: the single-reduction iteration
+  int pad_v;
 };
 
 // Arguments of one launch of the persistent kernel.
@@ -189,11 +196,14 @@ enum DevErr : unsigned { DERR_NONE = 0, DERR_TIMEOUT = 1, DERR_BAD_STATE = 2 };
 cudaError_t launch_cg(const Launch& L, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_cg_lockstep(const Launch& L, int grid, size_t smem, cudaStream_t s);
 // Stepped single solve (stepped.cu): kernels 0..3 are the product, residual, direction and
-// other-phases kernels; the graph repeats them (grids[w] CTAs each, smem bytes of dynamic
-// shared memory for kernels 0 and 3) until the system is done or `limit` passes ran.
+// other-phases kernels, 4 and 5 the single-reduction iteration's product and update kernels;
+// the graph repeats them (grids[w] CTAs each, smem bytes of dynamic shared memory for the
+// product kernels and kernel 3) until the system is done or `limit` passes ran.
+constexpr int kPhaseKernels = 6;
 cudaError_t stepped_occupancy(int which, int* blocks_per_sm, size_t smem);
 cudaError_t stepped_set_smem_limit(size_t bytes);
-cudaError_t stepped_graph(const Launch& L, const int grids[4], size_t smem, unsigned limit, cudaGraph_t* out);
+cudaError_t stepped_graph(const Launch& L, const int grids[kPhaseKernels], size_t smem, unsigned limit,
+                          cudaGraph_t* out);
 // the IC(0) instantiations (cg_kernel_ic.cu)
 cudaError_t launch_cg_ic(const Launch& L, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_cg_lockstep_ic(const Launch& L, int grid, size_t smem, cudaStream_t s);

@@ -42,11 +42,13 @@ struct Bcast {
   int k, mode;
   int fmt[4];
   int zfmt;
+  int wfmt;       // single-reduction iteration: product format of the finished iteration
   unsigned icep;  // epoch of the IC(0) application in this phase
 };
 
 struct Smem {
   double red[2 * (kThreads / 32)];
+  double tmp;  // a scalar handed from thread 0 to the CTA
   Bcast bc;
   int last;
   int ok;
@@ -187,6 +189,7 @@ __device__ __forceinline__ void load_bcast(const SysState* st, Smem& sm) {
     sm.bc.k = v->k;
     sm.bc.mode = v->mode;
     sm.bc.zfmt = v->zfmt;
+    sm.bc.wfmt = v->wfmt;
     sm.bc.icep = v->icep;
 #pragma unroll
     for (int j = 0; j < 4; ++j) sm.bc.fmt[j] = v->fmt[j];
@@ -738,6 +741,132 @@ __device__ void continue_step(const Launch& L, const DevSys& S, SysState* st, do
   }
 }
 
+// Single-reduction iteration: continues after the residual norm of iteration k's end is known
+// (from the recurrence, or recomputed when `replaced`): record, reward, transition, next state
+// and action. gamma and alpha of iteration k become the recurrence's previous values; a
+// replaced residual restarts the recurrence (beta = 0 next).
+__device__ void continue_sr(const Launch& L, const DevSys& S, SysState* st, double rho_new, int replaced, Smem& sm) {
+  if (threadIdx.x == 0) {
+    sm.need_action = 0;
+    const int k = st->k;
+    const int s_next = state_of(L.opt, k + 1, rho_new);
+    const double R = !L.train ? 0.0 : reward_of(L.opt, rho_new, st->act, S.tol, false);
+    write_record(S, st, replaced ? 4 : 0, rho_new, st->sigma, st->beta, L.train ? R : 0.0);
+    push_transition(L, S, st, s_next, R, 0);
+    for (int h = 8; h > 0; --h) st->rho_hist[h] = st->rho_hist[h - 1];
+    st->rho_hist[0] = rho_new;
+    st->alpha_prev = st->alpha;
+    st->beta_prev = st->beta;
+    st->have_prev = 1;
+    for (int j = 0; j < 4; ++j) st->prev_act[j] = st->act[j] >= 0 ? st->act[j] : 0;
+    st->sr_gamma = st->sigma;
+    st->sr_alpha = st->alpha;
+    st->restart_sr = replaced;
+    st->rho = rho_new;
+    st->k = k + 1;
+    st->mode = replaced ? M_RESTART : M_CONT;
+    if (k + 1 >= S.max_iter) {
+      st->outcome = MPCG_MAX_ITER;
+      st->iters = S.max_iter;
+      if (S.feat_log && k + 1 < S.feat_cap) {
+        mlp_features(L, S, st, k + 1, sm);
+        for (int j = 0; j < kNFeat; ++j) S.feat_log[(long long)(k + 1) * kNFeat + j] = sm.feat[j];
+      }
+    } else {
+      sm.need_action = 1;
+    }
+  }
+  __syncthreads();
+  if (sm.need_action) {
+    choose_action(L, S, st, st->k, st->rho, sm);
+    if (threadIdx.x == 0) adopt_action(st, sm);
+  }
+}
+
+// After the single-reduction product phase W: gamma = fl_p4(sum), delta = fl_p3(sum), then in
+// fp64 beta = gamma / gamma_prev, nu = delta - beta gamma / alpha_prev (beta = 0, nu = delta
+// at a restart), alpha = gamma / nu; breakdown tests as after phase A; the next residual norm
+// rr - 2 alpha (r.w + beta r.s) + alpha^2 (w.w + 2 beta w.s + beta^2 s.s) (clamped at 0) and the
+// stopping tests as after phase B. dots = r.r, r.w, r.s, w.w, w.s, s.s (fp64 sums).
+__device__ void step_W(const Launch& L, const DevSys& S, SysState* st, double gsum, double dsum, const double* dots,
+                       Smem& sm) {
+  if (threadIdx.x == 0) {
+    st->ns_a = stamp(st);
+    st->ns_b = 0;
+    sm.flag = 0;
+    const OptView& o = L.opt;
+    const int k = st->k;
+    const int p3 = st->fmt[2], p4 = st->fmt[3];
+    const double gamma = (p4 == F64) ? gsum : round_fmt(gsum, p4);
+    const double delta = (p3 == F64) ? dsum : round_fmt(dsum, p3);
+    const bool rs = st->restart_sr != 0;
+    const double beta = rs ? 0.0 : gamma / st->sr_gamma;
+    const double nu = rs ? delta : delta - beta * gamma / st->sr_alpha;
+    const double alpha = gamma / nu;
+    st->nu = nu;
+    st->alpha = alpha;
+    st->beta = beta;
+    st->sigma = gamma;
+    st->wfmt = st->fmt[0];
+    st->zfmt = st->fmt[1];
+    if (!(nu > 0.0) || !isfinite(nu) || !isfinite(alpha) || !isfinite(beta)) {
+      if (st->rho < S.tol && isfinite(nu)) {
+        st->outcome = MPCG_CONVERGED;
+        const double R = !L.train ? 0.0 : reward_of(o, st->rho, st->act, S.tol, false);
+        write_record(S, st, 1, st->rho, gamma, beta, L.train ? R : 0.0);
+        push_transition(L, S, st, st->s_cur, R, 1);
+        st->iters = k;
+        st->mode = M_DONE;
+      } else if (restart_ok(L, st)) {
+        write_record(S, st, 2 | 16, st->rho, gamma, beta, 0.0);
+        st->mode = M_RESTART64;
+      } else {
+        st->outcome = MPCG_BREAKDOWN;
+        const double R = !L.train ? 0.0 : reward_of(o, st->rho, st->act, S.tol, true);
+        write_record(S, st, 2, st->rho, gamma, beta, L.train ? R : 0.0);
+        push_transition(L, S, st, st->s_cur, R, 1);
+        st->iters = k;
+        st->mode = M_DONE;
+      }
+    } else {
+      double rr = dots[0] - 2.0 * alpha * (dots[1] + beta * dots[2]) +
+                  alpha * alpha * (dots[3] + 2.0 * beta * dots[4] + beta * beta * dots[5]);
+      if (rr < 0.0) rr = 0.0;
+      const double rho_rec = sqrt(rr) / st->bnorm;
+      const bool check = (o.true_every > 0 && (k + 1) % o.true_every == 0) ||
+                         (o.true_at_conv && rho_rec < S.tol && k >= o.min_k);
+      if (check && isfinite(rho_rec)) {
+        st->rho_true = rho_rec;
+        st->mode = M_TCHK;
+      } else if (!isfinite(rho_rec) && restart_ok(L, st)) {
+        write_record(S, st, 2 | 16, rho_rec, gamma, beta, 0.0);
+        st->mode = M_X_THEN_RESTART64;
+      } else if (!isfinite(rho_rec)) {
+        st->outcome = MPCG_BREAKDOWN;
+        st->iters = k + 1;
+        const double R = !L.train ? 0.0 : reward_of(o, rho_rec, st->act, S.tol, true);
+        write_record(S, st, 2, rho_rec, gamma, beta, L.train ? R : 0.0);
+        push_transition(L, S, st, st->s_cur, R, 1);
+        st->rho = rho_rec;
+        st->mode = M_X_THEN_DONE;
+      } else if (rho_rec < S.tol && k >= o.min_k) {
+        st->outcome = MPCG_CONVERGED;
+        st->iters = k + 1;
+        const double R = !L.train ? 0.0 : reward_of(o, rho_rec, st->act, S.tol, false);
+        write_record(S, st, 1, rho_rec, gamma, beta, L.train ? R : 0.0);
+        push_transition(L, S, st, st->s_cur, R, 1);
+        st->rho = rho_rec;
+        st->mode = M_X_THEN_DONE;
+      } else {
+        sm.flag = 1;
+        sm.tmp = rho_rec;
+      }
+    }
+  }
+  __syncthreads();
+  if (sm.flag) continue_sr(L, S, st, sm.tmp, 0, sm);
+}
+
 // After phase B: rho_{k+1} of the recursive residual, stopping tests.
 __device__ void step_B(const Launch& L, const DevSys& S, SysState* st, double rr, double sig_sum, Smem& sm) {
   if (threadIdx.x == 0) {
@@ -816,7 +945,10 @@ __device__ void step_T(const Launch& L, const DevSys& S, SysState* st, double rr
     }
   }
   __syncthreads();
-  if (sm.flag) continue_step(L, S, st, sqrt(rr) / st->bnorm, sig_sum, 1, sm);
+  if (sm.flag) {
+    if (L.opt.variant) continue_sr(L, S, st, sqrt(rr) / st->bnorm, 1, sm);
+    else continue_step(L, S, st, sqrt(rr) / st->bnorm, sig_sum, 1, sm);
+  }
 }
 
 // After the fp64 restart's residual recomputation (r = b - A x, p = r): iteration k counts
@@ -829,6 +961,7 @@ __device__ void step_restart(const Launch& L, const DevSys& S, SysState* st, dou
     st->fp64_lock = 1;
     st->n_restart += 1;
     st->n_true += 1;
+    st->restart_sr = 1;  // the single-reduction recurrence restarts with beta = 0
     st->sigma = sig;
     st->beta = 0.0;
     st->rho = rho;
@@ -1381,6 +1514,68 @@ __device__ __forceinline__ bool solve_system(const Launch& L, const TeamCtx& T, 
 }
 
 // ----------------------------------------------------------------------------------------
+// Single-reduction iteration: row work of its phases
+// ----------------------------------------------------------------------------------------
+
+// u_i in the product format p1 (fp64 included) in plow, the product's input.
+__device__ __forceinline__ void store_u(const DevSys& S, int i, double u, int p1) {
+  if (p1 == F64) ((double*)S.plow)[i] = u;
+  else store_low(S.plow, i, u, p1);
+}
+
+// Phase UL: u = fl_p2(M^-1 r) in the product format, from the current r (after the
+// initialisation, a residual replacement or the fp64 restart).
+__device__ __noinline__ void sr_ul_rows(const DevSys& S, Rows R, int p1, int p2) {
+  for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) store_u(S, i, z_of(minv_r(S, i, S.r[i]), p2), p1);
+}
+
+// Partial sums of phase W over the CTA's rows, after the product w = fl_p1(A u) is stored:
+// gamma = sum fl_p4(r_i) fl_p4(u_i) and delta = sum fl_p3(w_i) fl_p3(u_i) (compensated fp32, or
+// fp64 for fp64), and the fp64 sums r.r, r.w, r.s, w.w, w.s, s.s of the norm recurrence.
+struct SrSums {
+  DotAcc g, d;
+  double rr, rw, rs, ww, ws, ss;
+};
+__device__ __noinline__ void sr_w_tail(const DevSys& S, Rows R, int p1, int p2, int p3, int p4, SrSums& a) {
+  for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
+    const double ri = S.r[i];
+    const double wi = load_q(S, i, p1);
+    const double si = S.sv[i];
+    const double mi = minv_r(S, i, ri);
+    const double ui = z_of(mi, p2);
+    sigma_term(ri, mi, p2, p4, a.g);
+    if (p3 == F64) a.d.d = fma(wi, ui, a.d.d);
+    else dot_low(a.d, round_d2f(wi, p3), round_d2f(ui, p3), p3);
+    a.rr = fma(ri, ri, a.rr);
+    a.rw = fma(ri, wi, a.rw);
+    a.rs = fma(ri, si, a.rs);
+    a.ww = fma(wi, wi, a.ww);
+    a.ws = fma(wi, si, a.ws);
+    a.ss = fma(si, si, a.ss);
+  }
+}
+
+// Phase U: p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s (fp64) with u = fl_p2(M^-1 r)
+// and w (stored in format p1w) of the finished iteration; with `next`, the next iteration's u
+// in its product format (p1n, p2n) from the new r.
+__device__ __noinline__ void sr_u_rows(const DevSys& S, Rows R, double alpha, double beta, int p2, int p1w, bool next,
+                                       int p1n, int p2n) {
+  for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
+    const double ri = S.r[i];
+    const double ui = z_of(minv_r(S, i, ri), p2);
+    const double wi = load_q(S, i, p1w);
+    const double pn = fma(beta, S.p[i], ui);
+    const double sn = fma(beta, S.sv[i], wi);
+    S.p[i] = pn;
+    S.sv[i] = sn;
+    S.x[i] = fma(alpha, pn, S.x[i]);
+    const double rn = fma(-alpha, sn, ri);
+    S.r[i] = rn;
+    if (next) store_u(S, i, z_of(minv_r(S, i, rn), p2n), p1n);
+  }
+}
+
+// ----------------------------------------------------------------------------------------
 // Lockstep batches: all CTAs work on all active systems at every super-step
 // ----------------------------------------------------------------------------------------
 // Each system runs the same sequence of phases as solve_system, as a state machine: at a
@@ -1392,7 +1587,10 @@ __device__ __forceinline__ bool solve_system(const Launch& L, const TeamCtx& T, 
 // rows located by bisection on rp[r] + 3 r) and re-cut whenever a system finishes, so the
 // whole GPU keeps working on whatever systems are left.
 
-enum LkPhase : int { PH_INIT = 0, PH_PLOW, PH_A, PH_B, PH_C, PH_X, PH_T, PH_RZ, PH_R64, PH_FINAL, PH_DONE };
+// PH_W, PH_U, PH_UL: the single-reduction iteration's product-and-reduction phase, its update
+// phase, and the write of u's product-format copy after an initialisation or a restart.
+enum LkPhase : int { PH_INIT = 0, PH_PLOW, PH_A, PH_B, PH_C, PH_X, PH_T, PH_RZ, PH_R64, PH_FINAL, PH_DONE,
+                     PH_W, PH_U, PH_UL };
 
 __device__ __forceinline__ bool grid_sync(const Launch& L, const TeamCtx& G, Smem& sm) {
   if (team_arrive(G, sm)) {
@@ -1514,6 +1712,29 @@ __device__ __forceinline__ void lk_partial(const Launch& L, int slot, int k, dou
   if (threadIdx.x == 0) L.partials[(long long)slot * kNSlot + k] = v;
 }
 
+// Phase W row work: the product of u (no nu partial) and the iteration's partial sums (slots
+// 0..7: gamma, delta, r.r, r.w, r.s, w.w, w.s, s.s).
+__device__ __forceinline__ void sr_w_rows(const Launch& L, const DevSys& S, Rows R, int slot, Smem& sm,
+                                          const StreamCtx* sc) {
+  DotAcc none{0.0, 0.f, 0.f};
+  spmv_rows(S, R, sm.bc.fmt[0], -1, none, sc);
+  SrSums a{{0.0, 0.f, 0.f}, {0.0, 0.f, 0.f}, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  sr_w_tail(S, R, sm.bc.fmt[0], sm.bc.fmt[1], sm.bc.fmt[2], sm.bc.fmt[3], a);
+  lk_partial(L, slot, 0, cta_dot(a.g, sm.red));
+  lk_partial(L, slot, 1, cta_dot(a.d, sm.red));
+  lk_partial(L, slot, 2, cta_sum(a.rr, sm.red));
+  lk_partial(L, slot, 3, cta_sum(a.rw, sm.red));
+  lk_partial(L, slot, 4, cta_sum(a.rs, sm.red));
+  lk_partial(L, slot, 5, cta_sum(a.ww, sm.red));
+  lk_partial(L, slot, 6, cta_sum(a.ws, sm.red));
+  lk_partial(L, slot, 7, cta_sum(a.ss, sm.red));
+}
+
+// Phase U row work (updates; the next u's copy when the iteration continues normally).
+__device__ __forceinline__ void sr_u_phase(const DevSys& S, Rows R, Smem& sm) {
+  sr_u_rows(S, R, sm.bc.alpha, sm.bc.beta, sm.bc.zfmt, sm.bc.wfmt, sm.bc.mode == M_CONT, sm.bc.fmt[0], sm.bc.fmt[1]);
+}
+
 // Row work of one slice in the current phase of its system. ONLY >= 0 compiles the code of
 // that phase alone (the per-phase kernels of the stepped solve; the caller has checked the
 // phase), ONLY < 0 every phase behind a run-time switch.
@@ -1547,6 +1768,12 @@ __device__ void lk_slice_rows(const Launch& L, int s, Rows R, int slot, Smem& sm
   } else if constexpr (ONLY == PH_C) {
     phase_c(S, R, sm.bc.alpha, sm.bc.beta, sm.bc.zfmt, sm.bc.fmt[0]);
     return;
+  } else if constexpr (ONLY == PH_W) {
+    sr_w_rows(L, S, R, slot, sm, sc);
+    return;
+  } else if constexpr (ONLY == PH_U) {
+    sr_u_phase(S, R, sm);
+    return;
   }
   const int phase = sm.lk_phase;
   switch (phase) {
@@ -1555,21 +1782,23 @@ __device__ void lk_slice_rows(const Launch& L, int s, Rows R, int slot, Smem& sm
       DotAcc sg{0.0, 0.f, 0.f};
       const bool warm = L.opt.warm_start != 0;
       const bool ic = IC && S.icw != nullptr;
+      const bool sr = S.sv != nullptr;  // single-reduction iteration: p = s = 0, no sigma_0
       for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) {
         const double bi = __ldg(S.b + i);
         bb = fma(bi, bi, bb);
+        if (sr) S.p[i] = S.sv[i] = 0.0;
         if (!warm) {
           S.x[i] = 0.0;
           S.r[i] = bi;
           rr = fma(bi, bi, rr);
-          if (!ic) {
+          if (!ic && !sr) {
             const double wi = minv_r(S, i, bi);
             S.p[i] = wi;
             sg.d = fma(bi, wi, sg.d);
           }
         }
       }
-      if (warm) true_res_rows<IC>(L, S, R, -1, -1, true, rr, sg, sm.bc.icep);
+      if (warm) true_res_rows<IC>(L, S, R, -1, -1, !sr, rr, sg, sm.bc.icep);
       else if (ic)
         ic_phase(L, S, R, sm.bc.icep, -1, -1, true, sg);
       bb = cta_sum(bb, sm.red);
@@ -1636,7 +1865,10 @@ __device__ void lk_slice_rows(const Launch& L, int s, Rows R, int slot, Smem& sm
     case PH_R64: {
       double rr = 0.0;
       DotAcc sg{0.0, 0.f, 0.f};
-      true_res_rows<IC>(L, S, R, -1, -1, true, rr, sg, sm.bc.icep);
+      const bool sr = S.sv != nullptr;  // single-reduction iteration: the recurrence restarts from 0
+      true_res_rows<IC>(L, S, R, -1, -1, !sr, rr, sg, sm.bc.icep);
+      if (sr)
+        for (int i = R.r0 + threadIdx.x; i < R.r1; i += kThreads) S.p[i] = S.sv[i] = 0.0;
       rr = cta_sum(rr, sm.red);
       const double sp = cta_dot(sg, sm.red);
       lk_partial(L, slot, 0, rr);
@@ -1650,6 +1882,15 @@ __device__ void lk_slice_rows(const Launch& L, int s, Rows R, int slot, Smem& sm
       lk_partial(L, slot, 0, cta_sum(rr, sm.red));
       break;
     }
+    case PH_UL:
+      sr_ul_rows(S, R, sm.bc.fmt[0], sm.bc.fmt[1]);
+      break;
+    case PH_W:
+      sr_w_rows(L, S, R, slot, sm, sc);
+      break;
+    case PH_U:
+      sr_u_phase(S, R, sm);
+      break;
     default:
       break;
   }
@@ -1679,8 +1920,13 @@ __device__ void lk_step_slots(const Launch& L, int s, int base, int np, Smem& sm
   } else if constexpr (ONLY == PH_B) {
     const double trr = lk_sum(L, base, np, 0, sm), tsg = lk_sum(L, base, np, 1, sm);
     step_B(L, S, st, trr, tsg, sm);
-  } else if constexpr (ONLY == PH_C) {
+  } else if constexpr (ONLY == PH_C || ONLY == PH_U) {
     stamp_c(S, st);
+  } else if constexpr (ONLY == PH_W) {
+    double d[6];
+    const double g = lk_sum(L, base, np, 0, sm), dl = lk_sum(L, base, np, 1, sm);
+    for (int q = 0; q < 6; ++q) d[q] = lk_sum(L, base, np, 2 + q, sm);
+    step_W(L, S, st, g, dl, d, sm);
   } else {
   switch (phase) {
     case PH_INIT: {
@@ -1707,7 +1953,15 @@ __device__ void lk_step_slots(const Launch& L, int s, int base, int np, Smem& sm
       break;
     }
     case PH_FINAL: step_final(L, S, st, s, lk_sum(L, base, np, 0, sm)); break;
-    default: break;  // PH_PLOW, PH_X, PH_RZ: no scalar work
+    case PH_W: {
+      double d[6];
+      const double g = lk_sum(L, base, np, 0, sm), dl = lk_sum(L, base, np, 1, sm);
+      for (int q = 0; q < 6; ++q) d[q] = lk_sum(L, base, np, 2 + q, sm);
+      step_W(L, S, st, g, dl, d, sm);
+      break;
+    }
+    case PH_U: stamp_c(S, st); break;
+    default: break;  // PH_PLOW, PH_X, PH_RZ, PH_UL: no scalar work
   }
   }
   __syncthreads();
@@ -1715,16 +1969,29 @@ __device__ void lk_step_slots(const Launch& L, int s, int base, int np, Smem& sm
     const volatile SysState* v = st;
     const int mode = v->mode;
     int next = PH_FINAL;
+    const bool sr = S.sv != nullptr;
     switch (phase) {
-      case PH_INIT: next = mode == M_CONT ? (v->fmt[0] != F64 ? PH_PLOW : PH_A) : PH_FINAL; break;
+      case PH_INIT: next = mode == M_CONT ? (sr ? PH_UL : v->fmt[0] != F64 ? PH_PLOW : PH_A) : PH_FINAL; break;
+      case PH_UL: next = PH_W; break;
+      case PH_W: next = mode == M_RESTART64 ? PH_R64 : mode == M_DONE ? PH_FINAL : PH_U; break;
+      case PH_U:
+        next = mode == M_CONT ? (v->k >= S.max_iter ? PH_FINAL : PH_W)
+               : mode == M_TCHK ? PH_T
+               : mode == M_X_THEN_RESTART64 ? PH_R64
+                                            : PH_FINAL;
+        break;
       case PH_PLOW: next = PH_A; break;
       case PH_A: next = mode == M_RESTART64 ? PH_R64 : mode == M_CONT ? PH_B : PH_FINAL; break;
       case PH_B: next = mode == M_CONT ? PH_C : mode == M_DONE ? PH_FINAL : PH_X; break;
       case PH_C: next = v->k >= S.max_iter ? PH_FINAL : PH_A; break;
       case PH_X: next = mode == M_X_THEN_DONE ? PH_FINAL : mode == M_X_THEN_RESTART64 ? PH_R64 : PH_T; break;
-      case PH_T: next = mode == M_RESTART64 ? PH_R64 : mode == M_RESTART ? PH_RZ : PH_FINAL; break;
+      case PH_T:
+        next = mode == M_RESTART64 ? PH_R64
+               : mode == M_RESTART ? (sr ? (v->k >= S.max_iter ? PH_FINAL : PH_UL) : PH_RZ)
+                                   : PH_FINAL;
+        break;
       case PH_RZ: next = v->k >= S.max_iter ? PH_FINAL : PH_A; break;
-      case PH_R64: next = mode == M_CONT ? PH_A : PH_FINAL; break;
+      case PH_R64: next = mode == M_CONT ? (sr ? PH_UL : PH_A) : PH_FINAL; break;
       default: next = PH_DONE; break;  // PH_FINAL
     }
     st->phase = next;

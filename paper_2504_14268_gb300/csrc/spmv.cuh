@@ -398,15 +398,16 @@ __device__ __forceinline__ double lane_of<double>(const int4& q, int k) {
 }
 
 // One thread per row with 16-byte loads: the row's column indices and values are read in
-// aligned groups of G elements (G = 16 for 8-bit values, 8 for 16-bit, 4 otherwise; group starts rounded
+// aligned groups of G elements (G = 8 for 8- and 16-bit values, the 8-bit ones in one 8-byte
+// load; 4 otherwise; group starts rounded
 // down to a multiple of G, the arrays are padded so the last group stays in bounds), so a
 // thread issues one load per 4 columns and per 16 bytes of values instead of one per
 // element; elements of a group outside the row are skipped. Long rows go to the CTA queue.
 template <typename VT, bool COMP>
 __device__ void spmv_vload(const DevSys& S, const VT* __restrict__ vals, const VT* xin, Rows R, int p1, int nu_fmt,
                            DotAcc& nu) {
-  constexpr int G = sizeof(VT) == 1 ? 16 : sizeof(VT) == 2 ? 8 : 4;
-  constexpr int NV = G * (int)sizeof(VT) / 16;  // 16-byte value loads per group
+  constexpr int G = sizeof(VT) <= 2 ? 8 : 4;
+  constexpr int NV = G * (int)sizeof(VT) / 16;  // 16-byte value loads per group (0: one 8-byte load)
   const int* __restrict__ rp = S.A.rp;
   const int* __restrict__ ci = S.A.ci;
   // the row pointers and p_i of a thread's next row are loaded one row ahead
@@ -440,6 +441,12 @@ __device__ void spmv_vload(const DevSys& S, const VT* __restrict__ vals, const V
         c[4 * h + 1] = cc.y;
         c[4 * h + 2] = cc.z;
         c[4 * h + 3] = cc.w;
+      }
+      if constexpr (NV == 0) {  // eight one-byte values
+        const int2 v2 = __ldg(reinterpret_cast<const int2*>(vals + g));
+        const int4 vv = make_int4(v2.x, v2.y, 0, 0);
+#pragma unroll
+        for (int k = 0; k < G; ++k) v[k] = lane_of<VT>(vv, k);
       }
 #pragma unroll
       for (int h = 0; h < NV; ++h) {
@@ -555,7 +562,9 @@ __device__ void spmv_dispatch_k(const DevSys& S, const VT* vals, const VT* xin, 
 // shared-memory ring of the stream schedule (nullptr when the launch has none).
 __device__ void spmv_rows(const DevSys& S, Rows R, int p1, int nu_fmt, DotAcc& nu, const StreamCtx* sc) {
   switch (p1) {
-    case F64: spmv_dispatch_k<double, false>(S, S.A.v64, S.p, R, p1, nu_fmt, nu, sc); break;
+    case F64:  // the single-reduction iteration multiplies u, kept in plow in fp64
+      spmv_dispatch_k<double, false>(S, S.A.v64, S.sv ? (const double*)S.plow : S.p, R, p1, nu_fmt, nu, sc);
+      break;
     case F32: spmv_dispatch_k<float, false>(S, S.A.v32, (const float*)S.plow, R, p1, nu_fmt, nu, sc); break;
     case TF32: spmv_dispatch_k<float, true>(S, S.A.vtf, (const float*)S.plow, R, p1, nu_fmt, nu, sc); break;
     case F16: spmv_dispatch_k<__half, true>(S, S.A.v16, (const __half*)S.plow, R, p1, nu_fmt, nu, sc); break;

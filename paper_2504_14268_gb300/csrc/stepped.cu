@@ -45,18 +45,21 @@ template <int PH>
 __device__ __forceinline__ int stepped_row(const DevSys& S, int c, int G) {
   if (c <= 0) return 0;
   if (c >= G) return S.A.n;
-  if constexpr (PH == PH_A) {
+  if constexpr (PH == PH_A || PH == PH_W) {
     return part_row(S.A.rp, S.A.n, S.A.nnz, c, G);
-  } else if constexpr (PH == PH_B || PH == PH_C) {
+  } else if constexpr (PH == PH_B || PH == PH_C || PH == PH_U) {
     return (int)(((long long)S.A.n * c) / G);
   } else {
     return lk_row_at(S, ((S.A.nnz + 3LL * S.A.n) * c) / G);
   }
 }
 
-// PH = PH_A, PH_B or PH_C: that phase alone; PH = -1: any other phase.
+// PH = PH_A, PH_B, PH_C (or PH_W, PH_U of the single-reduction iteration): that phase alone;
+// PH = -1: any other phase.
+// At least four CTAs per SM (at most 64 registers): the phase kernels stream HBM, and the
+// loads in flight per SM come from resident threads.
 template <int PH>
-__global__ void __launch_bounds__(kThreads) cg_phase(const Launch L) {
+__global__ void __launch_bounds__(kThreads, 4) cg_phase(const Launch L) {
   __shared__ Smem sm;
   extern __shared__ __align__(128) unsigned char dyn[];
   if (threadIdx.x == 0) {
@@ -65,9 +68,10 @@ __global__ void __launch_bounds__(kThreads) cg_phase(const Launch L) {
   }
   __syncthreads();
   const int ph = sm.lk_phase;
-  const bool mine = PH >= 0 ? ph == PH : (ph != PH_A && ph != PH_B && ph != PH_C && ph != PH_DONE);
+  const bool mine = PH >= 0 ? ph == PH
+                            : (ph != PH_A && ph != PH_B && ph != PH_C && ph != PH_W && ph != PH_U && ph != PH_DONE);
   if (!mine || !sm.ok) return;
-  const bool ring = L.stream_stage > 0 && (PH == PH_A || PH < 0);
+  const bool ring = L.stream_stage > 0 && (PH == PH_A || PH == PH_W || PH < 0);
   StreamCtx scx{dyn, sm.mbar, &sm.mbar_phase, L.err, L.stream_stage};
   if (ring) {
     if (threadIdx.x == 0) {
@@ -108,6 +112,8 @@ const void* phase_kernel(int which) {
     case 0: return (const void*)cg_phase<PH_A>;
     case 1: return (const void*)cg_phase<PH_B>;
     case 2: return (const void*)cg_phase<PH_C>;
+    case 4: return (const void*)cg_phase<PH_W>;
+    case 5: return (const void*)cg_phase<PH_U>;
     default: return (const void*)cg_phase<-1>;
   }
 }
@@ -119,17 +125,18 @@ cudaError_t stepped_occupancy(int which, int* blocks_per_sm, size_t smem) {
 }
 
 cudaError_t stepped_set_smem_limit(size_t bytes) {
-  for (int w = 0; w < 4; ++w) {
+  for (int w = 0; w < 6; ++w) {
     const cudaError_t e = cudaFuncSetAttribute(phase_kernel(w), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-// The graph of one stepped solve: a while-loop node whose body chains the four phase kernels
-// (grids[0..3], dynamic shared memory smem for the product and the other-phases kernel when
-// the launch uses the stream schedule) and the control kernel.
-cudaError_t stepped_graph(const Launch& L, const int grids[4], size_t smem, unsigned limit, cudaGraph_t* out) {
+// The graph of one stepped solve: a while-loop node whose body chains the phase kernels
+// (kernels 0, 1, 2, 3 for the CG of Section 3, or 4, 5, 3 for the single-reduction iteration;
+// grids[w] CTAs for kernel w, dynamic shared memory smem for the product kernels and the
+// other-phases kernel when the launch uses the stream schedule) and the control kernel.
+cudaError_t stepped_graph(const Launch& L, const int grids[6], size_t smem, unsigned limit, cudaGraph_t* out) {
   *out = nullptr;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaGraphCreate(&g, 0);
@@ -150,13 +157,17 @@ cudaError_t stepped_graph(const Launch& L, const int grids[4], size_t smem, unsi
   Launch Lc = L;
   void* args[] = {(void*)&Lc};
   cudaGraphNode_t prev = nullptr;
-  for (int w = 0; w < 4 && e == cudaSuccess; ++w) {
+  const int std_body[4] = {0, 1, 2, 3}, sr_body[3] = {4, 5, 3};
+  const int* body_k = L.opt.variant ? sr_body : std_body;
+  const int nbody = L.opt.variant ? 3 : 4;
+  for (int i = 0; i < nbody && e == cudaSuccess; ++i) {
+    const int w = body_k[i];
     cudaKernelNodeParams kp;
     memset(&kp, 0, sizeof(kp));
     kp.func = (void*)phase_kernel(w);
     kp.gridDim = dim3(grids[w]);
     kp.blockDim = dim3(kThreads);
-    kp.sharedMemBytes = (w == 0 || w == 3) ? (unsigned)smem : 0u;
+    kp.sharedMemBytes = (w == 0 || w == 3 || w == 4) ? (unsigned)smem : 0u;
     kp.kernelParams = args;
     cudaGraphNode_t nd;
     e = cudaGraphAddKernelNode(&nd, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp);

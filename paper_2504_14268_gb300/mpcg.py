@@ -47,7 +47,7 @@ class COptions(C.Structure):
         ("batch_mode", C.c_int32),
         ("precond", C.c_int32),
         ("edge_tol", C.c_double),
-        ("stepped", C.c_int32), ("reserved_opt", C.c_int32),
+        ("stepped", C.c_int32), ("variant", C.c_int32),
     ]
 
 
@@ -203,7 +203,7 @@ class Options:
     precond: int = 0  # 0: M = I; 1: Jacobi; 2: fp32 IC(0) (factor kept with the matrix)
     edge_tol: float = 5e-3  # greedy decisions this close (relative) to a residual-bin edge are counted
     stepped: int = 0  # single solves: 0 automatic, 1 persistent launch, 2 one kernel per phase in a graph loop
-    reserved_opt: int = 0
+    variant: int = 0  # 0: the CG of Section 3; 1: the single-reduction iteration (lockstep / stepped kernels)
 
     def c(self) -> COptions:
         o = COptions()

@@ -4,6 +4,8 @@ launch configuration the benchmark times (autotuned schedules).
 The oracle cannot run this size end to end, so the product is checked on sampled rows
 (the oracle computes each sampled row of q = fl_p1(A fl_p1(x)) exactly as it would in a
 full product) and the solve through properties that hold at any size."""
+import math
+
 import numpy as np
 import pytest
 
@@ -14,7 +16,51 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 N = 256
-T_BITS = {0: 11, 1: 8, 2: 11, 3: 24, 5: 8, 6: 11}
+T_BITS = {0: 11, 1: 8, 2: 11, 3: 24, 5: 8, 6: 11, 7: 3}
+# (t, e_min, e_max) of the formats whose product output is the correctly rounded row sum
+FMT_TE = {0: (11, -14, 15), 1: (8, -126, 127), 2: (11, -126, 127), 5: (8, -126, 127), 6: (11, -14, 15),
+          7: (3, -14, 15)}
+
+
+def _round_exact(v, t, emin, emax):
+    """The value of the format (t digits, exponents emin..emax, gradual underflow) nearest to
+    the rational v, ties to even (infinity beyond the largest finite value)."""
+    from fractions import Fraction
+
+    if v == 0:
+        return 0.0
+    a = abs(v)
+    e = math.frexp(float(a))[1] - 1  # floor(log2 a), corrected below for the float rounding
+    while Fraction(2) ** e > a:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= a:
+        e += 1
+    e = max(e, emin)
+    q = Fraction(2) ** (e - t + 1)
+    m = a / q
+    k = m.numerator // m.denominator
+    rem = m - k
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and k % 2 == 1):
+        k += 1
+    y = k * q
+    if y > Fraction(2) ** emax * (2 - Fraction(2) ** (1 - t)):
+        return math.copysign(math.inf, float(v))
+    return math.copysign(float(y), float(v))
+
+
+def _exact_row(A, row, fmt, x):
+    """fl_fmt of the exact sum of the row's products of stored values and rounded inputs (the
+    row scale 2^e of the row-scaled formats applied after the rounding)."""
+    from fractions import Fraction
+
+    n, rp, ci, val = A
+    base = {5: 1, 6: 0}.get(fmt, fmt)
+    e0, e1 = rp[row], rp[row + 1]
+    s = O.row_scale(A, row) if fmt in (5, 6) else 1.0
+    vals = O.chop(val[e0:e1] / s, fmt)
+    xs = O.chop(x[ci[e0:e1]], base)
+    tot = sum((Fraction(float(a)) * Fraction(float(b)) for a, b in zip(vals, xs)), Fraction(0))
+    return s * _round_exact(tot, *FMT_TE[fmt])
 
 
 @pytest.fixture(scope="module")
@@ -54,14 +100,21 @@ def _sub_csr(A, rows):
     return (len(rows), srp, ci[idx].astype(np.int32), val[idx])
 
 
-def _check_rows(fmt, y, ref, absref):
+def _check_rows(fmt, y, ref, absref, A=None, rows=None, x=None):
     if fmt == 4:
         assert np.all(np.abs(y - ref) <= 1e-14 * absref + 1e-300)
     elif fmt == 3:
         assert np.all(np.abs(y - ref) <= 64 * 2.0 ** -24 * absref)
     else:
-        # correctly rounded row sums: equal to the oracle's fp64-sum rounding
-        assert np.mean(y == ref) >= 0.9999, (fmt, np.flatnonzero(y != ref)[:5])
+        # correctly rounded row sums: the oracle rounds its fp64 sum of the exact products (the
+        # paper's compute-high-then-round emulation), which can differ from the correctly rounded
+        # exact sum when the fp64 sum itself was rounded next to a midpoint; every row where the
+        # two sides differ must hold the correctly rounded exact sum on the GPU
+        bad = np.flatnonzero(y != ref)
+        assert len(bad) <= max(3, len(y) // 10000), (fmt, len(bad), bad[:5])
+        for i in bad:
+            want = _exact_row(A, int(rows[i]), fmt, x)
+            assert y[i] == want, (fmt, int(rows[i]), y[i], ref[i], want)
         assert np.all(np.abs(y - ref) <= np.abs(ref) * 2.0 ** (1 - T_BITS[fmt]) + 1e-300)
 
 
@@ -86,7 +139,7 @@ def test_fullsize_spmv_sampled_rows(big, sched, lanes):
         ref = _oracle_rows(sub, fmt, x)
         base = fmt if fmt < 5 or fmt == 7 else (1 if fmt == 5 else 0)
         absref = _oracle_rows(absub, 4, np.abs(O.chop(x, base)))
-        _check_rows(fmt, y, ref, absref)
+        _check_rows(fmt, y, ref, absref, A, rows, x)
         mat.set_schedule(fmt, 0, 1)
 
 

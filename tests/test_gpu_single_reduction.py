@@ -1,0 +1,128 @@
+"""The single-reduction iteration (Chronopoulos and Gear's form of CG, option variant = 1) on
+the GPU against the oracle's orc_run_sr, through the C ABI: lockstep batches, a single solve
+in the lockstep kernel and in the stepped graph, residual replacement and the fp64 restart,
+Jacobi, and training rounds.
+
+Tolerances: residual histories within 1e-6 relative on all-fp64 iterations and 5e-3 otherwise
+(over the prefix on which the oracle agrees with a perturbed twin of itself for systems where
+rounding alone moves the history), final error within 10x the oracle's."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2504_14268_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ALL64 = (4, 4, 4, 4)
+TOL64, TOL_LOW = 1e-6, 5e-3
+
+
+@pytest.fixture(scope="module")
+def M():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2504_14268_gb300 import mpcg
+
+    return mpcg
+
+
+def _dev(A):
+    n, rp, ci, val = A
+    return (n, torch.as_tensor(rp).cuda(), torch.as_tensor(ci).cuda(), torch.as_tensor(val).cuda())
+
+
+def _hist_ok(hg, ho, n, fmts):
+    err = np.abs(hg["rho"][:n] - ho["rho"][:n]) / np.abs(ho["rho"][:n])
+    lim = TOL64 if tuple(fmts) == ALL64 else TOL_LOW
+    assert np.all(err <= lim), (float(err.max()), int(np.argmax(err)))
+
+
+@pytest.mark.parametrize("stepped", [1, 2])
+@pytest.mark.parametrize("fmts,tol", [(ALL64, 1e-10), ((3, 3, 3, 3), 1e-6), ((0, 4, 3, 4), 1e-3),
+                                      ((3, 0, 4, 3), 1e-3), ((7, 4, 4, 4), 1e-3)])
+def test_single_reduction_fixed_policy_matches_oracle(M, fmts, tol, stepped):
+    A, b, xs = I.cfg_poisson32()
+    ctx = M.Context(0, M.Options(min_k=0, variant=1, stepped=stepped))
+    mat = ctx.matrix(_dev(A))
+    bd = torch.as_tensor(b).cuda()
+    x = torch.zeros_like(bd)
+    res, hist = ctx.solve(mat, bd, x, tol, 600, ctx.policy_fixed(fmts), history_cap=600)
+    ref = O.solve(O.Options(min_k=0, variant=1), A, b, tol, 600, fixed=fmts)
+    assert res["outcome"] == ref.outcome
+    n = min(res["iters"], ref.iters)
+    _hist_ok(hist, ref.hist, n, fmts)
+    assert abs(res["iters"] - ref.iters) <= max(1, ref.iters // 50)
+    eg = np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs)
+    eo = np.linalg.norm(ref.x - xs) / np.linalg.norm(xs)
+    assert eg <= 10 * eo + 1e-15
+    # the recorded scalars: gamma (op 4) and alpha
+    assert np.allclose(hist["sigma"][:n], ref.hist["sigma"][:n], rtol=TOL_LOW)
+
+
+def test_single_reduction_batch_replacement_restart_and_jacobi(M):
+    """A lockstep batch of diffusion systems with residual replacement at convergence, each
+    system against the oracle; the fp64 restart after a breakdown; Jacobi."""
+    sets = I.cfg_train_set(count=5, m_lo=6, m_hi=10, seed=4)
+    opts = dict(min_k=0, variant=1, true_res_at_conv=1)
+    ctx = M.Context(0, M.Options(**opts))
+    pol = ctx.policy_fixed((3, 4, 3, 4))
+    mats = [ctx.matrix(_dev(A)) for A, _, _ in sets]
+    bs = [torch.as_tensor(b).cuda() for _, b, _ in sets]
+    xs = [torch.zeros_like(b) for b in bs]
+    res = ctx.solve_batched(mats, bs, xs, [1e-8] * 5, [800] * 5, pol)
+    for (A, b, xstar), r, x in zip(sets, res, xs):
+        ref = O.solve(O.Options(**opts), A, b, 1e-8, 800, fixed=(3, 4, 3, 4))
+        assert r["outcome"] == ref.outcome == O.CONVERGED and r["rel_res_true"] < 1e-8
+        assert abs(r["iters"] - ref.iters) <= max(3, ref.iters // 20)
+        assert np.linalg.norm(x.cpu().numpy() - xstar) <= 10 * np.linalg.norm(ref.x - xstar) + 1e-12
+    # breakdown of the fp16 product on values beyond fp16's range, then the fp64 restart
+    A, b, _ = I.cfg_poisson32()
+    big = (A[0], A[1], A[2], A[3] * 1e5)
+    ctx2 = M.Context(0, M.Options(min_k=0, variant=1, on_breakdown=1))
+    x = np.zeros(A[0])
+    r, h = ctx2.solve(ctx2.matrix(big), b, x, 1e-8, 500, ctx2.policy_fixed((0, 4, 4, 4)), history_cap=500)
+    ref = O.solve(O.Options(min_k=0, variant=1, on_breakdown=1), big, b, 1e-8, 500, fixed=(0, 4, 4, 4))
+    assert r["outcome"] == ref.outcome == O.CONVERGED and r["n_restarts"] == 1
+    assert abs(r["iters"] - ref.iters) <= 1
+    # Jacobi
+    rng = np.random.default_rng(4)
+    Aj = I.diffusion_varcoef((12, 11, 10), 1.5, rng)
+    _, bj = I.rhs_from_xstar(Aj, rng)
+    ctx3 = M.Context(0, M.Options(min_k=0, variant=1, precond=1))
+    xj = np.zeros(Aj[0])
+    r, h = ctx3.solve(ctx3.matrix(Aj), bj, xj, 1e-8, 3000, ctx3.policy_fixed(ALL64), history_cap=3000)
+    ref = O.solve(O.Options(min_k=0, variant=1, precond=1), Aj, bj, 1e-8, 3000, fixed=ALL64)
+    assert r["outcome"] == ref.outcome == O.CONVERGED and abs(r["iters"] - ref.iters) <= 2
+    n = min(40, r["iters"])
+    _hist_ok(h, ref.hist, n, ALL64)
+    with pytest.raises(M.MpcgError):
+        M.Context(0, M.Options(variant=1, precond=2))
+
+
+def test_single_reduction_training_rounds_match_oracle(M):
+    """Batched Algorithm 1 with the single-reduction iteration: two lanes, product in fp64,
+    the other operations in {fp32, fp64} (as in the four-lane test of the CG of Section 3)."""
+    sets = []
+    for i, m in enumerate((20, 28)):
+        A = I.poisson2d(m)
+        xs, b = I.rhs_from_xstar(A, np.random.default_rng(50 + i))
+        sets.append((A, b))
+    oo = O.Options(seed=9, min_k=0, variant=1, precs=(O.FP32, O.FP64), cost={O.FP32: 1.0, O.FP64: 2.0},
+                   op_mask=(0b10, 0b11, 0b11, 0b11))
+    E, tmax = 6, 300
+    qt = O.QTable.zeros(oo)
+    it_o = np.array([O.train_round(oo, [s[0] for s in sets], [s[1] for s in sets], 1e-6, tmax, e, E, qt)
+                     for e in range(1, E + 1)])
+    ctx = M.Context(0, M.Options(min_k=0, seed=9, variant=1, precs=(3, 4), cost=(1.0, 2.0),
+                                 op_mask=(0b10, 0b11, 0b11, 0b11)))
+    mats = [ctx.matrix(_dev(A)) for A, _ in sets]
+    bs = [torch.as_tensor(b).cuda() for _, b in sets]
+    pol = ctx.policy_qtable(np.zeros((4, 100, 2)), np.zeros((4, 100), dtype=np.int32))
+    it_g = ctx.train_qtable(mats, bs, 1e-6, tmax, E, pol, want_iters=True)
+    Qg, vg = pol.qtable()
+    assert np.array_equal(it_g, it_o), (it_g, it_o)
+    assert np.array_equal(vg, qt.visits)
+    assert np.allclose(Qg, qt.Q, rtol=1e-6, atol=1e-9), float(np.max(np.abs(Qg - qt.Q)))
