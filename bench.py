@@ -72,8 +72,12 @@ def nvtx(name: str):
         torch.cuda.nvtx.range_pop()
 
 
+STEPPED = 0  # single solves: automatic (the stepped graph at this size); --stepped overrides
+
+
 def solver_options(M, op_mask=OP_MASK):
-    return M.Options(true_res_at_conv=1, on_breakdown=1, op_mask=op_mask, t_bin=T_BIN, seed=TRAIN_SEED)
+    return M.Options(true_res_at_conv=1, on_breakdown=1, op_mask=op_mask, t_bin=T_BIN, seed=TRAIN_SEED,
+                     stepped=STEPPED)
 
 
 def train_policy(M, ctx):
@@ -534,12 +538,17 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the full-precision-set policy, the 512-system batch and the SpMV table")
+    ap.add_argument("--stepped", type=int, default=0,
+                    help="single-solve launch form: 0 automatic, 1 persistent kernel, 2 stepped graph, 3 stepped "
+                         "passes launched by the host (profilers see each phase kernel)")
     ap.add_argument("--history-out", default=None,
                     help="write the first timed solve's per-iteration records (numpy .npy) to this path")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
+    global STEPPED
+    STEPPED = args.stepped
 
     import torch
 

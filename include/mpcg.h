@@ -147,7 +147,10 @@ typedef struct {
                             * of at least 2^24 nonzeros without IC(0)), 1 = one persistent
                             * cooperative launch, 2 = stepped: one kernel per phase of the
                             * iteration, repeated on the device by a conditional while-loop
-                            * CUDA graph (precond = 2 always runs the persistent launch,
+                            * CUDA graph, 3 = the same kernels with each pass launched by the
+                            * host, which reads the phase back after every pass (for tools
+                            * that cannot follow kernels inside graphs with conditional
+                            * nodes; slower) (precond = 2 always runs the persistent launch,
                             * whose substitutions need every CTA resident)              */
   int32_t variant;         /* 0: the CG of Section 3 (three reductions per iteration); 1: the
                             * single-reduction iteration of Chronopoulos and Gear (an

@@ -71,6 +71,7 @@ struct Plan {
   size_t icwork_bytes = 0;
   bool lockstep = false;
   bool stepped = false;      // one system, one kernel per phase in a while-loop graph
+  bool stepped_host = false; // ... the passes launched by the host instead (option stepped = 3)
   int sgrid[kPhaseKernels] = {0, 0, 0, 0, 0, 0};
   size_t ssmem = 0;
   cudaGraphExec_t sexec = nullptr;
@@ -186,7 +187,7 @@ mpcg_status build_optview(mpcg_ctx_t ctx, const mpcg_options& o, OptView& v) {
   if (o.batch_mode < 0 || o.batch_mode > 2) return fail(ctx, MPCG_ERR_INVALID_ARG, "batch_mode must be 0, 1 or 2");
   if (o.precond < 0 || o.precond > 2) return fail(ctx, MPCG_ERR_INVALID_ARG, "precond must be 0, 1 or 2");
   if (!(o.edge_tol >= 0.0 && o.edge_tol < 1.0)) return fail(ctx, MPCG_ERR_INVALID_ARG, "edge_tol must be in [0, 1)");
-  if (o.stepped < 0 || o.stepped > 2) return fail(ctx, MPCG_ERR_INVALID_ARG, "stepped must be 0, 1 or 2");
+  if (o.stepped < 0 || o.stepped > 3) return fail(ctx, MPCG_ERR_INVALID_ARG, "stepped must be 0, 1, 2 or 3");
   if (o.variant < 0 || o.variant > 1) return fail(ctx, MPCG_ERR_INVALID_ARG, "variant must be 0 or 1");
   if (o.variant == 1 && o.precond == 2)
     return fail(ctx, MPCG_ERR_INVALID_ARG, "the single-reduction iteration runs with precond 0 or 1");
@@ -509,6 +510,7 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
   if (sr && force_team > 0) return fail(ctx, MPCG_ERR_INVALID_ARG, "the single-reduction iteration runs without teams");
   pl.lockstep = !stepped && force_team == 0 && ((bm == 0 && nsys >= 2) || bm == 2 || sr) && nsys >= 1;
   pl.stepped = stepped;
+  pl.stepped_host = false;
   int pgrid = 0;
   if (stepped) {
     for (int w = 0; w < kPhaseKernels; ++w) {
@@ -604,6 +606,20 @@ mpcg_status enqueue_plan(mpcg_ctx_t ctx, Plan& pl, cudaStream_t s) {
       pl.sexec = nullptr;
     }
     const unsigned limit = 8u * (unsigned)std::min(pl.hsys[0].max_iter + 4, 1 << 26) + 64u;
+    if (pl.stepped_host) {
+      // the same passes launched from the host, the phase read back after each pass (for tools
+      // that do not follow kernels inside graphs with conditional nodes); bounded like the graph
+      int phase = 0;
+      unsigned herr = 0;
+      for (unsigned pass = 0; pass < limit; ++pass) {
+        CK(ctx, stepped_pass(pl.L, pl.sgrid, pl.ssmem, s));
+        CK(ctx, cudaMemcpyAsync(&phase, &pl.L.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(ctx, cudaMemcpyAsync(&herr, pl.L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        CK(ctx, cudaStreamSynchronize(s));
+        if (phase == kPhaseDone || herr) return MPCG_OK;
+      }
+      return fail(ctx, MPCG_ERR_INTERNAL, "the stepped solve did not finish within its pass limit");
+    }
     cudaGraph_t g = nullptr;
     CK(ctx, stepped_graph(pl.L, pl.sgrid, pl.ssmem, limit, &g));
     const cudaError_t e = cudaGraphInstantiate(&pl.sexec, g, 0);
@@ -1331,8 +1347,10 @@ mpcg_status mpcg_solve(mpcg_ctx_t ctx, mpcg_matrix_t A, const double* b, double*
   if (const char* f = getenv("MPCG_FORCE_TEAM")) force = atoi(f);
   // stepped (one kernel per phase in a while-loop graph) for large systems, or when asked
   const int sm = ctx->opt.stepped;
-  const bool stepped = ctx->opt.precond != 2 && force == 0 && (sm == 2 || (sm == 0 && A->dm.nnz >= (1LL << 24)));
+  const bool stepped =
+      ctx->opt.precond != 2 && force == 0 && (sm >= 2 || (sm == 0 && A->dm.nnz >= (1LL << 24)));
   mpcg_status st = build_plan(ctx, pl, in, policy, 0, 0, force, s, 0, stepped);
+  pl.stepped_host = stepped && sm == 3;
   if (st != MPCG_OK) return st;
   st = enqueue_plan(ctx, pl, s);
   if (st != MPCG_OK) return st;

@@ -200,10 +200,12 @@ cudaError_t launch_cg_lockstep(const Launch& L, int grid, size_t smem, cudaStrea
 // the graph repeats them (grids[w] CTAs each, smem bytes of dynamic shared memory for the
 // product kernels and kernel 3) until the system is done or `limit` passes ran.
 constexpr int kPhaseKernels = 6;
+constexpr int kPhaseDone = 10;  // the phase machine's final phase (PH_DONE in solver.cuh)
 cudaError_t stepped_occupancy(int which, int* blocks_per_sm, size_t smem);
 cudaError_t stepped_set_smem_limit(size_t bytes);
 cudaError_t stepped_graph(const Launch& L, const int grids[kPhaseKernels], size_t smem, unsigned limit,
                           cudaGraph_t* out);
+cudaError_t stepped_pass(const Launch& L, const int grids[kPhaseKernels], size_t smem, cudaStream_t s);
 // the IC(0) instantiations (cg_kernel_ic.cu)
 cudaError_t launch_cg_ic(const Launch& L, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_cg_lockstep_ic(const Launch& L, int grid, size_t smem, cudaStream_t s);

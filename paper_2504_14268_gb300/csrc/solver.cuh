@@ -619,6 +619,8 @@ __device__ void step_init(const Launch& L, const DevSys& S, SysState* st, double
     st->n_restart = 0;
     st->ns_a = st->ns_b = 0;
     st->near_edge = 0;
+    st->restart_sr = 1;  // the single-reduction recurrence starts with beta = 0
+    st->sr_gamma = st->sr_alpha = 0.0;
     st->t_last = gtime();
     for (int j = 0; j < 4; ++j) {
       st->prev_act[j] = 0;
@@ -1591,6 +1593,7 @@ __device__ __noinline__ void sr_u_rows(const DevSys& S, Rows R, double alpha, do
 // phase, and the write of u's product-format copy after an initialisation or a restart.
 enum LkPhase : int { PH_INIT = 0, PH_PLOW, PH_A, PH_B, PH_C, PH_X, PH_T, PH_RZ, PH_R64, PH_FINAL, PH_DONE,
                      PH_W, PH_U, PH_UL };
+static_assert(PH_DONE == kPhaseDone, "the host reads the final phase's code");
 
 __device__ __forceinline__ bool grid_sync(const Launch& L, const TeamCtx& G, Smem& sm) {
   if (team_arrive(G, sm)) {

@@ -132,6 +132,23 @@ cudaError_t stepped_set_smem_limit(size_t bytes) {
   return cudaSuccess;
 }
 
+// One pass through the body's phase kernels launched on `s` (the host-driven form of the loop:
+// the caller checks the system's phase between passes).
+cudaError_t stepped_pass(const Launch& L, const int grids[kPhaseKernels], size_t smem, cudaStream_t s) {
+  const int std_body[4] = {0, 1, 2, 3}, sr_body[3] = {4, 5, 3};
+  const int* body_k = L.opt.variant ? sr_body : std_body;
+  const int nbody = L.opt.variant ? 3 : 4;
+  Launch Lc = L;
+  void* args[] = {(void*)&Lc};
+  for (int i = 0; i < nbody; ++i) {
+    const int w = body_k[i];
+    const cudaError_t e = cudaLaunchKernel(phase_kernel(w), dim3(grids[w]), dim3(kThreads), args,
+                                           (w == 0 || w == 3 || w == 4) ? smem : 0, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // The graph of one stepped solve: a while-loop node whose body chains the phase kernels
 // (kernels 0, 1, 2, 3 for the CG of Section 3, or 4, 5, 3 for the single-reduction iteration;
 // grids[w] CTAs for kernel w, dynamic shared memory smem for the product kernels and the

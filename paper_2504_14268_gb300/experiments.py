@@ -66,6 +66,9 @@ def main():
     ap.add_argument("--train", type=int, default=10)
     ap.add_argument("--test", type=int, default=100)
     ap.add_argument("--episodes", type=int, default=200)
+    ap.add_argument("--on-breakdown", type=int, default=0,
+                    help="0: a breakdown ends the solve (the paper); 1: greedy solves restart in fp64")
+    ap.add_argument("--out", default=None, help="also write the report (one JSON object) to this file")
     args = ap.parse_args()
 
     import scipy.sparse as sp
@@ -79,7 +82,8 @@ def main():
     from paper_2504_14268_gb300 import mpcg as M
 
     tau, t_max = 1e-6, 1000
-    opts = M.Options(cost=COSTS[args.cost], precond=args.precond, min_k=10, t_bin=t_max)
+    opts = M.Options(cost=COSTS[args.cost], precond=args.precond, min_k=10, t_bin=t_max,
+                     on_breakdown=args.on_breakdown)
     ctx = M.Context(0, opts)
     skipped: list = []
     t0 = time.time()
@@ -103,7 +107,8 @@ def main():
         n, rp, ci, val = A
         xtrue.append(sla.spsolve(sp.csc_matrix(sp.csr_matrix((val, ci, rp), shape=(n, n))), b))
     report = {"family": args.family, "cost": args.cost, "precond": args.precond, "train": args.train,
-              "test": args.test, "episodes": args.episodes, "skipped_seeds": skipped,
+              "test": args.test, "episodes": args.episodes, "on_breakdown": args.on_breakdown,
+              "skipped_seeds": skipped,
               "setup_s": round(t_setup, 2), "train_s": round(t_train, 2)}
     for label, policy in (("rl", pol), ("fp64", ctx.policy_fixed((4, 4, 4, 4)))):
         xs = [torch.zeros_like(b) for b in bs]
@@ -113,10 +118,18 @@ def main():
         torch.cuda.synchronize()
         dt = time.time() - t0
         err = [float(np.linalg.norm(x.cpu().numpy() - xt) / np.linalg.norm(xt)) for x, xt in zip(xs, xtrue)]
+        ok = [r["outcome"] == 0 for r in res]
         report[label] = {"solve_s": round(dt, 3), "rel_err": _stats(err), "iters": _stats([r["iters"] for r in res]),
-                         "converged": float(np.mean([r["outcome"] == 0 for r in res])),
+                         "converged": float(np.mean(ok)),
+                         "breakdowns": int(sum(r["outcome"] == 2 for r in res)),
+                         "restarts": int(sum(r["n_restarts"] for r in res)),
+                         "rel_err_converged": _stats([e for e, c in zip(err, ok) if c]) if any(ok) else None,
                          "format_share": format_shares([r["action_hist"] for r in res])}
-    print(json.dumps(report))
+    line = json.dumps(report)
+    print(line)
+    if args.out:
+        with open(args.out, "w") as f:
+            f.write(line + "\n")
 
 
 if __name__ == "__main__":
