@@ -164,6 +164,13 @@ typedef struct {
                             * stepped kernels (every launch with variant 1 uses them), with
                             * M = I or Jacobi (precond 2 is refused); mpcg_solve_noalloc
                             * refuses it                                                  */
+  int32_t joint;           /* tabular policies: 0 = one table per operation (Section 4.1), 1 =
+                            * one table over the joint actions (the |P|^m alternative that
+                            * Section 4.1 weighs): Q[S][nprec^4], entry ((a1 P + a2) P + a3) P
+                            * + a4, update counts visits[S]; the allowed joint actions are the
+                            * product of the op_mask sets, greedy is the first largest allowed
+                            * entry, exploration draws op 1's u and each operation's pick    */
+  int32_t reserved_joint;
 } mpcg_options;
 
 /* Result of one solve. */
@@ -283,7 +290,8 @@ mpcg_status mpcg_policy_fixed(mpcg_ctx_t ctx, const int32_t fmt[4], mpcg_policy_
 /* Iteration k uses row min(k, len-1) of the host array fmts[len][4] (replay). */
 mpcg_status mpcg_policy_schedule(mpcg_ctx_t ctx, const int32_t* fmts, int32_t len, mpcg_policy_t* out);
 /* Tabular policy (Section 4.1): Q[4][b*r][nprec] fp64 and visits[4][b*r] (host arrays,
- * visits may be NULL = all visited), shaped by the context's options. */
+ * visits may be NULL = all visited), shaped by the context's options; with options.joint,
+ * Q[b*r][nprec^4] and visits[b*r]. */
 mpcg_status mpcg_policy_qtable(mpcg_ctx_t ctx, const double* Q, const int32_t* visits, mpcg_policy_t* out);
 /* MLP Q-function 16 -> H -> H -> 4*nprec (ReLU), fp32 parameters in the layout W1[H][16],
  * b1[H], W2[H][H], b2[H], W3[4*nprec][H], b3[4*nprec] (host array of mpcg_mlp_nparams

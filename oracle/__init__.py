@@ -56,7 +56,7 @@ class Opts(C.Structure):
         ("gamma", C.c_double), ("eps0", C.c_double), ("eps_floor", C.c_double), ("seed", C.c_uint64),
         ("unvisited_fallback", C.c_int), ("true_res_every", C.c_int), ("true_res_at_conv", C.c_int),
         ("op_mask", C.c_int * 4), ("on_breakdown", C.c_int), ("mlp_hidden", C.c_int), ("precond", C.c_int),
-        ("variant", C.c_int),
+        ("variant", C.c_int), ("joint", C.c_int),
     ]
 
 
@@ -172,12 +172,13 @@ class Options:
     mlp_hidden: int = 64
     precond: int = 0
     variant: int = 0  # 0: the CG of Section 3; 1: the single-reduction iteration (orc_run_sr)
+    joint: int = 0  # 0: a Q-table per operation (Section 4.1); 1: one table over the joint actions
 
     def c(self) -> Opts:
         o = Opts()
         for name in ("b_bins", "r_bins", "t_bin", "min_k", "eps_min", "w1", "w2", "w3", "lr", "gamma",
                      "eps0", "eps_floor", "seed", "unvisited_fallback", "true_res_every",
-                     "true_res_at_conv", "on_breakdown", "mlp_hidden", "precond", "variant"):
+                     "true_res_at_conv", "on_breakdown", "mlp_hidden", "precond", "variant", "joint"):
             setattr(o, name, getattr(self, name))
         for j in range(4):
             o.op_mask[j] = int(self.op_mask[j])
@@ -287,6 +288,8 @@ class QTable:
     @staticmethod
     def zeros(opts: Options) -> "QTable":
         S = opts.n_states
+        if opts.joint:  # one table over the joint actions: [S][|P|^4], counts per state
+            return QTable(np.zeros((S, len(opts.precs) ** 4)), np.zeros(S, dtype=np.int32))
         return QTable(np.zeros((4, S, len(opts.precs))), np.zeros((4, S), dtype=np.int32))
 
     def copy(self) -> "QTable":

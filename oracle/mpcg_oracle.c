@@ -156,6 +156,8 @@ typedef struct {
                              z = L^-T L^-1 r unrounded beyond fp32                      */
   int variant;            /* 0: the CG of Section 3 (orc_run); 1: the single-reduction
                              iteration of orc_run_sr (M = I or Jacobi)                  */
+  int joint;              /* 0: one Q-table per operation (Section 4.1); 1: one table over
+                             the joint actions (orc_q_update_joint)                     */
 } orc_opts;
 
 enum { ORC_POL_FIXED = 0, ORC_POL_SCHEDULE = 1, ORC_POL_QTABLE = 2, ORC_POL_MLP = 3 };
@@ -647,6 +649,70 @@ typedef struct {
 /* Select the action of operation-table j in state s.
  *   inference: greedy first-index argmax; a never-updated row falls back (READING)
  *   training : epsilon-greedy, draws from orc_draw(...) */
+/* ---- One table over joint actions (Section 4.1's alternative to a table per operation) --
+ * READING: Section 4.1 sets a table per operation against the |P|^m joint actions; the joint
+ * form is Q(s, a) with a = (a_1, a_2, a_3, a_4), stored at index ((a_1 |P| + a_2) |P| + a_3) |P|
+ * + a_4 of state s's row ([S][|P|^4]), update counts per state. The joint set is the product of
+ * the operations' allowed sets (op_mask); greedy: the first joint index with the largest value
+ * among the allowed ones (op 1 the most significant digit); a never-updated state takes the
+ * fallback format for every operation when all four allow it; exploration: operation 1's draw
+ * decides (u < epsilon), each operation's pick comes from its own draw (uniform over the
+ * product set); update: Q(s, a) += lr (R + gamma max_{a' allowed} Q(s', a') - Q(s, a)). */
+static int joint_size(const orc_opts* o) { return o->nprec * o->nprec * o->nprec * o->nprec; }
+
+static void joint_decode(const orc_opts* o, int a, int act[4]) {
+  for (int j = 3; j >= 0; --j) {
+    act[j] = a % o->nprec;
+    a /= o->nprec;
+  }
+}
+
+static int joint_ok(const orc_opts* o, int a) {
+  int act[4];
+  joint_decode(o, a, act);
+  for (int j = 0; j < 4; ++j)
+    if (!allowed(o, j, act[j])) return 0;
+  return 1;
+}
+
+static int joint_argmax(const orc_opts* o, const double* row) {
+  int best = -1;
+  for (int a = 0; a < joint_size(o); ++a)
+    if (joint_ok(o, a) && (best < 0 || row[a] > row[best])) best = a;
+  return best;
+}
+
+static double joint_max(const orc_opts* o, const double* row) {
+  double m = -INFINITY;
+  for (int a = 0; a < joint_size(o); ++a)
+    if (joint_ok(o, a) && row[a] > m) m = row[a];
+  return m;
+}
+
+static void select_joint(const orc_opts* o, const orc_policy* pol, int mode, int s, double eps, uint64_t ep,
+                         uint64_t lane, int k, int act[4], int* explored) {
+  const double* row = pol->Q + (int64_t)s * joint_size(o);
+  if (mode == ORC_MODE_TRAIN) {
+    double u[4];
+    uint32_t pick[4];
+    for (int j = 0; j < 4; ++j) orc_draw(o->seed, ep, lane, (uint64_t)k, (uint64_t)j, &u[j], &pick[j]);
+    if (u[0] < eps) {
+      *explored = 1;
+      for (int j = 0; j < 4; ++j) act[j] = random_allowed(o, j, pick[j]);
+      return;
+    }
+  } else if (o->unvisited_fallback >= 0 && pol->visits[s] == 0) {
+    int a = index_of(o, o->unvisited_fallback);
+    int all = a >= 0;
+    for (int j = 0; j < 4; ++j) all = all && allowed(o, j, a);
+    if (all) {
+      for (int j = 0; j < 4; ++j) act[j] = a;
+      return;
+    }
+  }
+  joint_decode(o, joint_argmax(o, row), act);
+}
+
 static int select_qtable(const orc_opts* o, const orc_policy* pol, int mode, int j, int s,
                          double eps, uint64_t ep, uint64_t lane, int k, int* explored) {
   int S = o->b_bins * o->r_bins;
@@ -681,7 +747,13 @@ int orc_greedy_action(const orc_opts* o, const double* Q, const int32_t* visits,
   pol.visits = (int32_t*)visits;
   int s = orc_state(o, k, rho);
   int explored = 0;
-  for (int j = 0; j < 4; ++j) act[j] = select_qtable(o, &pol, ORC_MODE_INFER, j, s, 0.0, 0, 0, k, &explored);
+  if (o->joint) {
+    int a[4];
+    select_joint(o, &pol, ORC_MODE_INFER, s, 0.0, 0, 0, k, a, &explored);
+    for (int j = 0; j < 4; ++j) act[j] = a[j];
+  } else {
+    for (int j = 0; j < 4; ++j) act[j] = select_qtable(o, &pol, ORC_MODE_INFER, j, s, 0.0, 0, 0, k, &explored);
+  }
   return s;
 }
 
@@ -690,6 +762,17 @@ int orc_greedy_action(const orc_opts* o, const double* Q, const int32_t* visits,
  * P_j is operation j's allowed set (all of P unless op_mask[j] restricts it). */
 void orc_q_update(const orc_opts* o, double* Q, int32_t* visits, const orc_transition* t) {
   int S = o->b_bins * o->r_bins;
+  if (o->joint) {
+    /* the joint table: one update of the joint action's entry */
+    int a = 0;
+    for (int j = 0; j < 4; ++j) a = a * o->nprec + t->act[j];
+    double* row = Q + (int64_t)t->s * joint_size(o);
+    double target = t->reward;
+    if (!t->terminal) target += o->gamma * joint_max(o, Q + (int64_t)t->s_next * joint_size(o));
+    row[a] += o->lr * (target - row[a]);
+    if (visits) visits[t->s] += 1;
+    return;
+  }
   for (int j = 0; j < 4; ++j) {
     double* row = Q + ((int64_t)j * S + t->s) * o->nprec;
     double target = t->reward;
@@ -721,6 +804,9 @@ static void choose_formats(const orc_opts* o, const orc_policy* pol, int mode, i
   } else if (pol->kind == ORC_POL_SCHEDULE) {
     int row = k < pol->sched_len ? k : pol->sched_len - 1;
     for (int j = 0; j < 4; ++j) fmt[j] = pol->sched[(int64_t)row * 4 + j];
+  } else if (pol->kind == ORC_POL_QTABLE && o->joint) {
+    select_joint(o, pol, mode, s, eps, ep, lane, k, act, explored);
+    for (int j = 0; j < 4; ++j) fmt[j] = o->precs[act[j]];
   } else if (pol->kind == ORC_POL_QTABLE) {
     for (int j = 0; j < 4; ++j) {
       int ex = 0;
@@ -1280,7 +1366,7 @@ int orc_train_round(const orc_opts* o, int B, const int32_t* ns, const int32_t* 
                     const double* const* bs, double tau, int t_max, int e, int E, double* Q,
                     int32_t* visits, int32_t* iters_out) {
   int S = o->b_bins * o->r_bins;
-  int64_t qsize = (int64_t)4 * S * o->nprec;
+  int64_t qsize = o->joint ? (int64_t)S * joint_size(o) : (int64_t)4 * S * o->nprec;
   double* Qp = malloc(sizeof(double) * qsize);
   orc_transition* all = malloc(sizeof(orc_transition) * (size_t)B * (size_t)(t_max > 0 ? t_max : 1));
   int32_t* counts = malloc(sizeof(int32_t) * (size_t)B);

@@ -120,6 +120,7 @@ struct mpcg_policy_s {
   int sched_len = 0;
   DevBuf sched, Q, visits, mlp;
   int S = 0, nprec = 0, H = 0;
+  int joint = 0;  // tabular: one table over the joint actions
   int device = 0;
   mpcg_options shape;
 };
@@ -189,6 +190,7 @@ mpcg_status build_optview(mpcg_ctx_t ctx, const mpcg_options& o, OptView& v) {
   if (!(o.edge_tol >= 0.0 && o.edge_tol < 1.0)) return fail(ctx, MPCG_ERR_INVALID_ARG, "edge_tol must be in [0, 1)");
   if (o.stepped < 0 || o.stepped > 3) return fail(ctx, MPCG_ERR_INVALID_ARG, "stepped must be 0, 1, 2 or 3");
   if (o.variant < 0 || o.variant > 1) return fail(ctx, MPCG_ERR_INVALID_ARG, "variant must be 0 or 1");
+  if (o.joint < 0 || o.joint > 1) return fail(ctx, MPCG_ERR_INVALID_ARG, "joint must be 0 or 1");
   if (o.variant == 1 && o.precond == 2)
     return fail(ctx, MPCG_ERR_INVALID_ARG, "the single-reduction iteration runs with precond 0 or 1");
   for (int a = 0; a < o.nprec; ++a)
@@ -230,6 +232,7 @@ mpcg_status build_optview(mpcg_ctx_t ctx, const mpcg_options& o, OptView& v) {
   v.precond = o.precond;
   v.edge_tol = o.edge_tol;
   v.variant = o.variant;
+  v.joint = o.joint ? 1 : 0;
   for (int j = 0; j < 4; ++j) {
     const unsigned all = (1u << o.nprec) - 1u;
     const unsigned m = o.op_mask[j] ? ((unsigned)o.op_mask[j] & all) : all;
@@ -341,7 +344,8 @@ mpcg_status fill_policy(mpcg_ctx_t ctx, mpcg_policy_t P, PolicyView& pv) {
   pv.H = P->H;
   if (P->kind == 2 || P->kind == 3) {
     const mpcg_options& o = ctx->opt;
-    if (P->nprec != o.nprec || (P->kind == 2 && P->S != o.b_bins * o.r_bins) || (P->kind == 3 && P->H != o.mlp_hidden))
+    if (P->nprec != o.nprec || (P->kind == 2 && (P->S != o.b_bins * o.r_bins || P->joint != (o.joint ? 1 : 0))) ||
+        (P->kind == 3 && P->H != o.mlp_hidden))
       return fail(ctx, MPCG_ERR_BAD_POLICY, "policy shape (S=%d, nprec=%d, H=%d) differs from the context's options",
                   P->S, P->nprec, P->H);
   }
@@ -446,7 +450,7 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
   if (mbytes) CK(ctx, pl.icwork.ensure(mbytes));
   unsigned long long* icw_next = pl.icwork.as<unsigned long long>();
   const int S = ctx->opt.b_bins * ctx->opt.r_bins;
-  const long long qsize = 4LL * S * ctx->opt.nprec;
+  const long long qsize = qtable_size(S, ctx->opt.nprec, ctx->opt.joint ? 1 : 0);
   if (train) {
     CK(ctx, pl.qpriv.ensure(sizeof(double) * qsize * nsys));
     CK(ctx, pl.trans.ensure(sizeof(Transition) * (size_t)trans_cap * nsys));
@@ -713,6 +717,8 @@ void mpcg_options_default(mpcg_options* o) {
   o->edge_tol = 5e-3;
   o->stepped = 0;
   o->variant = 0;
+  o->joint = 0;
+  o->reserved_joint = 0;
 }
 
 mpcg_status mpcg_create(mpcg_ctx_t* out, int device, const mpcg_options* opt) {
@@ -1135,6 +1141,7 @@ static mpcg_policy_s* new_policy(mpcg_ctx_t ctx, int kind) {
   P->nprec = ctx->opt.nprec;
   P->S = ctx->opt.b_bins * ctx->opt.r_bins;
   P->H = ctx->opt.mlp_hidden;
+  P->joint = ctx->opt.joint ? 1 : 0;
   return P;
 }
 
@@ -1165,11 +1172,11 @@ mpcg_status mpcg_policy_qtable(mpcg_ctx_t ctx, const double* Q, const int32_t* v
   if (!ctx || !Q || !out) return fail(ctx, MPCG_ERR_INVALID_ARG, "NULL argument");
   cudaSetDevice(ctx->device);
   std::unique_ptr<mpcg_policy_s> P(new_policy(ctx, 2));
-  const size_t qn = 4 * (size_t)P->S * P->nprec;
+  const size_t qn = (size_t)qtable_size(P->S, P->nprec, P->joint);
   CK(ctx, P->Q.ensure(sizeof(double) * qn));
-  CK(ctx, P->visits.ensure(sizeof(int) * 4 * (size_t)P->S));
+  CK(ctx, P->visits.ensure(sizeof(int) * (size_t)visits_size(P->S, P->joint)));
   CK(ctx, cudaMemcpy(P->Q.p, Q, sizeof(double) * qn, cudaMemcpyHostToDevice));
-  std::vector<int> v(4 * (size_t)P->S, 1);
+  std::vector<int> v((size_t)visits_size(P->S, P->joint), 1);
   if (visits) memcpy(v.data(), visits, sizeof(int) * v.size());
   CK(ctx, cudaMemcpy(P->visits.p, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice));
   *out = P.release();
@@ -1195,9 +1202,11 @@ mpcg_status mpcg_policy_mlp(mpcg_ctx_t ctx, const float* params, mpcg_policy_t* 
 mpcg_status mpcg_policy_get_qtable(mpcg_policy_t P, double* Q, int32_t* visits) {
   if (!P || P->kind != 2) return MPCG_ERR_INVALID_ARG;
   cudaSetDevice(P->ctx->device);
-  const size_t qn = 4 * (size_t)P->S * P->nprec;
+  const size_t qn = (size_t)qtable_size(P->S, P->nprec, P->joint);
   if (Q) CK(P->ctx, cudaMemcpy(Q, P->Q.p, sizeof(double) * qn, cudaMemcpyDeviceToHost));
-  if (visits) CK(P->ctx, cudaMemcpy(visits, P->visits.p, sizeof(int) * 4 * (size_t)P->S, cudaMemcpyDeviceToHost));
+  if (visits)
+    CK(P->ctx, cudaMemcpy(visits, P->visits.p, sizeof(int) * (size_t)visits_size(P->S, P->joint),
+                          cudaMemcpyDeviceToHost));
   return MPCG_OK;
 }
 
@@ -1217,6 +1226,7 @@ struct BlobHeader {
   int32_t precs[8];
   double cost[8];
   int32_t sched_len, fixed[4];
+  int32_t joint, pad;
   int64_t payload;
 };
 }  // namespace
@@ -1226,7 +1236,9 @@ mpcg_status mpcg_policy_save(mpcg_policy_t P, void* blob, size_t* bytes) {
   mpcg_ctx_t ctx = P->ctx;
   size_t payload = 0;
   if (P->kind == 1) payload = sizeof(int) * 4 * (size_t)P->sched_len;
-  if (P->kind == 2) payload = sizeof(double) * 4 * (size_t)P->S * P->nprec + sizeof(int) * 4 * (size_t)P->S;
+  if (P->kind == 2)
+    payload = sizeof(double) * (size_t)qtable_size(P->S, P->nprec, P->joint) +
+              sizeof(int) * (size_t)visits_size(P->S, P->joint);
   if (P->kind == 3) payload = sizeof(float) * (size_t)mpcg_mlp_nparams(P->H, P->nprec);
   const size_t total = sizeof(BlobHeader) + payload;
   if (!blob) {
@@ -1249,6 +1261,7 @@ mpcg_status mpcg_policy_save(mpcg_policy_t P, void* blob, size_t* bytes) {
     h.cost[a] = P->shape.cost[a];
   }
   h.sched_len = P->sched_len;
+  h.joint = P->joint;
   for (int j = 0; j < 4; ++j) h.fixed[j] = P->fixed[j];
   h.payload = (int64_t)payload;
   char* o = (char*)blob;
@@ -1257,9 +1270,10 @@ mpcg_status mpcg_policy_save(mpcg_policy_t P, void* blob, size_t* bytes) {
   cudaSetDevice(ctx->device);
   if (P->kind == 1) CK(ctx, cudaMemcpy(o, P->sched.p, payload, cudaMemcpyDeviceToHost));
   if (P->kind == 2) {
-    const size_t qb = sizeof(double) * 4 * (size_t)P->S * P->nprec;
+    const size_t qb = sizeof(double) * (size_t)qtable_size(P->S, P->nprec, P->joint);
     CK(ctx, cudaMemcpy(o, P->Q.p, qb, cudaMemcpyDeviceToHost));
-    CK(ctx, cudaMemcpy(o + qb, P->visits.p, sizeof(int) * 4 * (size_t)P->S, cudaMemcpyDeviceToHost));
+    CK(ctx, cudaMemcpy(o + qb, P->visits.p, sizeof(int) * (size_t)visits_size(P->S, P->joint),
+                       cudaMemcpyDeviceToHost));
   }
   if (P->kind == 3) CK(ctx, cudaMemcpy(o, P->mlp.p, payload, cudaMemcpyDeviceToHost));
   *bytes = total;
@@ -1287,8 +1301,11 @@ mpcg_status mpcg_policy_load(mpcg_ctx_t ctx, const void* blob, size_t bytes, mpc
     if (h.precs[a] != c.precs[a]) return fail(ctx, MPCG_ERR_BAD_POLICY, "precision set differs at %d", a);
   if (h.kind == 2) {
     if (h.b_bins != c.b_bins || h.r_bins != c.r_bins) return fail(ctx, MPCG_ERR_BAD_POLICY, "state bins differ");
-    const size_t qb = sizeof(double) * 4 * (size_t)c.b_bins * c.r_bins * c.nprec;
-    if ((size_t)h.payload != qb + sizeof(int) * 4 * (size_t)c.b_bins * c.r_bins) return fail(ctx, MPCG_ERR_INVALID_ARG, "bad table payload");
+    if ((h.joint != 0) != (c.joint != 0)) return fail(ctx, MPCG_ERR_BAD_POLICY, "joint and per-operation tables differ");
+    const int S = c.b_bins * c.r_bins;
+    const size_t qb = sizeof(double) * (size_t)qtable_size(S, c.nprec, c.joint ? 1 : 0);
+    if ((size_t)h.payload != qb + sizeof(int) * (size_t)visits_size(S, c.joint ? 1 : 0))
+      return fail(ctx, MPCG_ERR_INVALID_ARG, "bad table payload");
     return mpcg_policy_qtable(ctx, (const double*)o, (const int32_t*)(o + qb), out);
   }
   if (h.kind == 3) {
@@ -1497,7 +1514,7 @@ mpcg_status mpcg_train_qtable(mpcg_ctx_t ctx, int32_t nsys, const mpcg_matrix_t*
   if (st != MPCG_OK) return st;
   const mpcg_options& o = ctx->opt;
   const int S = o.b_bins * o.r_bins;
-  const long long qsize = 4LL * S * o.nprec;
+  const long long qsize = qtable_size(S, o.nprec, o.joint ? 1 : 0);
   std::vector<mpcg_result> rr(nsys);
   for (int e = 1; e <= episodes; ++e) {
     // epsilon_e = max(eps_floor, eps0 (1 - e / E))  (Section 4.1 with the floor of Section 5)
@@ -1509,7 +1526,8 @@ mpcg_status mpcg_train_qtable(mpcg_ctx_t ctx, int32_t nsys, const mpcg_matrix_t*
     st = enqueue_plan(ctx, pl, s);
     if (st != MPCG_OK) return st;
     CK(ctx, launch_qmerge(inout->Q.as<double>(), inout->visits.as<int>(), pl.trans.as<Transition>(),
-                          pl.st.as<SysState>(), nsys, t_max, S, o.nprec, o.lr, o.gamma, op_masks(o), s));
+                          pl.st.as<SysState>(), nsys, t_max, S, o.nprec, o.lr, o.gamma, op_masks(o), o.joint ? 1 : 0,
+                          s));
     if (iters_out || e == episodes) {
       st = finish_plan(ctx, pl, rr.data(), s);
       if (st != MPCG_OK) return st;
@@ -1551,7 +1569,7 @@ mpcg_status mpcg_collect(mpcg_ctx_t ctx, int32_t nsys, const mpcg_matrix_t* A, c
   st = build_plan(ctx, pl, in, behavior, 1, max_iter, 0, s, max_iter + 1);
   if (st != MPCG_OK) return st;
   const mpcg_options& o = ctx->opt;
-  const long long qsize = 4LL * o.b_bins * o.r_bins * o.nprec;
+  const long long qsize = qtable_size(o.b_bins * o.r_bins, o.nprec, o.joint ? 1 : 0);
   if (behavior->kind == 2) CK(ctx, launch_qcopy(behavior->Q.as<double>(), pl.qpriv.as<double>(), nsys, qsize, s));
   pl.L.episode = (unsigned long long)episode;
   pl.L.eps = eps;

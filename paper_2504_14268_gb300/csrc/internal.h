@@ -140,7 +140,7 @@ struct OptView {
   int op_mask[4];           // allowed action indices per operation (all bits set = no restriction)
   double edge_tol;          // relative distance to a residual-bin threshold counted as near an edge
   int variant;              // 0: the CG of Section 3; 1: the single-reduction iteration
-  int pad_v;
+  int joint;                // 1: one Q-table over the joint actions ([S][nprec^4], visits [S])
 };
 
 // Arguments of one launch of the persistent kernel.
@@ -187,6 +187,28 @@ __device__ __forceinline__ double row_max_allowed(const double* row, int n, unsi
   for (int a = 0; a < n; ++a)
     if (((mask >> a) & 1u) && row[a] > m) m = row[a];
   return m;
+}
+
+// Joint actions (one Q-table over the four operations' formats, the |P|^4 alternative of
+// Section 4.1): a = ((a_1 P + a_2) P + a_3) P + a_4 is allowed when each a_j is in operation
+// j's set (bit a_j of m[j]).
+template <class MT>
+__device__ __forceinline__ bool joint_allowed(int a, int P, const MT* m) {
+  for (int j = 3; j >= 0; --j) {
+    if (!(((unsigned)m[j] >> (a % P)) & 1u)) return false;
+    a /= P;
+  }
+  return true;
+}
+
+// max over the allowed joint actions of a joint row (the bootstrap term of the update).
+template <class MT>
+__device__ __forceinline__ double joint_row_max(const double* row, int P, const MT* m) {
+  double mx = -__longlong_as_double(0x7ff0000000000000ll);
+  const int n = P * P * P * P;
+  for (int a = 0; a < n; ++a)
+    if (joint_allowed(a, P, m) && row[a] > mx) mx = row[a];
+  return mx;
 }
 
 // Device status word values.
@@ -255,6 +277,11 @@ cudaError_t spmv_occupancy(int* blocks_per_sm, size_t smem);
 cudaError_t set_smem_limits(size_t bytes);
 cudaError_t launch_qcopy(const double* Q, double* Qpriv, int nlanes, long long qsize, cudaStream_t s);
 cudaError_t launch_qmerge(double* Q, int* visits, const Transition* trans, const SysState* st, int nlanes, int cap,
-                          int S, int nprec, double lr, double gamma, OpMask mask, cudaStream_t s);
+                          int S, int nprec, double lr, double gamma, OpMask mask, int joint, cudaStream_t s);
+// Entries of a tabular policy's Q array and of its visit counts.
+inline long long qtable_size(int S, int nprec, int joint) {
+  return joint ? (long long)S * nprec * nprec * nprec * nprec : 4LL * S * nprec;
+}
+inline long long visits_size(int S, int joint) { return joint ? (long long)S : 4LL * S; }
 
 }  // namespace mpcg

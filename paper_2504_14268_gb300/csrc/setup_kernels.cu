@@ -317,16 +317,33 @@ __global__ void qcopy_kernel(const double* __restrict__ Q, double* Qpriv, int nl
 // operation tables are independent, so one thread per table replays them in that order.
 __global__ void qmerge_kernel(double* Q, int* visits, const Transition* __restrict__ trans,
                               const SysState* __restrict__ st, int nlanes, int cap, int S, int nprec, double lr,
-                              double gamma, OpMask mask, int use_smem) {
+                              double gamma, OpMask mask, int joint, int use_smem) {
   extern __shared__ double tab[];
+  const long long np4 = (long long)nprec * nprec * nprec * nprec;
   const long long tsize = (long long)S * nprec;
+  const long long total = joint ? S * np4 : 4 * tsize;
   double* T = use_smem ? tab : Q;
   if (use_smem) {
-    for (long long i = threadIdx.x; i < 4 * tsize; i += blockDim.x) tab[i] = Q[i];
+    for (long long i = threadIdx.x; i < total; i += blockDim.x) tab[i] = Q[i];
     __syncthreads();
   }
   const int j = threadIdx.x >> 5;
-  if (j < 4 && (threadIdx.x & 31) == 0) {
+  if (joint && threadIdx.x == 0) {  // one table over the joint actions, one update per transition
+    for (int l = 0; l < nlanes; ++l) {
+      int nt = st[l].ntrans;
+      if (nt > cap) nt = cap;
+      for (int t = 0; t < nt; ++t) {
+        const Transition tr = trans[(long long)l * cap + t];
+        const int a = ((tr.act[0] * nprec + tr.act[1]) * nprec + tr.act[2]) * nprec + tr.act[3];
+        double* row = T + tr.s * np4;
+        double target = tr.reward;
+        if (!tr.terminal) target = __dadd_rn(target, __dmul_rn(gamma, joint_row_max(T + tr.s_next * np4, nprec, mask.m)));
+        const double cur = row[a];
+        row[a] = __dadd_rn(cur, __dmul_rn(lr, __dsub_rn(target, cur)));
+        visits[tr.s] += 1;
+      }
+    }
+  } else if (!joint && j < 4 && (threadIdx.x & 31) == 0) {
     double* Tj = T + j * tsize;
     for (int l = 0; l < nlanes; ++l) {
       int nt = st[l].ntrans;
@@ -347,7 +364,7 @@ __global__ void qmerge_kernel(double* Q, int* visits, const Transition* __restri
   }
   if (use_smem) {
     __syncthreads();
-    for (long long i = threadIdx.x; i < 4 * tsize; i += blockDim.x) Q[i] = tab[i];
+    for (long long i = threadIdx.x; i < total; i += blockDim.x) Q[i] = tab[i];
   }
 }
 
@@ -457,12 +474,12 @@ cudaError_t launch_qcopy(const double* Q, double* Qpriv, int nlanes, long long q
 }
 
 cudaError_t launch_qmerge(double* Q, int* visits, const Transition* trans, const SysState* st, int nlanes, int cap,
-                          int S, int nprec, double lr, double gamma, OpMask mask, cudaStream_t s) {
-  const size_t bytes = sizeof(double) * 4 * (size_t)S * nprec;
+                          int S, int nprec, double lr, double gamma, OpMask mask, int joint, cudaStream_t s) {
+  const size_t bytes = sizeof(double) * (size_t)qtable_size(S, nprec, joint);
   const int use_smem = bytes <= 48 * 1024 ? 1 : 0;
   cudaGetLastError();
   qmerge_kernel<<<1, 128, use_smem ? bytes : 0, s>>>(Q, visits, trans, st, nlanes, cap, S, nprec, lr, gamma, mask,
-                                                     use_smem);
+                                                     joint, use_smem);
   return cudaGetLastError();
 }
 

@@ -246,10 +246,35 @@ __device__ __forceinline__ int kth_allowed(unsigned mask, int k) {
   return 0;
 }
 
+// The exploration draws of operation j at iteration k (Philox4x64-10 keyed by the seed, counter
+// (episode, lane, k, j)): u uniform in [0, 1) from 53 bits of the first word, pick the low 32
+// bits of the second.
+__device__ __forceinline__ void policy_draw(const Launch& L, const DevSys& S, int k, int j, double& u, unsigned& pick) {
+  U64x4 c;
+  c.v[0] = L.episode;
+  c.v[1] = (unsigned long long)S.lane;
+  c.v[2] = (unsigned long long)k;
+  c.v[3] = (unsigned long long)j;
+  const U64x4 w = philox4x64_10(c, L.opt.seed, 0x6d706367ull);
+  u = (double)(w.v[0] >> 11) * 0x1.0p-53;
+  pick = (unsigned)(w.v[1] & 0xffffffffull);
+}
+
 // Q_j(s, a_j) += lr (R + gamma max_{p in P_j} Q_j(s', p) - Q_j(s, a_j)), terminal without the max
 // term; P_j = the entries operation j may choose (op_mask).
 __device__ void q_update(double* Q, const OptView& o, const Transition& t) {
   const int S = o.b_bins * o.r_bins;
+  if (o.joint) {  // one entry of the joint table, bootstrap max over the allowed joint actions
+    const int np4 = o.nprec * o.nprec * o.nprec * o.nprec;
+    const int a = ((t.act[0] * o.nprec + t.act[1]) * o.nprec + t.act[2]) * o.nprec + t.act[3];
+    double* row = Q + (long long)t.s * np4;
+    double target = t.reward;
+    if (!t.terminal)
+      target = __dadd_rn(target, __dmul_rn(o.gamma, joint_row_max(Q + (long long)t.s_next * np4, o.nprec, o.op_mask)));
+    const double cur = row[a];
+    row[a] = __dadd_rn(cur, __dmul_rn(o.lr, __dsub_rn(target, cur)));
+    return;
+  }
   for (int j = 0; j < 4; ++j) {
     double* row = Q + ((long long)j * S + t.s) * o.nprec;
     double target = t.reward;
@@ -328,10 +353,54 @@ __device__ void choose_action(const Launch& L, const DevSys& S, SysState* st, in
   }
   if (threadIdx.x == 0) {
     int expl = 0;
+    int jact[4] = {0, 0, 0, 0};
+    if (P.kind == 2 && o.joint && !st->fp64_lock) {
+      // the joint table: exploration decided by operation 1's draw, each operation's pick from
+      // its own draw; greedy: first largest allowed joint entry; unvisited state: the fallback
+      // format for all four operations when each allows it
+      bool done = false;
+      if (L.train) {
+        double u[4];
+        unsigned pick[4];
+        for (int j = 0; j < 4; ++j) policy_draw(L, S, k, j, u[j], pick[j]);
+        if (u[0] < L.eps) {
+          for (int j = 0; j < 4; ++j)
+            jact[j] = kth_allowed((unsigned)o.op_mask[j], (int)(pick[j] % (unsigned)__popc((unsigned)o.op_mask[j])));
+          expl = 1;
+          done = true;
+        }
+      } else {
+        int near = 0;
+        for (int m = 1; m < o.r_bins; ++m) near |= fabs(rho / o.thr[m] - 1.0) <= o.edge_tol ? 1 : 0;
+        st->near_edge += near;
+        if (P.visits && o.fallback_fmt >= 0 && o.fallback_idx >= 0 && P.visits[s] == 0) {
+          bool all = true;
+          for (int j = 0; j < 4; ++j) all = all && (((unsigned)o.op_mask[j] >> o.fallback_idx) & 1u);
+          if (all) {
+            for (int j = 0; j < 4; ++j) jact[j] = o.fallback_idx;
+            done = true;
+          }
+        }
+      }
+      if (!done) {
+        const int np4 = o.nprec * o.nprec * o.nprec * o.nprec;
+        const double* row = (L.train ? S.Qpriv : P.Q) + (long long)s * np4;
+        int best = -1;
+        for (int a = 0; a < np4; ++a)
+          if (joint_allowed(a, o.nprec, o.op_mask) && (best < 0 || row[a] > row[best])) best = a;
+        for (int j = 3; j >= 0; --j) {
+          jact[j] = best % o.nprec;
+          best /= o.nprec;
+        }
+      }
+    }
     for (int j = 0; j < 4; ++j) {
       int fmt, act = -1;
       if (st->fp64_lock) {
         fmt = F64;
+      } else if (P.kind == 2 && o.joint) {
+        act = jact[j];
+        fmt = o.precs[act];
       } else if (P.kind == 0) {
         fmt = P.fixed[j];
       } else if (P.kind == 1) {
@@ -359,15 +428,11 @@ __device__ void choose_action(const Launch& L, const DevSys& S, SysState* st, in
           act = b;
         }
         if (L.train) {
-          U64x4 c;
-          c.v[0] = L.episode;
-          c.v[1] = (unsigned long long)S.lane;
-          c.v[2] = (unsigned long long)k;
-          c.v[3] = (unsigned long long)j;
-          const U64x4 w = philox4x64_10(c, o.seed, 0x6d706367ull);
-          const double u = (double)(w.v[0] >> 11) * 0x1.0p-53;
+          double u;
+          unsigned pick;
+          policy_draw(L, S, k, j, u, pick);
           if (u < L.eps) {
-            act = kth_allowed(mask, (int)((unsigned)(w.v[1] & 0xffffffffull) % (unsigned)__popc(mask)));
+            act = kth_allowed(mask, (int)(pick % (unsigned)__popc(mask)));
             expl = 1;
           }
         }

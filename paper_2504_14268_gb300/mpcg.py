@@ -48,6 +48,7 @@ class COptions(C.Structure):
         ("precond", C.c_int32),
         ("edge_tol", C.c_double),
         ("stepped", C.c_int32), ("variant", C.c_int32),
+        ("joint", C.c_int32), ("reserved_joint", C.c_int32),
     ]
 
 
@@ -204,11 +205,12 @@ class Options:
     edge_tol: float = 5e-3  # greedy decisions this close (relative) to a residual-bin edge are counted
     stepped: int = 0  # single solves: 0 automatic, 1 persistent launch, 2 one kernel per phase in a graph loop
     variant: int = 0  # 0: the CG of Section 3; 1: the single-reduction iteration (lockstep / stepped kernels)
+    joint: int = 0  # tabular policies: 1 = one table over the joint actions, Q[S][nprec^4], visits[S]
 
     def c(self) -> COptions:
         o = COptions()
         for f in fields(self):
-            if f.name in ("precs", "cost", "op_mask"):
+            if f.name in ("precs", "cost", "op_mask", "reserved_joint"):
                 continue
             setattr(o, f.name, getattr(self, f.name))
         if len(self.precs) != len(self.cost):
@@ -287,9 +289,20 @@ class Context:
         self._check(lib().mpcg_policy_schedule(self.handle, _ptr(a), a.shape[0], C.byref(h)))
         return Policy(self, h, "schedule")
 
+    def qtable_shapes(self):
+        """Shapes of a tabular policy's (Q, visits) under this context's options."""
+        o = self.options
+        P = len(o.precs)
+        if o.joint:
+            return (o.n_states, P ** 4), (o.n_states,)
+        return (4, o.n_states, P), (4, o.n_states)
+
     def policy_qtable(self, Q, visits=None) -> "Policy":
         Q = np.ascontiguousarray(Q, dtype=np.float64)
         v = None if visits is None else np.ascontiguousarray(visits, dtype=np.int32)
+        qs, vs = self.qtable_shapes()
+        if Q.size != int(np.prod(qs)) or (v is not None and v.size != int(np.prod(vs))):
+            raise ValueError(f"Q-table must have {qs} entries and visits {vs}")
         h = C.c_void_p()
         self._check(lib().mpcg_policy_qtable(self.handle, _ptr(Q), _ptr(v), C.byref(h)))
         return Policy(self, h, "qtable")
@@ -467,9 +480,9 @@ class Policy:
         self.ctx, self.handle, self.kind = ctx, handle, kind
 
     def qtable(self):
-        o = self.ctx.options
-        Q = np.zeros((4, o.n_states, len(o.precs)))
-        v = np.zeros((4, o.n_states), dtype=np.int32)
+        qs, vs = self.ctx.qtable_shapes()
+        Q = np.zeros(qs)
+        v = np.zeros(vs, dtype=np.int32)
         self.ctx._check(lib().mpcg_policy_get_qtable(self.handle, _ptr(Q), _ptr(v)))
         return Q, v
 

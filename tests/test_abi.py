@@ -41,7 +41,7 @@ def test_struct_layouts():
 
     assert ctypes.sizeof(mpcg.CResult) == 296
     assert mpcg.REC_DTYPE.itemsize == 80
-    assert ctypes.sizeof(mpcg.COptions) == 256
+    assert ctypes.sizeof(mpcg.COptions) == 264
     assert ctypes.sizeof(mpcg.Csr) == 40
 
 
@@ -57,7 +57,7 @@ def test_options_default_matches_paper(lib):
     assert (o.lr, o.gamma, o.eps0, o.eps_floor) == (0.1, 0.9, 1.0, 0.1)
     assert list(o.precs)[:5] == [0, 1, 2, 3, 4]
     assert list(o.cost)[:5] == [0.8, 0.6, 0.8, 1.0, 2.0]
-    assert o.edge_tol == 5e-3 and o.stepped == 0
+    assert o.edge_tol == 5e-3 and o.stepped == 0 and o.variant == 0 and o.joint == 0
     assert L.mpcg_mlp_nparams(64, 5) == 64 * 16 + 64 + 64 * 64 + 64 + 20 * 64 + 20
 
 

@@ -188,6 +188,51 @@ def test_training_one_lane_under_an_operation_mask(M):
     assert np.allclose(Qg, qt.Q, rtol=1e-6, atol=1e-9), float(np.max(np.abs(Qg - qt.Q)))
 
 
+def test_joint_table_training_and_greedy_match_oracle(M):
+    """One Q-table over the joint actions (the |P|^4 alternative that Section 4.1 weighs):
+    four-lane training rounds as in the per-operation test (same systems, same mask, so both
+    sides take the same actions), tables [S][|P|^4] and per-state visits compared; then a
+    greedy solve with the trained table on each lane system, every decision equal to the
+    oracle's unless the library counted it as lying within the history tolerance of a
+    residual-bin edge."""
+    sets = []
+    for i, m in enumerate((20, 26, 32)):
+        A = I.poisson2d(m)
+        xs, b = I.rhs_from_xstar(A, np.random.default_rng(40 + i))
+        sets.append((A, b, xs))
+    precs, cost = (O.FP32, O.FP64), (1.0, 2.0)
+    oo = O.Options(seed=11, min_k=0, precs=precs, cost={O.FP32: 1.0, O.FP64: 2.0}, op_mask=(0b10, 0b11, 0b11, 0b11),
+                   joint=1)
+    E, tmax = 8, 300
+    qt = O.QTable.zeros(oo)
+    assert qt.Q.shape == (oo.n_states, 16) and qt.visits.shape == (oo.n_states,)
+    it_o = np.array([O.train_round(oo, [s[0] for s in sets], [s[1] for s in sets], 1e-6, tmax, e, E, qt)
+                     for e in range(1, E + 1)])
+    ctx = M.Context(0, M.Options(min_k=0, seed=11, precs=precs, cost=cost, op_mask=oo.op_mask, joint=1))
+    mats = [ctx.matrix(_dev(A)) for A, _, _ in sets]
+    bs = [torch.as_tensor(b).cuda() for _, b, _ in sets]
+    qs, vs = ctx.qtable_shapes()
+    pol = ctx.policy_qtable(np.zeros(qs), np.zeros(vs, dtype=np.int32))
+    it_g = ctx.train_qtable(mats, bs, 1e-6, tmax, E, pol, want_iters=True)
+    Qg, vg = pol.qtable()
+    assert np.array_equal(it_g, it_o), (it_g, it_o)
+    assert np.array_equal(vg, qt.visits)
+    # entries of joint actions with the product in fp32 are outside the mask: never updated
+    outside = [a for a in range(16) if (a >> 3) & 1 == 0]
+    assert not Qg[:, outside].any() and not qt.Q[:, outside].any()
+    assert np.allclose(Qg, qt.Q, rtol=1e-6, atol=1e-9), float(np.max(np.abs(Qg - qt.Q)))
+    for (A, b, _), mat in zip(sets, mats):
+        x = torch.zeros(A[0], dtype=torch.float64, device="cuda")
+        r, h = ctx.solve(mat, torch.as_tensor(b).cuda(), x, 1e-6, tmax, pol, history_cap=tmax)
+        ref = O.solve(oo, A, b, 1e-6, tmax, qtable=qt)
+        assert r["outcome"] == ref.outcome == O.CONVERGED
+        n = min(len(h), len(ref.hist), r["iters"])
+        differ = int(np.sum(np.any(h["fmt"][:n] != ref.hist["fmt"][:n], axis=1)))
+        assert differ <= r["near_edge_count"], (differ, r["near_edge_count"])
+        if differ == 0:
+            assert r["iters"] == ref.iters
+
+
 def test_adam_step_matches_oracle(M):
     """mpcg_mlp_adam (the fp32 kernel of mpcg_mlp_train) against the oracle's fp64 Adam on the
     same gradients, one and several steps."""

@@ -263,3 +263,52 @@ def test_greedy_action_is_the_solvers_decision():
         s, fm = O.greedy_action(o, qt, k, rho)
         assert s == rec["state"] and fm == tuple(int(f) for f in rec["fmt"]), k
         rho = rec["rho"]
+
+
+def test_joint_table_equals_the_free_operations_table():
+    """With operations 2-4 restricted to fp64 the joint table's entries (a, fp64, fp64, fp64)
+    are operation 1's table, update for update: the joint set is operation 1's set, its
+    exploration draw and pick are operation 1's, and every target is the same max."""
+    A, b, _ = I.cfg_poisson32()
+    precs, cost = (O.FP32, O.FP64), {O.FP32: 1.0, O.FP64: 2.0}
+    masks = (0b11, 0b10, 0b10, 0b10)
+    sep = O.Options(seed=5, min_k=0, precs=precs, cost=cost, op_mask=masks)
+    jnt = O.Options(seed=5, min_k=0, precs=precs, cost=cost, op_mask=masks, joint=1)
+    qs, qj = O.QTable.zeros(sep), O.QTable.zeros(jnt)
+    it_s = O.train_sequential(sep, A, b, 1e-6, 200, 12, qs)
+    it_j = O.train_sequential(jnt, A, b, 1e-6, 200, 12, qj)
+    assert list(it_s) == list(it_j)
+    assert qj.Q.shape == (100, 16) and qj.visits.shape == (100,)
+    # joint index of (a, fp64, fp64, fp64) = a * 8 + 1 * 4 + 1 * 2 + 1
+    assert np.array_equal(qj.Q[:, [7, 15]], qs.Q[0])
+    assert np.array_equal(qj.visits, qs.visits[0])
+    out_s = O.solve(sep, A, b, 1e-6, 200, qtable=qs)
+    out_j = O.solve(jnt, A, b, 1e-6, 200, qtable=qj)
+    assert np.array_equal(out_s.hist["fmt"], out_j.hist["fmt"])
+
+
+def test_joint_table_one_step_closed_form_and_bellman_chain():
+    """A = 2 I converges in one step: the greedy joint action on a zero table is the first
+    joint index (all fp16), and after m episodes Q(s_0, 0) = (1 - (1 - lr)^m) R, R = 25.68.
+    A chain s0 -> s1 -> end with rewards (1, 5) on joint action (fp32, fp32, fp32, fp32):
+    Q(s1) = 5, Q(s0) = 1 + 0.9 * 5 (the max over the joint row of s1)."""
+    A = _scaled_identity()
+    b = np.arange(1.0, 9.0)
+    o = O.Options(min_k=0, eps0=0.0, eps_floor=0.0, joint=1)
+    qt = O.QTable.zeros(o)
+    m = 15
+    O.train_sequential(o, A, b, 1e-6, 50, m, qt)
+    s0 = O.state(o, 0, 1.0)
+    assert qt.Q[s0, 0] == pytest.approx((1 - 0.9 ** m) * 25.68, rel=1e-12)
+    assert qt.visits[s0] == m and np.count_nonzero(qt.Q) == 1
+    o2 = O.Options(joint=1)
+    q2 = O.QTable.zeros(o2)
+    chain = np.zeros(2, dtype=O.TRANS_DTYPE)
+    for t, (s, sn, r, term) in enumerate([(0, 1, 1.0, 0), (1, 1, 5.0, 1)]):
+        chain[t]["s"], chain[t]["s_next"], chain[t]["reward"], chain[t]["terminal"] = s, sn, r, term
+        chain[t]["act"] = [3, 3, 3, 3]
+    for _ in range(400):
+        O.q_update(o2, q2, chain)
+    a = ((3 * 5 + 3) * 5 + 3) * 5 + 3
+    assert q2.Q[[0, 1], a] == pytest.approx([1 + 0.9 * 5.0, 5.0], rel=1e-9)
+    assert np.count_nonzero(q2.Q) == 2
