@@ -710,7 +710,7 @@ def main():
             "e2e": {"value": args.steps / e2e_T, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                     "d2h_bytes_per_step": 8 * n + 296},
             "cpu_baseline": cpu,
-            "gpu_launches": args.steps,
+            "gpu_launches": int(sum(r["kernel_launches"] for r in results)),
             "clocks": clk.summary(),
             "setup_s": {"generate": round(t_gen, 1), "matrix_create": round(t_setup, 2), "autotune": round(t_tune, 2),
                         "train_policy": round(t_train, 2)},

@@ -184,7 +184,10 @@ typedef struct {
   int64_t action_hist[MPCG_NUM_OPS][MPCG_MAX_PREC]; /* iterations per (op, format)       */
   int32_t near_edge_count; /* greedy tabular decisions taken within edge_tol of a residual-bin
                               edge (options.edge_tol); 0 for other policies             */
-  int32_t reserved;
+  int32_t kernel_launches; /* the library's solver-kernel launches of the call: 1 for one
+                              persistent or lockstep launch (shared by a batch), passes x
+                              kernels for the stepped solve (the phase kernels and the loop
+                              control kernel of every pass of the graph)               */
 } mpcg_result;
 
 /* One record per iteration k (80 bytes). rho is rho_{k+1} after the iteration (the true

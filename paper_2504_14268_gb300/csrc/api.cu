@@ -72,6 +72,7 @@ struct Plan {
   bool lockstep = false;
   bool stepped = false;      // one system, one kernel per phase in a while-loop graph
   bool stepped_host = false; // ... the passes launched by the host instead (option stepped = 3)
+  unsigned host_passes = 0;  // passes the host launched (stepped_host)
   int sgrid[kPhaseKernels] = {0, 0, 0, 0, 0, 0};
   size_t ssmem = 0;
   cudaGraphExec_t sexec = nullptr;
@@ -615,8 +616,10 @@ mpcg_status enqueue_plan(mpcg_ctx_t ctx, Plan& pl, cudaStream_t s) {
       // that do not follow kernels inside graphs with conditional nodes); bounded like the graph
       int phase = 0;
       unsigned herr = 0;
+      pl.host_passes = 0;
       for (unsigned pass = 0; pass < limit; ++pass) {
         CK(ctx, stepped_pass(pl.L, pl.sgrid, pl.ssmem, s));
+        pl.host_passes = pass + 1;
         CK(ctx, cudaMemcpyAsync(&phase, &pl.L.st->phase, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(ctx, cudaMemcpyAsync(&herr, pl.L.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CK(ctx, cudaStreamSynchronize(s));
@@ -650,9 +653,18 @@ mpcg_status finish_plan(mpcg_ctx_t ctx, Plan& pl, mpcg_result* res, cudaStream_t
   pl.hres.resize(std::max(pl.nsys, 1));
   if (pl.nsys) CK(ctx, cudaMemcpyAsync(pl.hres.data(), pl.res.p, sizeof(mpcg_result) * pl.nsys, cudaMemcpyDeviceToHost, s));
   CK(ctx, cudaMemcpyAsync(&herr, pl.err.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  unsigned passes = 0;  // the stepped graph's pass counter (bars[16], kept by its control kernel)
+  if (pl.stepped && !pl.stepped_host)
+    CK(ctx, cudaMemcpyAsync(&passes, pl.bars.as<unsigned>() + 16, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   CK(ctx, cudaStreamSynchronize(s));
   if (herr == DERR_TIMEOUT) return fail(ctx, MPCG_ERR_TIMEOUT, "a device-side barrier wait exceeded its limit");
   if (herr) return fail(ctx, MPCG_ERR_INTERNAL, "device status word %u", herr);
+  int launches = 1;
+  if (pl.stepped) {
+    const int nbody = pl.L.opt.variant ? 3 : 4;  // phase kernels per pass (stepped.cu)
+    launches = pl.stepped_host ? (int)pl.host_passes * nbody : (int)passes * (nbody + 1);
+  }
+  for (int i = 0; i < pl.nsys; ++i) pl.hres[i].kernel_launches = launches;
   if (res && pl.nsys) memcpy(res, pl.hres.data(), sizeof(mpcg_result) * pl.nsys);
   return MPCG_OK;
 }
@@ -1893,6 +1905,7 @@ mpcg_status mpcg_solve_noalloc(mpcg_ctx_t ctx, mpcg_matrix_t A, const double* b,
   CK(ctx, cudaStreamSynchronize(s));
   if (herr == DERR_TIMEOUT) return fail(ctx, MPCG_ERR_TIMEOUT, "a device-side barrier wait exceeded its limit");
   if (herr) return fail(ctx, MPCG_ERR_INTERNAL, "device status word %u", herr);
+  res->kernel_launches = 1;
   return MPCG_OK;
 }
 

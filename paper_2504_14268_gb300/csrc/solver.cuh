@@ -1077,7 +1077,7 @@ __device__ void step_final(const Launch& L, const DevSys& S, SysState* st, int s
   for (int j = 0; j < 4; ++j)
     for (int f = 0; f < 8; ++f) res.action_hist[j][f] = st->counts[j][f];
   res.near_edge_count = st->near_edge;
-  res.reserved = 0;
+  res.kernel_launches = 0;
   L.res[sid] = res;
 }
 

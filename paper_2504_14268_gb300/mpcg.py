@@ -55,7 +55,8 @@ class COptions(C.Structure):
 class CResult(C.Structure):
     _fields_ = [("outcome", C.c_int32), ("iters", C.c_int32), ("rel_res_rec", C.c_double),
                 ("rel_res_true", C.c_double), ("n_true_checks", C.c_int32), ("n_restarts", C.c_int32),
-                ("action_hist", (C.c_int64 * 8) * 4), ("near_edge_count", C.c_int32), ("reserved", C.c_int32)]
+                ("action_hist", (C.c_int64 * 8) * 4), ("near_edge_count", C.c_int32),
+                ("kernel_launches", C.c_int32)]
 
 
 class CStats(C.Structure):
@@ -231,7 +232,8 @@ class Options:
 def result_dict(r: CResult) -> dict:
     return dict(outcome=r.outcome, iters=r.iters, rel_res_rec=r.rel_res_rec, rel_res_true=r.rel_res_true,
                 n_true_checks=r.n_true_checks, n_restarts=r.n_restarts,
-                action_hist=np.array([list(row) for row in r.action_hist]), near_edge_count=r.near_edge_count)
+                action_hist=np.array([list(row) for row in r.action_hist]), near_edge_count=r.near_edge_count,
+                kernel_launches=r.kernel_launches)
 
 
 class Context:

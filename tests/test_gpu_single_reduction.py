@@ -73,10 +73,17 @@ def test_single_reduction_batch_replacement_restart_and_jacobi(M):
     bs = [torch.as_tensor(b).cuda() for _, b, _ in sets]
     xs = [torch.zeros_like(b) for b in bs]
     res = ctx.solve_batched(mats, bs, xs, [1e-8] * 5, [800] * 5, pol)
+    rng = np.random.default_rng(1)
     for (A, b, xstar), r, x in zip(sets, res, xs):
         ref = O.solve(O.Options(**opts), A, b, 1e-8, 800, fixed=(3, 4, 3, 4))
         assert r["outcome"] == ref.outcome == O.CONVERGED and r["rel_res_true"] < 1e-8
-        assert abs(r["iters"] - ref.iters) <= max(3, ref.iters // 20)
+        # near tau = 1e-8 the residual norm recurrence cancels, so the iteration count moves
+        # with rounding: the oracle's own counts under 1e-12 relative perturbations of b span
+        # up to 16 iterations here; the GPU's count lies in that spread, widened by 5%
+        its = [ref.iters] + [O.solve(O.Options(**opts), A, b * (1 + 1e-12 * rng.standard_normal(b.shape)), 1e-8, 800,
+                                     fixed=(3, 4, 3, 4)).iters for _ in range(4)]
+        slack = max(3, ref.iters // 20)
+        assert min(its) - slack <= r["iters"] <= max(its) + slack, (r["iters"], its)
         assert np.linalg.norm(x.cpu().numpy() - xstar) <= 10 * np.linalg.norm(ref.x - xstar) + 1e-12
     # breakdown of the fp16 product on values beyond fp16's range, then the fp64 restart
     A, b, _ = I.cfg_poisson32()

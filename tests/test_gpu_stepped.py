@@ -75,6 +75,10 @@ def test_stepped_fixed_policy_matches_oracle_and_persistent(M, case, fmts, tol):
         m = res["iters"]
         assert np.all(np.abs(hp["rho"][:m] - hist["rho"][:m]) <= 1e-9 * hist["rho"][:m])
     assert np.all(hist["ns_a"][:n] > 0) and np.all(hist["ns_b"][:n] > 0)
+    # launches: one persistent kernel; the graph runs four phase kernels and the control
+    # kernel per pass, at least one pass per iteration plus the initialisation
+    assert rp_["kernel_launches"] == 1
+    assert res["kernel_launches"] % 5 == 0 and res["kernel_launches"] >= 5 * (res["iters"] + 1)
 
 
 def test_stepped_greedy_qtable_with_replacement_and_restart(M):
