@@ -58,7 +58,7 @@ TRAIN_SET = [(24, 1e-3), (28, 1e-3), (32, 1e-3), (36, 1e-3), (40, 1e-3), (44, 1e
              (40, 1e-2), (48, 3e-3), (30, 3e-3), (36, 1e-2), (26, 1e-3), (34, 3e-3), (42, 1e-3), (46, 1e-2)]
 TRAIN_ROUNDS = 150
 TRAIN_SEED = 3
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_cg_persistent_fem27_128.md")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_solve_fem27_128.md")
 
 
 @contextlib.contextmanager

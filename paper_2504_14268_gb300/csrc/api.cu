@@ -104,6 +104,8 @@ struct mpcg_matrix_s {
   DevBuf rp, ci, v64, v32, vtf, v16, vbf, v16r, vbfr, v8, rexp, dinv;
   bool diag_ok = false;             // every row has a positive diagonal entry (Jacobi defined)
   DevBuf icf, icd;                  // IC(0) factor (fp32, one value per stored entry), diagonal positions
+  DevBuf icpf, icpb;                // IC(0): rows in level order of the two substitutions
+  int icwf = 0, icwb = 0;           // ... and the widest level's row count
   unsigned ic_fail = 0;             // 0: not factored or factored fine; else the factorization's error bits
   bool ic_ready = false;
   int device = 0;
@@ -386,8 +388,44 @@ mpcg_status ensure_ic0(mpcg_ctx_t ctx, mpcg_matrix_s* M, cudaStream_t s) {
     M->ic_fail = bits;
     return ic0_error(ctx, bits);
   }
+  // level schedule of the substitutions (host pass over the pattern): rows sorted by level,
+  // stable in the row index
+  std::vector<int> hrp(n + 1), hci((size_t)std::max(nnz, 1LL)), hdp(std::max(n, 1));
+  CK(ctx, cudaMemcpy(hrp.data(), M->dm.rp, 4 * (size_t)(n + 1), cudaMemcpyDeviceToHost));
+  if (nnz) CK(ctx, cudaMemcpy(hci.data(), M->dm.ci, 4 * (size_t)nnz, cudaMemcpyDeviceToHost));
+  if (n) CK(ctx, cudaMemcpy(hdp.data(), M->icd.p, 4 * (size_t)n, cudaMemcpyDeviceToHost));
+  std::vector<int> lev(std::max(n, 1)), perm(std::max(n, 1));
+  auto sort_by_level = [&](int depth, DevBuf& out, int& width) -> mpcg_status {
+    std::vector<int> cnt(depth + 1, 0);
+    for (int i = 0; i < n; ++i) ++cnt[lev[i] + 1];
+    width = 0;
+    for (int l = 0; l < depth; ++l) width = std::max(width, cnt[l + 1]);
+    for (int l = 0; l < depth; ++l) cnt[l + 1] += cnt[l];
+    for (int i = 0; i < n; ++i) perm[cnt[lev[i]]++] = i;
+    CK(ctx, out.ensure(4 * (size_t)std::max(n, 1)));
+    if (n) CK(ctx, cudaMemcpy(out.p, perm.data(), 4 * (size_t)n, cudaMemcpyHostToDevice));
+    return MPCG_OK;
+  };
+  int depth = 0;
+  for (int i = 0; i < n; ++i) {  // L y = r: row i reads y_j, j < i, over its lower entries
+    int l = 0;
+    for (int e = hrp[i]; e < hdp[i]; ++e) l = std::max(l, lev[hci[e]] + 1);
+    lev[i] = l;
+    depth = std::max(depth, l + 1);
+  }
+  mpcg_status ls = sort_by_level(depth, M->icpf, M->icwf);
+  if (ls != MPCG_OK) return ls;
+  depth = 0;
+  for (int i = n - 1; i >= 0; --i) {  // L^T w = y: row i reads w_j, j > i, over its upper entries
+    int l = 0;
+    for (int e = hdp[i] + 1; e < hrp[i + 1]; ++e) l = std::max(l, lev[hci[e]] + 1);
+    lev[i] = l;
+    depth = std::max(depth, l + 1);
+  }
+  ls = sort_by_level(depth, M->icpb, M->icwb);
+  if (ls != MPCG_OK) return ls;
   M->ic_ready = true;
-  M->bytes += 4 * nnz + 4LL * n;
+  M->bytes += 4 * nnz + 12LL * n;
   return MPCG_OK;
 }
 
@@ -471,6 +509,10 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
     d.A.dinv = ctx->opt.precond == 1 ? in[i].A->dinv.as<double>() : nullptr;
     d.A.icf = ic ? in[i].A->icf.as<float>() : nullptr;
     d.A.icd = ic ? in[i].A->icd.as<int>() : nullptr;
+    d.A.icpf = ic ? in[i].A->icpf.as<int>() : nullptr;
+    d.A.icpb = ic ? in[i].A->icpb.as<int>() : nullptr;
+    d.A.icwf = ic ? in[i].A->icwf : 0;
+    d.A.icwb = ic ? in[i].A->icwb : 0;
     const int n = d.A.n;
     d.b = in[i].b;
     d.x = in[i].x;

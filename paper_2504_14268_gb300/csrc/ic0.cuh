@@ -101,14 +101,29 @@ __device__ __forceinline__ bool ic_accumulate(const int* __restrict__ ci, const 
   return true;
 }
 
-// w = M^-1 fl32(r) over the rows of R for one application with epoch `ep` (marks 2 ep + 1
-// on y_i after the forward row, 2 ep + 2 on w_i after the backward row; the words start at
-// 0 for a launch and the marks only grow). Both substitutions run in fp32 with each row's
-// sum over its stored columns in increasing order and one correctly rounded division by
-// l_ii, so the result equals a sequential evaluation bit for bit. y and w share the work
-// vector: row i overwrites y_i only after every row that reads y_i has finished its own
-// backward step. consume(i, r_i, w_i) runs for every row of R once w_i is final. Starts
-// and ends with a CTA barrier (r written by other threads of the CTA is read here).
+// Threads of a substitution: about two levels' worth of rows (whole warps), at most the
+// group's threads. Thread t of the group takes the positions t, t + T, t + 2T, ... of the
+// level order, so that every thread works within a few levels of the front.
+__device__ __forceinline__ int ic_threads(int width, int ng) {
+  const int want = ((2 * width + 31) / 32) * 32;
+  const int have = ng * kThreads;
+  return want < 32 ? 32 : (want < have ? want : have);
+}
+
+// w = M^-1 fl32(r) for one application with epoch `ep`, run by the ng CTAs that hold rows of
+// the system (this CTA is number R.g; R is its own row range). Marks in the high word of each
+// row's 64-bit word: 3 ep + 1 when fl32(r_i) is published (by the CTA holding row i, which
+// wrote r_i), 3 ep + 2 when y_i is, 3 ep + 3 when w_i is; the words start at 0 for a launch and
+// the marks only grow. Both substitutions run in fp32 with each row's sum over its stored
+// columns in increasing order and one correctly rounded division by l_ii, so the result
+// equals a sequential evaluation bit for bit. The rows are taken in level order (icpf for
+// L y = r, icpb for L^T w = y): a row's inputs lie in lower levels, hence at earlier
+// positions, so the earliest unfinished position always has its inputs and the group, resident
+// by the cooperative launch, makes progress; the threads near the front are the only ones
+// waiting, which keeps the polling small. y and w share the word: row i overwrites y_i with
+// w_i only after every row that reads y_i has published its w (they are exactly the rows its
+// backward step waits on, the pattern being symmetric). consume(i, r_i, w_i) runs once per row
+// on the thread that finishes w_i. Starts and ends with a CTA barrier.
 //
 // Waiting never diverges inside a warp: a warp loops as a whole; in each round every lane
 // extends its current row's sum over the inputs that are ready, finishing the row when all
@@ -124,17 +139,21 @@ __device__ __forceinline__ void ic_apply(const DevSys& S, Rows R, unsigned ep, u
   const float* __restrict__ Lf = S.A.icf;
   const int* __restrict__ dp = S.A.icd;
   unsigned long long* W = S.icw;
-  const unsigned tf = 2u * ep + 1u, tb = 2u * ep + 2u;
+  const int n = S.A.n;
+  const unsigned tr = 3u * ep + 1u, tf = 3u * ep + 2u, tb = 3u * ep + 3u;
+  // publish fl32(r_i) of this CTA's rows (r written by this CTA's threads before the barrier)
+  __threadfence();
   __syncthreads();
+  for (int i = R.r0 + (int)threadIdx.x; i < R.r1; i += kThreads)
+    st_relaxed64(W + i, ic_word(__double2float_rn(S.r[i]), tr));
   bool bad = *(volatile unsigned*)err != 0u;
-  const int cnt = R.r1 - R.r0 > (int)threadIdx.x ? (R.r1 - R.r0 - (int)threadIdx.x + kThreads - 1) / kThreads : 0;
+  const int gt = R.g * kThreads + (int)threadIdx.x;  // this thread in the group
   unsigned rounds = 0, nap = 0;
   long long t_last = clock64();
-  // a round without progress in the whole warp: back off (up to about a microsecond, so that
-  // waiting warps leave the memory system to the rows being finished), check the status
-  // word now and then, and the time since the warp last moved
+  // a round without progress in the whole warp: back off briefly, check the status word now
+  // and then, and the time since the warp last moved
   auto idle = [&]() {
-    nap = nap ? min(2u * nap, 1024u) : 32u;
+    nap = nap ? min(2u * nap, 256u) : 32u;
     __nanosleep(nap);
     if ((++rounds & 63u) != 0u) return;
     if (*(volatile unsigned*)err != 0u) {
@@ -144,30 +163,40 @@ __device__ __forceinline__ void ic_apply(const DevSys& S, Rows R, unsigned ep, u
       bad = true;
     }
   };
-  // forward: L y = fl32(r), this thread's rows in increasing order
+  // forward: L y = fl32(r), positions gt, gt + T, ... of the forward level order
   {
-    int m = 0, ea = 0, eb = 0;
+    const int T = ic_threads(S.A.icwf, R.ng);
+    const int cnt = gt < T ? (n - gt + T - 1) / T : 0;
+    int m = 0, ea = 0, eb = 0, i = 0;
     float s = 0.f;
-    bool fresh = true;
+    int stage = 0;  // 0: new row, 1: waiting for fl32(r_i), 2: summing
     while (__any_sync(kFull, m < cnt)) {
       bool moved = false;
       if (m < cnt) {
-        const int i = R.r0 + (int)threadIdx.x + m * kThreads;
-        const bool fresh_row = fresh;
-        if (fresh) {
+        if (stage == 0) {
+          i = __ldg(S.A.icpf + gt + m * T);
           ea = __ldg(rp + i);
           eb = __ldg(dp + i);
-          s = __double2float_rn(S.r[i]);
-          fresh = false;
+          stage = 1;
         }
-        const int e_before = ea;
-        if (ic_accumulate(ci, Lf, W, ea, eb, bad ? 0u : tf, s, !fresh_row)) {
-          st_relaxed64(W + i, ic_word(__fdiv_rn(s, __ldg(Lf + eb)), tf));
-          ++m;
-          fresh = true;
-          moved = true;
-        } else {
-          moved = ea != e_before;
+        if (stage == 1) {
+          const unsigned long long w = ld_relaxed64(W + i);
+          if (bad || ic_mark(w) >= tr) {
+            s = ic_value(w);
+            stage = 2;
+            moved = true;
+          }
+        }
+        if (stage == 2) {
+          const int e_before = ea;
+          if (ic_accumulate(ci, Lf, W, ea, eb, bad ? 0u : tf, s, !moved)) {
+            st_relaxed64(W + i, ic_word(__fdiv_rn(s, __ldg(Lf + eb)), tf));
+            ++m;
+            stage = 0;
+            moved = true;
+          } else {
+            moved = moved || ea != e_before;
+          }
         }
       }
       if (__any_sync(kFull, moved)) {
@@ -178,33 +207,43 @@ __device__ __forceinline__ void ic_apply(const DevSys& S, Rows R, unsigned ep, u
       }
     }
   }
-  // backward: L^T w = y, this thread's rows in decreasing order
+  // backward: L^T w = y, positions gt, gt + T, ... of the backward level order
   {
-    int m = cnt - 1, ea = 0, eb = 0, di = 0;
+    const int T = ic_threads(S.A.icwb, R.ng);
+    const int cnt = gt < T ? (n - gt + T - 1) / T : 0;
+    int m = 0, ea = 0, eb = 0, di = 0, i = 0;
     float s = 0.f;
-    bool fresh = true;
-    while (__any_sync(kFull, m >= 0)) {
+    int stage = 0;  // 0: new row, 1: waiting for y_i, 2: summing
+    while (__any_sync(kFull, m < cnt)) {
       bool moved = false;
-      if (m >= 0) {
-        const int i = R.r0 + (int)threadIdx.x + m * kThreads;
-        const bool fresh_row = fresh;
-        if (fresh) {
+      if (m < cnt) {
+        if (stage == 0) {
+          i = __ldg(S.A.icpb + gt + m * T);
           di = __ldg(dp + i);
           ea = di + 1;
           eb = __ldg(rp + i + 1);
-          s = ic_value(ld_relaxed64(W + i));  // y_i, written by this thread
-          fresh = false;
+          stage = 1;
         }
-        const int e_before = ea;
-        if (ic_accumulate(ci, Lf, W, ea, eb, bad ? 0u : tb, s, !fresh_row)) {
-          const float w = __fdiv_rn(s, __ldg(Lf + di));
-          st_relaxed64(W + i, ic_word(w, tb));
-          consume(i, S.r[i], (double)w);
-          --m;
-          fresh = true;
-          moved = true;
-        } else {
-          moved = ea != e_before;
+        if (stage == 1) {
+          const unsigned long long w = ld_relaxed64(W + i);
+          if (bad || ic_mark(w) >= tf) {
+            s = ic_value(w);
+            stage = 2;
+            moved = true;
+          }
+        }
+        if (stage == 2) {
+          const int e_before = ea;
+          if (ic_accumulate(ci, Lf, W, ea, eb, bad ? 0u : tb, s, !moved)) {
+            const float w = __fdiv_rn(s, __ldg(Lf + di));
+            st_relaxed64(W + i, ic_word(w, tb));
+            consume(i, __ldcg(S.r + i), (double)w);
+            ++m;
+            stage = 0;
+            moved = true;
+          } else {
+            moved = moved || ea != e_before;
+          }
         }
       }
       if (__any_sync(kFull, moved)) {

@@ -47,6 +47,9 @@ struct DevMatrix {
   const float* icf;         // IC(0) factor in fp32 when the launch preconditions with it, else
                             // nullptr: l_ij at (i, j) for j <= i, l_ji at (i, j) for j > i
   const int* icd;           // IC(0): position of the diagonal entry of each row
+  const int* icpf;          // IC(0): the rows sorted by level of L y = r (level 0 first), then
+  const int* icpb;          // ... of L^T w = y; a row's level is 1 + the largest level of the rows
+  int icwf, icwb;           // its sum reads (0 if none); icw*: the widest level's row count
 };
 
 // One transition of an exploration episode (Algorithm 1), recorded for the end-of-round merge.

@@ -1414,7 +1414,7 @@ __device__ __forceinline__ bool solve_system(const Launch& L, const TeamCtx& T, 
     sm.r1 = part_row(S.A.rp, S.A.n, S.A.nnz, T.rank + 1, T.size);
   }
   __syncthreads();
-  const Rows R{sm.r0, sm.r1};
+  const Rows R{sm.r0, sm.r1, T.rank, T.size};
 
   // ---- initialisation: x_0, r_0 = b - A x_0, p_0 = z_0 = M^-1 r_0, ||b||^2, ||r_0||^2,
   //      sigma_0 = r_0^T z_0 ----
@@ -2112,7 +2112,10 @@ __global__ void __launch_bounds__(kThreads, 4) cg_lockstep(const Launch L) {
     const int nseg = L.lk_nseg[blockIdx.x];
     for (int i = 0; i < nseg; ++i) {
       const int4 sg = L.lk_seg[(long long)blockIdx.x * (L.nsys + 1) + i];
-      lk_slice_rows<IC>(L, sg.x, Rows{sg.y, sg.z}, sg.w, sm, sc);
+      // the system's slices sit on its CTA range, one per CTA: this slice's index and count
+      const int sg_g = sg.w - L.lk_base[sg.x];
+      const int sg_n = L.lk_clast[sg.x] - L.lk_cfirst[sg.x] + 1;
+      lk_slice_rows<IC>(L, sg.x, Rows{sg.y, sg.z, sg_g, sg_n}, sg.w, sm, sc);
     }
     if (!grid_sync(L, G, sm)) return;
     for (int s = blockIdx.x; s < L.nsys; s += gridDim.x) lk_step(L, s, sm);

@@ -12,6 +12,7 @@ constexpr unsigned kFull = 0xffffffffu;
 
 struct Rows {
   int r0, r1;
+  int g = 0, ng = 1;  // IC(0) substitutions: this CTA's index among the CTAs holding the system
 };
 
 // Read-only load of a stored value (the q52 byte through its unsigned char form).
