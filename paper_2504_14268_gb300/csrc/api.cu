@@ -105,7 +105,9 @@ struct mpcg_matrix_s {
   bool diag_ok = false;             // every row has a positive diagonal entry (Jacobi defined)
   DevBuf icf, icd;                  // IC(0) factor (fp32, one value per stored entry), diagonal positions
   DevBuf icpf, icpb;                // IC(0): rows in level order of the two substitutions
-  int icwf = 0, icwb = 0;           // ... and the widest level's row count
+  DevBuf icof, icob;                // ... the start of each level in them
+  int icwf = 0, icwb = 0;           // ... the widest level's row count
+  int nlevf = 0, nlevb = 0;         // ... and the number of levels
   unsigned ic_fail = 0;             // 0: not factored or factored fine; else the factorization's error bits
   bool ic_ready = false;
   int device = 0;
@@ -395,12 +397,15 @@ mpcg_status ensure_ic0(mpcg_ctx_t ctx, mpcg_matrix_s* M, cudaStream_t s) {
   if (nnz) CK(ctx, cudaMemcpy(hci.data(), M->dm.ci, 4 * (size_t)nnz, cudaMemcpyDeviceToHost));
   if (n) CK(ctx, cudaMemcpy(hdp.data(), M->icd.p, 4 * (size_t)n, cudaMemcpyDeviceToHost));
   std::vector<int> lev(std::max(n, 1)), perm(std::max(n, 1));
-  auto sort_by_level = [&](int depth, DevBuf& out, int& width) -> mpcg_status {
+  auto sort_by_level = [&](int depth, DevBuf& out, DevBuf& starts, int& width, int& nlev) -> mpcg_status {
     std::vector<int> cnt(depth + 1, 0);
     for (int i = 0; i < n; ++i) ++cnt[lev[i] + 1];
     width = 0;
     for (int l = 0; l < depth; ++l) width = std::max(width, cnt[l + 1]);
     for (int l = 0; l < depth; ++l) cnt[l + 1] += cnt[l];
+    CK(ctx, starts.ensure(4 * (size_t)(depth + 1)));
+    CK(ctx, cudaMemcpy(starts.p, cnt.data(), 4 * (size_t)(depth + 1), cudaMemcpyHostToDevice));
+    nlev = depth;
     for (int i = 0; i < n; ++i) perm[cnt[lev[i]]++] = i;
     CK(ctx, out.ensure(4 * (size_t)std::max(n, 1)));
     if (n) CK(ctx, cudaMemcpy(out.p, perm.data(), 4 * (size_t)n, cudaMemcpyHostToDevice));
@@ -413,7 +418,7 @@ mpcg_status ensure_ic0(mpcg_ctx_t ctx, mpcg_matrix_s* M, cudaStream_t s) {
     lev[i] = l;
     depth = std::max(depth, l + 1);
   }
-  mpcg_status ls = sort_by_level(depth, M->icpf, M->icwf);
+  mpcg_status ls = sort_by_level(depth, M->icpf, M->icof, M->icwf, M->nlevf);
   if (ls != MPCG_OK) return ls;
   depth = 0;
   for (int i = n - 1; i >= 0; --i) {  // L^T w = y: row i reads w_j, j > i, over its upper entries
@@ -422,7 +427,7 @@ mpcg_status ensure_ic0(mpcg_ctx_t ctx, mpcg_matrix_s* M, cudaStream_t s) {
     lev[i] = l;
     depth = std::max(depth, l + 1);
   }
-  ls = sort_by_level(depth, M->icpb, M->icwb);
+  ls = sort_by_level(depth, M->icpb, M->icob, M->icwb, M->nlevb);
   if (ls != MPCG_OK) return ls;
   M->ic_ready = true;
   M->bytes += 4 * nnz + 12LL * n;
@@ -513,6 +518,10 @@ mpcg_status build_plan(mpcg_ctx_t ctx, Plan& pl, const std::vector<SysIn>& in, m
     d.A.icpb = ic ? in[i].A->icpb.as<int>() : nullptr;
     d.A.icwf = ic ? in[i].A->icwf : 0;
     d.A.icwb = ic ? in[i].A->icwb : 0;
+    d.A.icof = ic ? in[i].A->icof.as<int>() : nullptr;
+    d.A.icob = ic ? in[i].A->icob.as<int>() : nullptr;
+    d.A.nlevf = ic ? in[i].A->nlevf : 0;
+    d.A.nlevb = ic ? in[i].A->nlevb : 0;
     const int n = d.A.n;
     d.b = in[i].b;
     d.x = in[i].x;

@@ -75,17 +75,10 @@ __device__ __forceinline__ unsigned ic_mark(unsigned long long w) { return (unsi
 // Continues the row sum s -= l_e v_col(e) over e = ea, ea + 1, ... < eb in order, eight
 // words per memory round trip, as long as the rows read carry a mark >= target. True when
 // the sum is complete; otherwise ea and s hold the progress for the next attempt (the order
-// of the terms never changes). A retry first reads only the word it stopped at, so that
-// waiting rows add one load per round to the lines being polled.
+// of the terms never changes).
 __device__ __forceinline__ bool ic_accumulate(const int* __restrict__ ci, const float* __restrict__ Lf,
                                               const unsigned long long* W, int& ea, int eb, unsigned target,
-                                              float& s, bool retry) {
-  if (retry && ea < eb) {
-    const unsigned long long w = ld_relaxed64(W + __ldg(ci + ea));
-    if (ic_mark(w) < target) return false;
-    s = __fsub_rn(s, __fmul_rn(__ldg(Lf + ea), ic_value(w)));
-    ++ea;
-  }
+                                              float& s) {
   while (ea < eb) {
     unsigned long long w[8];
 #pragma unroll
@@ -99,6 +92,61 @@ __device__ __forceinline__ bool ic_accumulate(const int* __restrict__ ci, const 
     }
   }
   return true;
+}
+
+// Both substitutions by one CTA, level by level (ic_apply for systems whose levels hold at
+// most half a CTA's threads' worth of rows). Row i of a level waits (bounded) only for the mark
+// of its own fl32(r_i), published by the CTA holding the row; the values of earlier levels were
+// stored by this CTA before the barrier that ends their level.
+template <class F>
+__device__ __noinline__ void ic_levels_cta(const DevSys& S, unsigned ep, unsigned* err, unsigned tbit,
+                                           long long limit, bool bad, F&& consume) {
+  const int* __restrict__ rp = S.A.rp;
+  const int* __restrict__ ci = S.A.ci;
+  const float* __restrict__ Lf = S.A.icf;
+  const int* __restrict__ dp = S.A.icd;
+  unsigned long long* W = S.icw;
+  const unsigned tr = 3u * ep + 1u, tf = 3u * ep + 2u, tb = 3u * ep + 3u;
+  for (int l = 0; l < S.A.nlevf; ++l) {
+    const int a = __ldg(S.A.icof + l), b = __ldg(S.A.icof + l + 1);
+    for (int x = a + (int)threadIdx.x; x < b; x += kThreads) {
+      const int i = __ldg(S.A.icpf + x);
+      unsigned long long w = ld_relaxed64(W + i);
+      if (ic_mark(w) < tr && !bad) {
+        const long long t0 = clock64();
+        unsigned spins = 0;
+        while (ic_mark(w = ld_relaxed64(W + i)) < tr) {
+          __nanosleep(64);
+          if ((++spins & 63u) == 0u) {
+            if (*(volatile unsigned*)err != 0u) break;
+            if (clock64() - t0 > limit) {
+              atomicOr(err, tbit);
+              break;
+            }
+          }
+        }
+      }
+      float s = ic_value(w);
+      const int e1 = __ldg(dp + i);
+      for (int e = __ldg(rp + i); e < e1; ++e)
+        s = __fsub_rn(s, __fmul_rn(__ldg(Lf + e), ic_value(W[__ldg(ci + e)])));
+      W[i] = ic_word(__fdiv_rn(s, __ldg(Lf + e1)), tf);
+    }
+    __syncthreads();
+  }
+  for (int l = 0; l < S.A.nlevb; ++l) {
+    const int a = __ldg(S.A.icob + l), b = __ldg(S.A.icob + l + 1);
+    for (int x = a + (int)threadIdx.x; x < b; x += kThreads) {
+      const int i = __ldg(S.A.icpb + x);
+      const int di = __ldg(dp + i), e1 = __ldg(rp + i + 1);
+      float s = ic_value(W[i]);  // y_i
+      for (int e = di + 1; e < e1; ++e) s = __fsub_rn(s, __fmul_rn(__ldg(Lf + e), ic_value(W[__ldg(ci + e)])));
+      const float wv = __fdiv_rn(s, __ldg(Lf + di));
+      W[i] = ic_word(wv, tb);
+      consume(i, __ldcg(S.r + i), (double)wv);
+    }
+    __syncthreads();
+  }
 }
 
 // Threads of a substitution: about two levels' worth of rows (whole warps), at most the
@@ -147,6 +195,15 @@ __device__ __forceinline__ void ic_apply(const DevSys& S, Rows R, unsigned ep, u
   for (int i = R.r0 + (int)threadIdx.x; i < R.r1; i += kThreads)
     st_relaxed64(W + i, ic_word(__double2float_rn(S.r[i]), tr));
   bool bad = *(volatile unsigned*)err != 0u;
+  if (ic_threads(S.A.icwf, R.ng) <= kThreads && ic_threads(S.A.icwb, R.ng) <= kThreads) {
+    // levels of at most half a CTA: the group's first CTA alone runs both substitutions,
+    // level by level with a CTA barrier between levels (the values of earlier levels come from
+    // this CTA's own stores); only fl32(r_i) of other CTAs' rows is waited for
+    __syncthreads();
+    if (R.g == 0) ic_levels_cta(S, ep, err, tbit, limit, bad, consume);
+    __syncthreads();
+    return;
+  }
   const int gt = R.g * kThreads + (int)threadIdx.x;  // this thread in the group
   unsigned rounds = 0, nap = 0;
   long long t_last = clock64();
@@ -189,7 +246,7 @@ __device__ __forceinline__ void ic_apply(const DevSys& S, Rows R, unsigned ep, u
         }
         if (stage == 2) {
           const int e_before = ea;
-          if (ic_accumulate(ci, Lf, W, ea, eb, bad ? 0u : tf, s, !moved)) {
+          if (ic_accumulate(ci, Lf, W, ea, eb, bad ? 0u : tf, s)) {
             st_relaxed64(W + i, ic_word(__fdiv_rn(s, __ldg(Lf + eb)), tf));
             ++m;
             stage = 0;
@@ -234,7 +291,7 @@ __device__ __forceinline__ void ic_apply(const DevSys& S, Rows R, unsigned ep, u
         }
         if (stage == 2) {
           const int e_before = ea;
-          if (ic_accumulate(ci, Lf, W, ea, eb, bad ? 0u : tb, s, !moved)) {
+          if (ic_accumulate(ci, Lf, W, ea, eb, bad ? 0u : tb, s)) {
             const float w = __fdiv_rn(s, __ldg(Lf + di));
             st_relaxed64(W + i, ic_word(w, tb));
             consume(i, __ldcg(S.r + i), (double)w);

@@ -50,6 +50,9 @@ struct DevMatrix {
   const int* icpf;          // IC(0): the rows sorted by level of L y = r (level 0 first), then
   const int* icpb;          // ... of L^T w = y; a row's level is 1 + the largest level of the rows
   int icwf, icwb;           // its sum reads (0 if none); icw*: the widest level's row count
+  const int* icof;          // IC(0): start of each level in icpf (nlevf + 1 entries), then
+  const int* icob;          // ... in icpb (nlevb + 1 entries)
+  int nlevf, nlevb;
 };
 
 // One transition of an exploration episode (Algorithm 1), recorded for the end-of-round merge.
