@@ -274,8 +274,11 @@ mpcg_status mpcg_csr_levels(int32_t n, const int32_t* row_ptr, const int32_t* co
 /* Forces the SpMV schedule of value format `fmt` (sched: 0 = sub-warp vector CSR with
  * `lanes` lanes per row (1, 2, 4, 8, 16 or 32); 1 = staged stream CSR, shared-memory tiles
  * filled by bulk copies, `lanes` = 1, 2 or 4 lanes per row; 2 = one thread per row reading
- * columns and values with 16-byte loads, `lanes` = 1). In schedules 0 and 2 a row longer
- * than 1024 nonzeros (a power-law hub) is summed by a whole CTA after the CTA's other rows.
+ * columns and values with 16-byte loads, `lanes` = 1; 3 = merge-path CSR (Merrill and
+ * Garland, SC 2016): every thread of a CTA an equal share of the merged list of the CTA's row
+ * ends and products, rows split over threads merged exactly before the one rounding, `lanes`
+ * = 1). In schedules 0 and 2 a row longer than 1024 nonzeros (a power-law hub) is summed by a
+ * whole CTA after the CTA's other rows.
  * INVALID_ARG for other combinations and for a stream tile that does not fit its
  * shared-memory stage. */
 mpcg_status mpcg_matrix_set_schedule(mpcg_matrix_t A, int32_t fmt, int32_t sched, int32_t lanes);

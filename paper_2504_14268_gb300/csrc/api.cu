@@ -1052,6 +1052,8 @@ mpcg_status mpcg_matrix_set_schedule(mpcg_matrix_t A, int32_t fmt, int32_t sched
     A->dm.tile_bytes[fmt] = vreg;
   } else if (sched == SCHED_VLOAD) {
     if (lanes != 1) return fail(A->ctx, MPCG_ERR_INVALID_ARG, "the vector-load schedule takes one lane per row");
+  } else if (sched == SCHED_MERGE) {
+    if (lanes != 1) return fail(A->ctx, MPCG_ERR_INVALID_ARG, "the merge-path schedule takes lanes = 1");
   } else if (sched != SCHED_VECTOR) {
     return fail(A->ctx, MPCG_ERR_INVALID_ARG, "unknown schedule %d", sched);
   }
@@ -1142,11 +1144,11 @@ mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, 
       if (st != MPCG_OK) return st;
       if (ms < best) { best = ms; bestP[f] = lanes; }
     }
-    {
+    for (int sched : {SCHED_VLOAD, SCHED_MERGE}) {
       double ms = 0;
-      mpcg_status st = time_it(f, SCHED_VLOAD, 1, ms);
+      mpcg_status st = time_it(f, sched, 1, ms);
       if (st != MPCG_OK) return st;
-      if (ms < best) { best = ms; bestP[f] = 1; schedP[f] = SCHED_VLOAD; }
+      if (ms < best) { best = ms; bestP[f] = 1; schedP[f] = sched; }
     }
     A->dm.sched[f] = schedP[f];
     A->dm.lanes[f] = bestP[f];
@@ -1166,9 +1168,9 @@ mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, 
       schedS[f] = schedP[f];
       lanesS[f] = bestP[f];
       for (int lanes = 1; lanes <= 32; lanes *= 2) {
-        for (int sched = 0; sched < 3; ++sched) {
+        for (int sched = 0; sched < 4; ++sched) {
           if (sched == SCHED_STREAM && (lanes > 4 || stream_vreg(A, f, lanes) < 0)) continue;
-          if (sched == SCHED_VLOAD && lanes != 1) continue;
+          if ((sched == SCHED_VLOAD || sched == SCHED_MERGE) && lanes != 1) continue;
           double ms = 0;
           mpcg_status st = time_it(f, sched, lanes, ms);
           if (st != MPCG_OK) {

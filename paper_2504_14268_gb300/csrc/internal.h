@@ -21,7 +21,7 @@ constexpr int kMaxHidden = 128;     // MLP hidden width bound
 constexpr int kBarStride = 32;      // uint32 words between team barriers (128 bytes)
 constexpr int kStageBytes = 24 * 1024;  // one stage of the stream schedule's shared-memory ring
 
-enum Sched : int { SCHED_VECTOR = 0, SCHED_STREAM = 1, SCHED_VLOAD = 2 };
+enum Sched : int { SCHED_VECTOR = 0, SCHED_STREAM = 1, SCHED_VLOAD = 2, SCHED_MERGE = 3 };
 
 // Device view of a matrix: CSR structure plus the value copy of every format.
 struct DevMatrix {

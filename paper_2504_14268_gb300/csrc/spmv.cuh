@@ -217,14 +217,16 @@ __device__ __forceinline__ double row_sum64(int rs, int re, V&& val, Cf&& col, c
   return acc;
 }
 
-// Finishes a row of the product from its accumulator (lane 0 of the row's lanes).
+// Finishes a row of the product from its accumulator (lane 0 of the row's lanes). `extra`:
+// additions into the accumulator beyond the row's own (partials merged from other threads).
 template <typename VT, bool COMP, class V, class Cf>
 __device__ __forceinline__ void finish_row(const DevSys& S, int row, int rs, int re, const RowAcc<VT, COMP>& acc, int p1,
-                                           int nu_fmt, double pi, DotAcc& nu, V&& val, Cf&& col, const VT* xin) {
+                                           int nu_fmt, double pi, DotAcc& nu, V&& val, Cf&& col, const VT* xin,
+                                           int extra = 0) {
   if constexpr (sizeof(VT) == 8) {
     finish_row_64(S, row, acc.s, nu_fmt, pi, nu);
   } else {
-    const float qf = acc.rounded(p1, re - rs, [&] { return row_sum64<VT>(rs, re, val, col, xin); });
+    const float qf = acc.rounded(p1, re - rs + extra, [&] { return row_sum64<VT>(rs, re, val, col, xin); });
     finish_row_low(S, row, qf, p1, nu_fmt, pi, nu);
   }
 }
@@ -295,10 +297,23 @@ struct LongRows {
   int rows[kLongMax];
   double part[3][kThreads / 32];
 };
-__device__ __forceinline__ LongRows& long_rows() {
-  __shared__ LongRows lr;
-  return lr;
+// Partial accumulations that the merge-path schedule hands from thread to thread.
+struct MergeTails {
+  int row[kThreads];
+  double s[kThreads];
+  float c[kThreads], a[kThreads];
+};
+// The product's shared memory: the long-row queue of schedules 0 and 2, or the partials of
+// the merge-path schedule (never both in one call).
+union SpmvShared {
+  LongRows lr;
+  MergeTails mt;
+};
+__device__ __forceinline__ SpmvShared& spmv_shared() {
+  __shared__ SpmvShared u;
+  return u;
 }
+__device__ __forceinline__ LongRows& long_rows() { return spmv_shared().lr; }
 // Empties the CTA's queue (all threads of the CTA call it).
 __device__ __forceinline__ void long_begin(LongRows& lr) {
   if (threadIdx.x == 0) lr.n = 0;
@@ -535,11 +550,97 @@ __device__ void spmv_stream(const DevSys& S, const VT* __restrict__ vals, const 
   }
 }
 
+// Merge-path CSR (Merrill and Garland, SC 2016): the CTA's rows and nonzeros form one merged
+// list of row ends and products, and every thread takes an equal share of it, so a thread's
+// work does not depend on row lengths (a power-law row is split over consecutive threads). A
+// thread finds its start by a binary search along its diagonal of the merge, walks its share
+// and finishes every row that begins and ends inside it; the partial accumulation of the row
+// it leaves unfinished goes to shared memory, and the thread that ends a row begun before its
+// share merges the partials of the threads before it, in thread order, with its own before
+// rounding once (TwoSum pairs merge exactly, so the 16-bit, tf32 and q52 row sums stay
+// correctly rounded).
+template <typename VT, bool COMP>
+__device__ void spmv_merge(const DevSys& S, const VT* __restrict__ vals, const VT* xin, Rows R, int p1, int nu_fmt,
+                           DotAcc& nu) {
+  const int* __restrict__ rp = S.A.rp;
+  const int* __restrict__ ci = S.A.ci;
+  MergeTails& mt = spmv_shared().mt;
+  const int nrows = R.r1 - R.r0;
+  if (nrows <= 0) return;  // the same for the whole CTA
+  const int t = threadIdx.x;
+  const int E0 = __ldg(rp + R.r0);
+  const int nnz = __ldg(rp + R.r1) - E0;
+  const long long total = (long long)nrows + nnz;
+  const long long ipt = (total + kThreads - 1) / kThreads;
+  const long long d0 = min((long long)t * ipt, total), d1 = min(d0 + ipt, total);
+  // the point of the merge path on diagonal d0: lo row ends and d0 - lo products passed
+  int lo = (int)max(d0 - (long long)nnz, 0ll), hi = (int)min(d0, (long long)nrows);
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((long long)(__ldg(rp + R.r0 + mid + 1) - E0) <= d0 - mid - 1) lo = mid + 1;
+    else hi = mid;
+  }
+  int row = R.r0 + lo;
+  int e = E0 + (int)(d0 - lo);
+  int rs = row < R.r1 ? __ldg(rp + row) : 0, re = row < R.r1 ? __ldg(rp + row + 1) : 0;
+  bool begun_here = e == rs;  // the row's first product (or its end, if empty) is in this share
+  bool touched = false;       // products of the current row accumulated by this thread
+  RowAcc<VT, COMP> acc, head;
+  int head_row = -1;
+  __syncthreads();  // the shared union may hold the long-row queue of an earlier product
+  mt.row[t] = -1;
+  for (long long d = d0; d < d1; ++d) {
+    if (e < re) {
+      acc.add(ldg_val(vals + e), xin[__ldg(ci + e)]);
+      ++e;
+      touched = true;
+    } else {  // row `row` ends in this share
+      if (begun_here) {
+        finish_row<VT, COMP>(S, row, rs, re, acc, p1, nu_fmt, nu_input(S, xin, row, p1, nu_fmt), nu,
+                             [&](int k) { return ldg_val(vals + k); }, [&](int k) { return __ldg(ci + k); }, xin);
+      } else {
+        head = acc;
+        head_row = row;
+      }
+      acc = RowAcc<VT, COMP>();
+      ++row;
+      begun_here = true;
+      touched = false;
+      rs = re;
+      if (row < R.r1) re = __ldg(rp + row + 1);
+    }
+  }
+  if (touched) {  // the current row continues in the next share
+    mt.row[t] = row;
+    mt.s[t] = (double)acc.s;
+    mt.c[t] = (float)acc.c;
+    mt.a[t] = (float)acc.a;
+  }
+  __syncthreads();
+  if (head_row >= 0) {
+    int tf = t;
+    while (tf > 0 && mt.row[tf - 1] == head_row) --tf;
+    RowAcc<VT, COMP> m;
+    int merged = 0;
+    for (int u = tf; u < t; ++u, ++merged) m.merge(mt.s[u], mt.c[u], mt.a[u]);
+    m.merge((double)head.s, (double)head.c, (double)head.a);
+    const int hs = __ldg(rp + head_row), he = __ldg(rp + head_row + 1);
+    finish_row<VT, COMP>(S, head_row, hs, he, m, p1, nu_fmt, nu_input(S, xin, head_row, p1, nu_fmt), nu,
+                         [&](int k) { return ldg_val(vals + k); }, [&](int k) { return __ldg(ci + k); }, xin,
+                         merged + 1);
+  }
+  __syncthreads();
+}
+
 template <typename VT, bool COMP>
 __device__ void spmv_dispatch_k(const DevSys& S, const VT* vals, const VT* xin, Rows R, int p1, int nu_fmt,
                                 DotAcc& nu, const StreamCtx* sc) {
   if (S.A.sched[p1] == SCHED_VLOAD) {
     spmv_vload<VT, COMP>(S, vals, xin, R, p1, nu_fmt, nu);
+    return;
+  }
+  if (S.A.sched[p1] == SCHED_MERGE) {
+    spmv_merge<VT, COMP>(S, vals, xin, R, p1, nu_fmt, nu);
     return;
   }
   if (sc && S.A.sched[p1] == SCHED_STREAM) {

@@ -12,7 +12,7 @@ from paper_2504_14268_gb300 import inputs as I
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-SCHEDULES = [(0, 1), (0, 2), (0, 4), (0, 32), (2, 1), (1, 1), (1, 4)]
+SCHEDULES = [(0, 1), (0, 2), (0, 4), (0, 32), (2, 1), (1, 1), (1, 4), (3, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -71,7 +71,25 @@ def _check_products(M, A, fmts, schedules, seed):
 def test_hub_rows_every_format_and_schedule(M):
     A = I.hub_laplacian(60000, 24, 1100, 20000, 1.0, np.random.default_rng(2))
     assert np.diff(A[1]).max() > 10000
-    assert _check_products(M, A, range(8), SCHEDULES, seed=3) >= 8 * 5
+    assert _check_products(M, A, range(8), SCHEDULES, seed=3) >= 8 * 6
+
+
+def test_merge_path_splits_rows_at_every_kind_of_boundary(M):
+    """The merge-path schedule on rows of mixed lengths (empty rows, single entries, rows of a
+    few dozen to a few thousand entries, in runs, so that shares of the merged list begin and
+    end inside rows, exactly at row ends and on empty rows), every format, against the
+    oracle: bit for bit where the row sum is correctly rounded."""
+    rng = np.random.default_rng(7)
+    n = 6000
+    lens = rng.choice([0, 0, 1, 2, 5, 27, 33, 257, 3000], size=n, p=[.2, .1, .15, .1, .15, .15, .1, .04, .01])
+    rows = []
+    for i, k in enumerate(lens):
+        rows.append(np.sort(rng.choice(n, size=min(int(k), n), replace=False)))
+    rp = np.concatenate([[0], np.cumsum([r.size for r in rows])]).astype(np.int32)
+    ci = np.concatenate(rows).astype(np.int32)
+    val = rng.uniform(-2, 2, ci.size)
+    A = (n, rp, ci, val)
+    assert _check_products(M, A, range(8), [(3, 1)], seed=8) == 8
 
 
 def test_long_row_queue_overflow(M):
@@ -87,7 +105,7 @@ def test_long_row_queue_overflow(M):
     vals[cols == np.arange(n)[:, None]] = 2.0 * kd + 2.0
     rp = np.arange(0, n * (2 * kd + 1) + 1, 2 * kd + 1, dtype=np.int32)
     A = (n, rp, cols.ravel().astype(np.int32), vals.ravel())
-    assert _check_products(M, A, (0, 2, 3, 4), [(0, 1), (0, 32), (2, 1)], seed=5) == 12
+    assert _check_products(M, A, (0, 2, 3, 4), [(0, 1), (0, 32), (2, 1), (3, 1)], seed=5) == 16
 
 
 def _stable_prefix(ref, twin, lim):
@@ -101,7 +119,7 @@ def _stable_prefix(ref, twin, lim):
 
 
 @pytest.mark.parametrize("fmts,tol", [((4, 4, 4, 4), 1e-10), ((3, 3, 3, 4), 1e-6), ((1, 3, 3, 4), 1e-4), ((6, 3, 3, 4), 1e-4)])
-@pytest.mark.parametrize("sched", [(2, 1), (0, 32)])
+@pytest.mark.parametrize("sched", [(2, 1), (0, 32), (3, 1)])
 def test_solve_on_hub_graph_matches_oracle(M, fmts, tol, sched):
     A = I.hub_laplacian(20000, 12, 1100, 8000, 1.0, np.random.default_rng(6))
     xs, b = I.rhs_from_xstar(A, np.random.default_rng(7))

@@ -101,7 +101,7 @@ def test_format_copies_are_bit_exact(M):
         assert np.array_equal(y, ref, equal_nan=True), (fmt, np.flatnonzero(~((y == ref) | (np.isnan(y) & np.isnan(ref))))[:5])
 
 
-SCHEDULES = [(0, 1), (0, 2), (0, 4), (0, 8), (0, 16), (0, 32), (2, 1), (1, 1), (1, 2), (1, 4)]
+SCHEDULES = [(0, 1), (0, 2), (0, 4), (0, 8), (0, 16), (0, 32), (2, 1), (1, 1), (1, 2), (1, 4), (3, 1)]
 
 
 @pytest.mark.parametrize("which", ["poisson", "diffusion3d", "banded"])
