@@ -75,19 +75,24 @@ def test_hub_rows_every_format_and_schedule(M):
 
 
 def test_merge_path_splits_rows_at_every_kind_of_boundary(M):
-    """The merge-path schedule on rows of mixed lengths (empty rows, single entries, rows of a
-    few dozen to a few thousand entries, in runs, so that shares of the merged list begin and
-    end inside rows, exactly at row ends and on empty rows), every format, against the
-    oracle: bit for bit where the row sum is correctly rounded."""
+    """The merge-path schedule on rows of mixed lengths (the diagonal alone, a few entries,
+    rows of a few dozen to a few thousand entries, in runs, so that shares of the merged list
+    begin and end inside rows and exactly at row ends), every format, against the oracle: bit
+    for bit where the row sum is correctly rounded."""
     rng = np.random.default_rng(7)
     n = 6000
-    lens = rng.choice([0, 0, 1, 2, 5, 27, 33, 257, 3000], size=n, p=[.2, .1, .15, .1, .15, .15, .1, .04, .01])
-    rows = []
+    lens = rng.choice([0, 1, 2, 5, 27, 33, 257, 3000], size=n, p=[.3, .15, .1, .15, .15, .1, .04, .01])
+    rows, vals = [], []
     for i, k in enumerate(lens):
-        rows.append(np.sort(rng.choice(n, size=min(int(k), n), replace=False)))
+        others = rng.choice(n - 1, size=int(k), replace=False)
+        cols = np.sort(np.concatenate([[i], others + (others >= i)]))  # the diagonal and k others
+        v = rng.uniform(-2, 2, cols.size)
+        v[cols == i] = 4.0 + k  # the library takes matrices with a positive diagonal
+        rows.append(cols)
+        vals.append(v)
     rp = np.concatenate([[0], np.cumsum([r.size for r in rows])]).astype(np.int32)
     ci = np.concatenate(rows).astype(np.int32)
-    val = rng.uniform(-2, 2, ci.size)
+    val = np.concatenate(vals)
     A = (n, rp, ci, val)
     assert _check_products(M, A, range(8), [(3, 1)], seed=8) == 8
 
