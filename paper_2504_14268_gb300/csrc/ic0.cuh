@@ -71,6 +71,28 @@ __device__ __forceinline__ unsigned long long ic_word(float v, unsigned mark) {
 __device__ __forceinline__ float ic_value(unsigned long long w) { return __uint_as_float((unsigned)w); }
 __device__ __forceinline__ unsigned ic_mark(unsigned long long w) { return (unsigned)(w >> 32); }
 
+// Continues the row sum s -= l_e v_col(e) over e = ea, ea + 1, ... < eb in order, eight
+// words per memory round trip, as long as the rows read carry a mark >= target. True when
+// the sum is complete; otherwise ea and s hold the progress for the next attempt (the order
+// of the terms never changes).
+__device__ __forceinline__ bool ic_accumulate(const int* __restrict__ ci, const float* __restrict__ Lf,
+                                              const unsigned long long* W, int& ea, int eb, unsigned target,
+                                              float& s) {
+  while (ea < eb) {
+    unsigned long long w[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) w[u] = ea + u < eb ? ld_relaxed64(W + __ldg(ci + ea + u)) : 0ull;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (ea >= eb) return true;
+      if (ic_mark(w[u]) < target) return false;
+      s = __fsub_rn(s, __fmul_rn(__ldg(Lf + ea), ic_value(w[u])));
+      ++ea;
+    }
+  }
+  return true;
+}
+
 // Both substitutions by one CTA, level by level (ic_apply for systems whose levels hold at
 // most half a CTA's threads' worth of rows). Row i of a level waits (bounded) only for the mark
 // of its own fl32(r_i), published by the CTA holding the row; the values of earlier levels were
@@ -135,168 +157,6 @@ __device__ __forceinline__ int ic_threads(int width, int ng) {
   return want < 32 ? 32 : (want < have ? want : have);
 }
 
-// Row bounds of a substitution: the entries [ea, eb) the row's sum reads and the diagonal's
-// position (forward: the lower entries, the diagonal after them; backward: the upper ones,
-// the diagonal before them).
-template <bool BACK>
-__device__ __forceinline__ void ic_bounds(const DevSys& S, int i, int& ea, int& eb, int& diag) {
-  if constexpr (BACK) {
-    diag = __ldg(S.A.icd + i);
-    ea = diag + 1;
-    eb = __ldg(S.A.rp + i + 1);
-  } else {
-    ea = __ldg(S.A.rp + i);
-    eb = __ldg(S.A.icd + i);
-    diag = eb;
-  }
-}
-
-// One substitution (BACK: L^T w = y, else L y = fl32(r)) by threads 0..T-1 of the group, thread
-// gt taking the positions gt, gt + T, ... of the level order `order`. A row waits for its own
-// word to carry own_mark (fl32(r_i), or y_i), for the words it reads to carry in_mark, and
-// publishes its value with in_mark (forward) or its w with in_mark (backward; both the mark of
-// this sweep's outputs). The warp advances in rounds; in a round every lane issues at most one
-// batch of independent loads (the next row's bounds two rows ahead, its own word, eight columns
-// and factor values, or the eight words those columns name) and uses what it loaded in the round
-// before, so a round lasts about one memory round trip whatever the lanes are doing.
-template <bool BACK, class F>
-__device__ __forceinline__ void ic_sweep(const DevSys& S, int gt, int T, const int* __restrict__ order,
-                                         unsigned own_mark, unsigned in_mark, unsigned* err, unsigned tbit,
-                                         long long limit, bool& bad, F&& consume) {
-  const int* __restrict__ ci = S.A.ci;
-  const float* __restrict__ Lf = S.A.icf;
-  unsigned long long* W = S.icw;
-  const int n = S.A.n;
-  const int cnt = gt < T ? (n - gt + T - 1) / T : 0;
-  int m = 0;
-  int i = 0, ea = 0, eb = 0, diag = 0;  // the current row
-  int i1 = 0, a1 = 0, b1 = 0, d1 = 0;   // the next row (its bounds loaded while the current one runs)
-  int i2 = 0;                           // the row after it (its index)
-  if (cnt > 0) {
-    i = __ldg(order + gt);
-    ic_bounds<BACK>(S, i, ea, eb, diag);
-  }
-  if (cnt > 1) i1 = __ldg(order + gt + T);
-  if (cnt > 2) i2 = __ldg(order + gt + 2 * T);
-  int stage = 0;  // 0: start the row, 1: own word loaded, 2: words loaded, 3: columns loaded
-  unsigned long long w0 = 0ull;
-  unsigned long long wv[8];
-  int c[8];
-  float lv[8];
-  int nb = 0, kd = 0;  // entries in the batch, entries of it already summed
-  float s = 0.f, ldiag = 1.f;
-  double rv = 0.0;
-  unsigned rounds = 0, nap = 0;
-  long long t_last = clock64();
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    wv[k] = 0ull;
-    c[k] = 0;
-    lv[k] = 0.f;
-  }
-  while (__any_sync(kFull, m < cnt)) {
-    bool moved = false;
-    if (m < cnt) {
-      if (stage == 0) {  // the row's own word, its first columns and factor values, its diagonal
-        w0 = ld_relaxed64(W + i);
-        nb = min(8, eb - ea);
-        kd = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (k < nb) {
-            c[k] = __ldg(ci + ea + k);
-            lv[k] = __ldg(Lf + ea + k);
-          }
-        ldiag = __ldg(Lf + diag);
-        if (m + 1 < cnt) ic_bounds<BACK>(S, i1, a1, b1, d1);
-        stage = 1;
-        moved = true;
-      } else if (stage == 1) {  // own word: start the sum, or look again
-        if (bad || ic_mark(w0) >= own_mark) {
-          s = ic_value(w0);
-          // backward: r_i was written before fl32(r_i) was published, which came before y_i
-          if constexpr (BACK) rv = __ldcg(S.r + i);
-#pragma unroll
-          for (int k = 0; k < 8; ++k)
-            if (k < nb) wv[k] = ld_relaxed64(W + c[k]);
-          stage = 2;
-          moved = true;
-        } else {
-          w0 = ld_relaxed64(W + i);
-        }
-      } else if (stage == 3) {  // columns of the next batch loaded: load their words
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (k < nb) wv[k] = ld_relaxed64(W + c[k]);
-        stage = 2;
-        moved = true;
-      } else {  // stage 2: sum the ready words in order
-        bool stop = false;
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (k >= kd && k < nb && !stop) {
-            if (bad || ic_mark(wv[k]) >= in_mark) {
-              s = __fsub_rn(s, __fmul_rn(lv[k], ic_value(wv[k])));
-              kd = k + 1;
-              moved = true;
-            } else {
-              stop = true;
-            }
-          }
-        if (kd == nb) {
-          ea += nb;
-          if (ea == eb) {  // the row is done
-            const float v = __fdiv_rn(s, ldiag);
-            st_relaxed64(W + i, ic_word(v, in_mark));
-            if constexpr (BACK) consume(i, rv, (double)v);
-            ++m;
-            i = i1;
-            ea = a1;
-            eb = b1;
-            diag = d1;
-            i1 = i2;
-            if (m + 2 < cnt) i2 = __ldg(order + gt + (m + 2) * T);
-            stage = 0;
-            moved = true;
-          } else {  // the next batch of columns and factor values
-            nb = min(8, eb - ea);
-            kd = 0;
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-              if (k < nb) {
-                c[k] = __ldg(ci + ea + k);
-                lv[k] = __ldg(Lf + ea + k);
-              }
-            stage = 3;
-            moved = true;
-          }
-        } else {  // look again at the words not ready yet
-#pragma unroll
-          for (int k = 0; k < 8; ++k)
-            if (k >= kd && k < nb) wv[k] = ld_relaxed64(W + c[k]);
-        }
-      }
-    }
-    if (__any_sync(kFull, moved)) {
-      t_last = clock64();
-      nap = 0;
-    } else {
-      // a round without progress in the whole warp: back off briefly, check the status word
-      // now and then, and the time since the warp last moved
-      nap = nap ? min(2u * nap, 256u) : 32u;
-      __nanosleep(nap);
-      if ((++rounds & 63u) == 0u) {
-        if (*(volatile unsigned*)err != 0u) {
-          bad = true;
-        } else if (clock64() - t_last > limit) {
-          atomicOr(err, tbit);
-          bad = true;
-        }
-      }
-    }
-  }
-}
-
 // w = M^-1 fl32(r) for one application with epoch `ep`, run by the ng CTAs that hold rows of
 // the system (this CTA is number R.g; R is its own row range). Marks in the high word of each
 // row's 64-bit word: 3 ep + 1 when fl32(r_i) is published (by the CTA holding row i, which
@@ -321,7 +181,12 @@ __device__ __forceinline__ void ic_sweep(const DevSys& S, int gt, int T, const i
 template <class F>
 __device__ __forceinline__ void ic_apply(const DevSys& S, Rows R, unsigned ep, unsigned* err, unsigned tbit,
                                          long long limit, F&& consume) {
+  const int* __restrict__ rp = S.A.rp;
+  const int* __restrict__ ci = S.A.ci;
+  const float* __restrict__ Lf = S.A.icf;
+  const int* __restrict__ dp = S.A.icd;
   unsigned long long* W = S.icw;
+  const int n = S.A.n;
   const unsigned tr = 3u * ep + 1u, tf = 3u * ep + 2u, tb = 3u * ep + 3u;
   // publish fl32(r_i) of this CTA's rows (r written by this CTA's threads before the barrier)
   __threadfence();
@@ -339,8 +204,112 @@ __device__ __forceinline__ void ic_apply(const DevSys& S, Rows R, unsigned ep, u
     return;
   }
   const int gt = R.g * kThreads + (int)threadIdx.x;  // this thread in the group
-  ic_sweep<false>(S, gt, ic_threads(S.A.icwf, R.ng), S.A.icpf, tr, tf, err, tbit, limit, bad, consume);
-  ic_sweep<true>(S, gt, ic_threads(S.A.icwb, R.ng), S.A.icpb, tf, tb, err, tbit, limit, bad, consume);
+  unsigned rounds = 0, nap = 0;
+  long long t_last = clock64();
+  // a round without progress in the whole warp: back off briefly, check the status word now
+  // and then, and the time since the warp last moved
+  auto idle = [&]() {
+    nap = nap ? min(2u * nap, 256u) : 32u;
+    __nanosleep(nap);
+    if ((++rounds & 63u) != 0u) return;
+    if (*(volatile unsigned*)err != 0u) {
+      bad = true;
+    } else if (clock64() - t_last > limit) {
+      atomicOr(err, tbit);
+      bad = true;
+    }
+  };
+  // forward: L y = fl32(r), positions gt, gt + T, ... of the forward level order
+  {
+    const int T = ic_threads(S.A.icwf, R.ng);
+    const int cnt = gt < T ? (n - gt + T - 1) / T : 0;
+    int m = 0, ea = 0, eb = 0, i = 0;
+    float s = 0.f;
+    int stage = 0;  // 0: new row, 1: waiting for fl32(r_i), 2: summing
+    while (__any_sync(kFull, m < cnt)) {
+      bool moved = false;
+      if (m < cnt) {
+        if (stage == 0) {
+          i = __ldg(S.A.icpf + gt + m * T);
+          ea = __ldg(rp + i);
+          eb = __ldg(dp + i);
+          stage = 1;
+        }
+        if (stage == 1) {
+          const unsigned long long w = ld_relaxed64(W + i);
+          if (bad || ic_mark(w) >= tr) {
+            s = ic_value(w);
+            stage = 2;
+            moved = true;
+          }
+        }
+        if (stage == 2) {
+          const int e_before = ea;
+          if (ic_accumulate(ci, Lf, W, ea, eb, bad ? 0u : tf, s)) {
+            st_relaxed64(W + i, ic_word(__fdiv_rn(s, __ldg(Lf + eb)), tf));
+            ++m;
+            stage = 0;
+            moved = true;
+          } else {
+            moved = moved || ea != e_before;
+          }
+        }
+      }
+      if (__any_sync(kFull, moved)) {
+        t_last = clock64();
+        nap = 0;
+      } else {
+        idle();
+      }
+    }
+  }
+  // backward: L^T w = y, positions gt, gt + T, ... of the backward level order
+  {
+    const int T = ic_threads(S.A.icwb, R.ng);
+    const int cnt = gt < T ? (n - gt + T - 1) / T : 0;
+    int m = 0, ea = 0, eb = 0, di = 0, i = 0;
+    float s = 0.f;
+    int stage = 0;  // 0: new row, 1: waiting for y_i, 2: summing
+    while (__any_sync(kFull, m < cnt)) {
+      bool moved = false;
+      if (m < cnt) {
+        if (stage == 0) {
+          i = __ldg(S.A.icpb + gt + m * T);
+          di = __ldg(dp + i);
+          ea = di + 1;
+          eb = __ldg(rp + i + 1);
+          stage = 1;
+        }
+        if (stage == 1) {
+          const unsigned long long w = ld_relaxed64(W + i);
+          if (bad || ic_mark(w) >= tf) {
+            s = ic_value(w);
+            stage = 2;
+            moved = true;
+          }
+        }
+        if (stage == 2) {
+          const int e_before = ea;
+          if (ic_accumulate(ci, Lf, W, ea, eb, bad ? 0u : tb, s)) {
+            const float w = __fdiv_rn(s, __ldg(Lf + di));
+            st_relaxed64(W + i, ic_word(w, tb));
+            consume(i, __ldcg(S.r + i), (double)w);
+            ++m;
+            stage = 0;
+            moved = true;
+          } else {
+            moved = moved || ea != e_before;
+          }
+        }
+      }
+      if (__any_sync(kFull, moved)) {
+        t_last = clock64();
+        nap = 0;
+      } else {
+        idle();
+      }
+    }
+  }
   __syncthreads();
 }
 
