@@ -479,7 +479,9 @@ __device__ __forceinline__ void sigma_term(double ri, double wi, int p2, int p4,
   } else {
     const float a = round_d2f(ri, p4);
     float b;
-    if (wi == ri && (p2 == F64 || base_fmt(p2) == base_fmt(p4))) b = a;
+    // z_i = r_i (M = I): compared on the bit patterns, an integer test (an fp64 comparison
+    // would take the narrow fp64 pipe once per row)
+    if (__double_as_longlong(wi) == __double_as_longlong(ri) && (p2 == F64 || base_fmt(p2) == base_fmt(p4))) b = a;
     else if (p2 == F64) b = round_d2f(wi, p4);
     else {
       const float zf = round_d2f(wi, p2);
