@@ -14,8 +14,12 @@
  *     assignment of Section 4.2 (q = fl_p1(A p), z = fl_p2(M^-1 r), nu = fl_p3(p^T q),
  *     sigma = fl_p4(r^T z); residual update, alpha and beta in fp64);
  *   - the MDP of Section 4.1 (state discretisation, reward, Q-learning update,
- *     epsilon-greedy exploration) and Algorithms 1 (training) and 2 (inference).
- *   - a small MLP Q-function (forward, backward, Adam) used by the learned policy.
+ *     epsilon-greedy exploration) and Algorithms 1 (training) and 2 (inference), with
+ *     per-operation tables or one table over the joint actions;
+ *   - a small MLP Q-function (forward, backward, Adam) used by the learned policy;
+ *   - the preconditioners of op 2: Jacobi and the fp32 incomplete Cholesky IC(0);
+ *   - a single-reduction form of the iteration (Chronopoulos and Gear), beside the CG of
+ *     Section 3.
  *
  * Every sum runs in fp64 in index order and the result is then rounded ("compute
  * high, round the output"), which is the emulation model the paper used (Section 5).
