@@ -277,8 +277,11 @@ mpcg_status mpcg_csr_levels(int32_t n, const int32_t* row_ptr, const int32_t* co
  * columns and values with 16-byte loads, `lanes` = 1; 3 = merge-path CSR (Merrill and
  * Garland, SC 2016): every thread of a CTA an equal share of the merged list of the CTA's row
  * ends and products, rows split over threads merged exactly before the one rounding, `lanes`
- * = 1). In schedules 0 and 2 a row longer than 1024 nonzeros (a power-law hub) is summed by a
- * whole CTA after the CTA's other rows.
+ * = 1; 4 = staged x: one thread per row as schedule 2, gathering from a copy in shared memory
+ * of the window of x that the CTA's rows read, when it fits (otherwise from x), `lanes` = 1,
+ * for matrices whose column indices increase in every row). In schedules 0, 2 and 4 a row
+ * longer than 1024 nonzeros (a power-law hub) is summed by a whole CTA after the CTA's other
+ * rows.
  * INVALID_ARG for other combinations and for a stream tile that does not fit its
  * shared-memory stage. */
 mpcg_status mpcg_matrix_set_schedule(mpcg_matrix_t A, int32_t fmt, int32_t sched, int32_t lanes);

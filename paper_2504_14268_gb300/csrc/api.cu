@@ -177,9 +177,11 @@ int stream_vreg(const mpcg_matrix_s* M, int fmt, int lanes) {
   return vreg + creg <= kStageBytes ? (int)vreg : -1;
 }
 
+// The launch carries the shared-memory buffer (two stream stages) when some format's product
+// uses it: the stream ring, or the staged x window.
 bool uses_stream(const DevMatrix& d) {
   for (int f = 0; f < NFMT; ++f)
-    if (d.sched[f] == SCHED_STREAM) return true;
+    if (d.sched[f] == SCHED_STREAM || d.sched[f] == SCHED_XSTAGE) return true;
   return false;
 }
 
@@ -886,7 +888,7 @@ mpcg_status mpcg_matrix_create(mpcg_ctx_t ctx, const mpcg_csr* A, mpcg_matrix_t*
   int hf[2] = {0, 0};
   CK(ctx, cudaMemcpyAsync(hf, flags.p, sizeof(hf), cudaMemcpyDeviceToHost, s));
   CK(ctx, cudaStreamSynchronize(s));
-  if (hf[0]) {
+  if (hf[0] & 31) {
     const unsigned f = (unsigned)hf[0];
     return fail(ctx, MPCG_ERR_INVALID_ARG, "invalid CSR at row %d:%s%s%s%s%s", hf[1], (f & 1) ? " row_ptr bounds" : "",
                 (f & 2) ? " row_ptr decreasing" : "", (f & 4) ? " column out of range" : "",
@@ -907,6 +909,7 @@ mpcg_status mpcg_matrix_create(mpcg_ctx_t ctx, const mpcg_csr* A, mpcg_matrix_t*
   d.vbfr = M->vbfr.as<__nv_bfloat16>();
   d.v8 = M->v8.as<q52_t>();
   d.rexp = M->rexp.as<short>();
+  d.cols_sorted = (hf[0] & 32) ? 0 : 1;
   CK(ctx, launch_convert(d, M->v32.as<float>(), M->vtf.as<float>(), M->v16.as<__half>(), M->vbf.as<__nv_bfloat16>(),
                          M->v16r.as<__half>(), M->vbfr.as<__nv_bfloat16>(), M->v8.as<q52_t>(), M->rexp.as<short>(), s));
   // Jacobi: fp64 reciprocals of the diagonal, and whether every row has a positive one.
@@ -1054,6 +1057,10 @@ mpcg_status mpcg_matrix_set_schedule(mpcg_matrix_t A, int32_t fmt, int32_t sched
     if (lanes != 1) return fail(A->ctx, MPCG_ERR_INVALID_ARG, "the vector-load schedule takes one lane per row");
   } else if (sched == SCHED_MERGE) {
     if (lanes != 1) return fail(A->ctx, MPCG_ERR_INVALID_ARG, "the merge-path schedule takes lanes = 1");
+  } else if (sched == SCHED_XSTAGE) {
+    if (lanes != 1) return fail(A->ctx, MPCG_ERR_INVALID_ARG, "the staged-x schedule takes lanes = 1");
+    if (!A->dm.cols_sorted)
+      return fail(A->ctx, MPCG_ERR_INVALID_ARG, "the staged-x schedule needs increasing column indices in every row");
   } else if (sched != SCHED_VECTOR) {
     return fail(A->ctx, MPCG_ERR_INVALID_ARG, "unknown schedule %d", sched);
   }
@@ -1156,7 +1163,7 @@ mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, 
   }
   // Configuration S: launch shape with the stream ring; each format takes the faster of the
   // stream schedule and the vector schedule measured in that shape.
-  bool any = false;
+  bool any = A->dm.cols_sorted != 0;  // the staged-x schedule runs in this shape too
   for (int f = 0; f < NFMT && !any; ++f)
     for (int lanes = 1; lanes <= 4; lanes *= 2) any = any || stream_vreg(A, f, lanes) >= 0;
   if (any) {
@@ -1168,9 +1175,10 @@ mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, 
       schedS[f] = schedP[f];
       lanesS[f] = bestP[f];
       for (int lanes = 1; lanes <= 32; lanes *= 2) {
-        for (int sched = 0; sched < 4; ++sched) {
+        for (int sched = 0; sched < 5; ++sched) {
           if (sched == SCHED_STREAM && (lanes > 4 || stream_vreg(A, f, lanes) < 0)) continue;
-          if ((sched == SCHED_VLOAD || sched == SCHED_MERGE) && lanes != 1) continue;
+          if ((sched == SCHED_VLOAD || sched == SCHED_MERGE || sched == SCHED_XSTAGE) && lanes != 1) continue;
+          if (sched == SCHED_XSTAGE && !A->dm.cols_sorted) continue;
           double ms = 0;
           mpcg_status st = time_it(f, sched, lanes, ms);
           if (st != MPCG_OK) {
@@ -1185,7 +1193,7 @@ mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, 
     }
     A->force_stream_shape = false;
     bool s_uses = false;
-    for (int f = 0; f < NFMT; ++f) s_uses = s_uses || schedS[f] == SCHED_STREAM;
+    for (int f = 0; f < NFMT; ++f) s_uses = s_uses || schedS[f] == SCHED_STREAM || schedS[f] == SCHED_XSTAGE;
     if (s_uses && sumS < sumP) {
       for (int f = 0; f < NFMT; ++f) mpcg_matrix_set_schedule(A, f, schedS[f], lanesS[f]);
       return MPCG_OK;

@@ -21,7 +21,7 @@ constexpr int kMaxHidden = 128;     // MLP hidden width bound
 constexpr int kBarStride = 32;      // uint32 words between team barriers (128 bytes)
 constexpr int kStageBytes = 24 * 1024;  // one stage of the stream schedule's shared-memory ring
 
-enum Sched : int { SCHED_VECTOR = 0, SCHED_STREAM = 1, SCHED_VLOAD = 2, SCHED_MERGE = 3 };
+enum Sched : int { SCHED_VECTOR = 0, SCHED_STREAM = 1, SCHED_VLOAD = 2, SCHED_MERGE = 3, SCHED_XSTAGE = 4 };
 
 // Device view of a matrix: CSR structure plus the value copy of every format.
 struct DevMatrix {
@@ -43,6 +43,7 @@ struct DevMatrix {
   int lanes[8];             // lanes per row per format
   int tile_rows[8];         // stream schedule: rows per shared-memory tile (kThreads / lanes)
   int tile_bytes[8];        // stream schedule: bytes of a stage's value region (columns follow)
+  int cols_sorted;          // every row's column indices strictly increase
   const double* dinv;       // Jacobi: 1 / a_ii in fp64 when the launch preconditions, else nullptr
   const float* icf;         // IC(0) factor in fp32 when the launch preconditions with it, else
                             // nullptr: l_ij at (i, j) for j <= i, l_ji at (i, j) for j > i

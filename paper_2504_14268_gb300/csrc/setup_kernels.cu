@@ -17,6 +17,7 @@ enum : unsigned {
   VF_COL = 4u,      // column index outside [0, n)
   VF_VALUE = 8u,    // non-finite value
   VF_DIAG = 16u,    // diagonal entry missing or not positive
+  VF_UNSORTED = 32u // (not an error) some row's column indices do not strictly increase
 };
 
 __global__ void validate_rowptr(int n, long long nnz, const int* __restrict__ rp, unsigned* flags, int* bad_row) {
@@ -42,21 +43,24 @@ __global__ void validate_rows(int n, const int* __restrict__ rp, const int* __re
        row += ((long long)gridDim.x * blockDim.x) >> 5) {
     const int e0 = rp[row], e1 = rp[row + 1];
     unsigned f = 0;
-    int diag_ok = 0;
+    int diag_ok = 0, unsorted = 0;
     for (int e = e0 + lane; e < e1; e += 32) {
       const int c = ci[e];
       const double a = v[e];
       if (c < 0 || c >= n) f |= VF_COL;
       if (!isfinite(a)) f |= VF_VALUE;
       if (c == row && a > 0.0) diag_ok = 1;
+      if (e > e0 && ci[e - 1] >= c) unsorted = 1;
     }
     diag_ok = __any_sync(kFull, diag_ok);
+    unsorted = __any_sync(kFull, unsorted);
     f = __reduce_or_sync(kFull, f);
     if (!diag_ok) f |= VF_DIAG;
     if (f && lane == 0) {
       atomicOr(flags, f);
       atomicMin(bad_row, (int)row);
     }
+    if (unsorted && lane == 0) atomicOr(flags, (unsigned)VF_UNSORTED);
   }
 }
 

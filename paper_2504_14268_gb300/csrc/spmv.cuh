@@ -419,9 +419,12 @@ __device__ __forceinline__ double lane_of<double>(const int4& q, int k) {
 // down to a multiple of G, the arrays are padded so the last group stays in bounds), so a
 // thread issues one load per 4 columns and per 16 bytes of values instead of one per
 // element; elements of a group outside the row are skipped. Long rows go to the CTA queue.
+// xs, xoff: where the gathers read x (element c at xs[c - xoff]): x itself, or its staged
+// window in shared memory.
 template <typename VT, bool COMP>
 __device__ void spmv_vload(const DevSys& S, const VT* __restrict__ vals, const VT* xin, Rows R, int p1, int nu_fmt,
-                           DotAcc& nu) {
+                           DotAcc& nu, const VT* xs = nullptr, int xoff = 0) {
+  if (xs == nullptr) xs = xin;
   constexpr int G = sizeof(VT) <= 2 ? 8 : 4;
   constexpr int NV = G * (int)sizeof(VT) / 16;  // 16-byte value loads per group (0: one 8-byte load)
   const int* __restrict__ rp = S.A.rp;
@@ -474,7 +477,7 @@ __device__ void spmv_vload(const DevSys& S, const VT* __restrict__ vals, const V
       VT xv[G];
 #pragma unroll
       for (int j = 0; j < G; ++j)
-        if (g + j >= e0 && g + j < e1) xv[j] = xin[c[j]];
+        if (g + j >= e0 && g + j < e1) xv[j] = xs[c[j] - xoff];
 #pragma unroll
       for (int j = 0; j < G; ++j)
         if (g + j >= e0 && g + j < e1) acc.add(v[j], xv[j]);
@@ -632,6 +635,48 @@ __device__ void spmv_merge(const DevSys& S, const VT* __restrict__ vals, const V
   __syncthreads();
 }
 
+// Staged x: the CTA's rows read x only within [lo, hi], the smallest and largest column of its
+// rows (columns increase in every row); when that window fits the launch's shared-memory
+// buffer, the CTA first copies it there with coalesced loads and the one-thread-per-row
+// product gathers from shared memory; otherwise it gathers from x as the vector-load schedule.
+template <typename VT, bool COMP>
+__device__ void spmv_xstage(const DevSys& S, const VT* __restrict__ vals, const VT* xin, Rows R, int p1, int nu_fmt,
+                            DotAcc& nu, const StreamCtx& sc) {
+  __shared__ int win[2];
+  const int* __restrict__ rp = S.A.rp;
+  const int* __restrict__ ci = S.A.ci;
+  if (threadIdx.x == 0) {
+    win[0] = 0x7fffffff;
+    win[1] = -1;
+  }
+  __syncthreads();
+  int lo = 0x7fffffff, hi = -1;
+  for (int r = R.r0 + (int)threadIdx.x; r < R.r1; r += kThreads) {
+    const int e0 = __ldg(rp + r), e1 = __ldg(rp + r + 1);
+    if (e1 > e0) {
+      lo = min(lo, __ldg(ci + e0));
+      hi = max(hi, __ldg(ci + e1 - 1));
+    }
+  }
+  if (hi >= 0) {
+    atomicMin(&win[0], lo);
+    atomicMax(&win[1], hi);
+  }
+  __syncthreads();
+  const int wlo = win[0], whi = win[1];
+  const long long cap = 2LL * sc.stage_bytes / (long long)sizeof(VT);
+  if (whi < 0 || (long long)whi - wlo + 1 > cap) {
+    __syncthreads();  // win is read by every thread before the next call resets it
+    spmv_vload<VT, COMP>(S, vals, xin, R, p1, nu_fmt, nu);
+    return;
+  }
+  VT* sx = reinterpret_cast<VT*>(sc.buf);
+  for (int k = threadIdx.x; k <= whi - wlo; k += kThreads) sx[k] = xin[wlo + k];
+  __syncthreads();
+  spmv_vload<VT, COMP>(S, vals, xin, R, p1, nu_fmt, nu, sx, wlo);
+  __syncthreads();  // the buffer and win are reused by the next call
+}
+
 template <typename VT, bool COMP>
 __device__ void spmv_dispatch_k(const DevSys& S, const VT* vals, const VT* xin, Rows R, int p1, int nu_fmt,
                                 DotAcc& nu, const StreamCtx* sc) {
@@ -641,6 +686,11 @@ __device__ void spmv_dispatch_k(const DevSys& S, const VT* vals, const VT* xin, 
   }
   if (S.A.sched[p1] == SCHED_MERGE) {
     spmv_merge<VT, COMP>(S, vals, xin, R, p1, nu_fmt, nu);
+    return;
+  }
+  if (S.A.sched[p1] == SCHED_XSTAGE) {
+    if (sc) spmv_xstage<VT, COMP>(S, vals, xin, R, p1, nu_fmt, nu, *sc);
+    else spmv_vload<VT, COMP>(S, vals, xin, R, p1, nu_fmt, nu);
     return;
   }
   if (sc && S.A.sched[p1] == SCHED_STREAM) {

@@ -21,7 +21,7 @@ FP16, BF16, TF32, FP32, FP64, BF16R, FP16R, Q52 = range(8)
 FORMAT_NAMES = ["fp16", "bf16", "tf32", "fp32", "fp64", "bf16r", "fp16r", "q52"]
 CONVERGED, MAX_ITER, BREAKDOWN = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "BAD_POLICY", 5: "TIMEOUT", 6: "INTERNAL"}
-SCHED_VECTOR, SCHED_STREAM, SCHED_VLOAD, SCHED_MERGE = 0, 1, 2, 3
+SCHED_VECTOR, SCHED_STREAM, SCHED_VLOAD, SCHED_MERGE, SCHED_XSTAGE = 0, 1, 2, 3, 4
 
 
 class MpcgError(RuntimeError):

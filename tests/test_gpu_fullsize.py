@@ -118,7 +118,7 @@ def _check_rows(fmt, y, ref, absref, A=None, rows=None, x=None):
         assert np.all(np.abs(y - ref) <= np.abs(ref) * 2.0 ** (1 - T_BITS[fmt]) + 1e-300)
 
 
-@pytest.mark.parametrize("sched,lanes", [(0, 1), (0, 2), (2, 1), (1, 2), (1, 4), (3, 1)])
+@pytest.mark.parametrize("sched,lanes", [(0, 1), (0, 2), (2, 1), (1, 2), (1, 4), (3, 1), (4, 1)])
 def test_fullsize_spmv_sampled_rows(big, sched, lanes):
     M, A, xs, b, ctx, mat = big
     n = A[0]

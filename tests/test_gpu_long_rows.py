@@ -12,7 +12,7 @@ from paper_2504_14268_gb300 import inputs as I
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-SCHEDULES = [(0, 1), (0, 2), (0, 4), (0, 32), (2, 1), (1, 1), (1, 4), (3, 1)]
+SCHEDULES = [(0, 1), (0, 2), (0, 4), (0, 32), (2, 1), (1, 1), (1, 4), (3, 1), (4, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -71,7 +71,7 @@ def _check_products(M, A, fmts, schedules, seed):
 def test_hub_rows_every_format_and_schedule(M):
     A = I.hub_laplacian(60000, 24, 1100, 20000, 1.0, np.random.default_rng(2))
     assert np.diff(A[1]).max() > 10000
-    assert _check_products(M, A, range(8), SCHEDULES, seed=3) >= 8 * 6
+    assert _check_products(M, A, range(8), SCHEDULES, seed=3) >= 8 * 7
 
 
 def test_merge_path_splits_rows_at_every_kind_of_boundary(M):
@@ -94,7 +94,7 @@ def test_merge_path_splits_rows_at_every_kind_of_boundary(M):
     ci = np.concatenate(rows).astype(np.int32)
     val = np.concatenate(vals)
     A = (n, rp, ci, val)
-    assert _check_products(M, A, range(8), [(3, 1)], seed=8) == 8
+    assert _check_products(M, A, range(8), [(3, 1), (4, 1)], seed=8) == 16
 
 
 def test_long_row_queue_overflow(M):

@@ -101,7 +101,7 @@ def test_format_copies_are_bit_exact(M):
         assert np.array_equal(y, ref, equal_nan=True), (fmt, np.flatnonzero(~((y == ref) | (np.isnan(y) & np.isnan(ref))))[:5])
 
 
-SCHEDULES = [(0, 1), (0, 2), (0, 4), (0, 8), (0, 16), (0, 32), (2, 1), (1, 1), (1, 2), (1, 4), (3, 1)]
+SCHEDULES = [(0, 1), (0, 2), (0, 4), (0, 8), (0, 16), (0, 32), (2, 1), (1, 1), (1, 2), (1, 4), (3, 1), (4, 1)]
 
 
 @pytest.mark.parametrize("which", ["poisson", "diffusion3d", "banded"])
@@ -306,6 +306,45 @@ def test_batched_matches_single_and_oracle(M):
         eg = np.linalg.norm(x.cpu().numpy() - xstar)
         eo = np.linalg.norm(ref.x - xstar)
         assert eg <= 10 * eo + 1e-12
+
+
+@pytest.mark.parametrize("stepped", [0, 2])
+def test_staged_x_schedule_in_the_solver_kernels(M, stepped):
+    """The staged-x product (schedule 4) inside the solver: a lockstep batch of diffusion systems
+    (stepped = 0) and the stepped single solve of a 2D Poisson system (stepped = 2), every
+    product format's schedule forced to it, against the oracle; a matrix whose columns do not
+    increase in every row is refused for it."""
+    ctx = _ctx(M, stepped=stepped)
+    pol = ctx.policy_fixed((0, 3, 3, 4))
+    if stepped == 0:
+        sets = I.cfg_train_set(count=4, m_lo=6, m_hi=12)
+    else:
+        A = I.poisson2d(64)
+        xs0, b0 = I.rhs_from_xstar(A, np.random.default_rng(9))
+        sets = [(A, b0, xs0)]
+    mats = [ctx.matrix(_dev(A)) for A, _, _ in sets]
+    for m in mats:
+        for f in range(8):
+            m.set_schedule(f, 4, 1)
+    bs = [torch.as_tensor(b).cuda() for _, b, _ in sets]
+    xs = [torch.zeros_like(b) for b in bs]
+    if stepped == 0:
+        res = ctx.solve_batched(mats, bs, xs, [1e-6] * len(sets), [500] * len(sets), pol)
+    else:
+        res = [ctx.solve(mats[0], bs[0], xs[0], 1e-6, 500, pol)[0]]
+    for (A, b, xstar), r, x in zip(sets, res, xs):
+        ref = O.solve(_oopts(), A, b, 1e-6, 500, fixed=(0, 3, 3, 4))
+        assert r["outcome"] == ref.outcome
+        assert abs(r["iters"] - ref.iters) <= max(2, ref.iters // 20)
+        assert np.linalg.norm(x.cpu().numpy() - xstar) <= 10 * np.linalg.norm(ref.x - xstar) + 1e-12
+    # columns out of order in one row: the staged window cannot be read off the row ends
+    n, rp, ci, val = I.poisson2d(8)
+    ci2, val2 = ci.copy(), val.copy()
+    e0, e1 = rp[10], rp[11]
+    ci2[e0:e1], val2[e0:e1] = ci[e0:e1][::-1].copy(), val[e0:e1][::-1].copy()
+    m2 = ctx.matrix(_dev((n, rp, ci2, val2)))
+    with pytest.raises(M.MpcgError):
+        m2.set_schedule(3, 4, 1)
 
 
 def test_graph_replay_reproduces_results(M):
