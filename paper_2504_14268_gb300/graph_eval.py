@@ -66,11 +66,16 @@ def main():
     rng = np.random.default_rng(0)
     nparam = M.lib().mpcg_mlp_nparams(H, len(opts.precs))
     mlp = ctx.policy_mlp((rng.standard_normal(nparam) * 0.1).astype(np.float32))
+    torch.cuda.synchronize()
+    t1 = time.time()
     losses = ctx.mlp_train(mlp, data, steps=args.mlp_steps, batch=1024, lr=1e-3, target_sync=500, seed=3)
     torch.cuda.synchronize()
+    t_mlp = time.time() - t1
     report = {"train": {"systems": len(train), "rounds": args.rounds, "transitions": int(len(data)),
                         "mlp_loss_first_last": [float(np.mean(losses[:100])), float(np.mean(losses[-100:]))],
-                        "seconds": round(time.time() - t0, 2)},
+                        "seconds": round(time.time() - t0, 2),
+                        "mlp_train": {"steps": args.mlp_steps, "batch": 1024, "seconds": round(t_mlp, 3),
+                                      "samples_per_s": round(args.mlp_steps * 1024 / max(t_mlp, 1e-9))}},
               "tau": tau, "cap": args.cap, "graphs": []}
     for n in args.sizes:
         t0 = time.time()
