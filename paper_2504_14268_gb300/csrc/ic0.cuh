@@ -74,10 +74,17 @@ __device__ __forceinline__ unsigned ic_mark(unsigned long long w) { return (unsi
 // Continues the row sum s -= l_e v_col(e) over e = ea, ea + 1, ... < eb in order, eight
 // words per memory round trip, as long as the rows read carry a mark >= target. True when
 // the sum is complete; otherwise ea and s hold the progress for the next attempt (the order
-// of the terms never changes).
+// of the terms never changes). A retry first reads only the word it stopped at, so that
+// waiting rows add one load per round to the lines being polled.
 __device__ __forceinline__ bool ic_accumulate(const int* __restrict__ ci, const float* __restrict__ Lf,
                                               const unsigned long long* W, int& ea, int eb, unsigned target,
-                                              float& s) {
+                                              float& s, bool retry) {
+  if (retry && ea < eb) {
+    const unsigned long long w = ld_relaxed64(W + __ldg(ci + ea));
+    if (ic_mark(w) < target) return false;
+    s = __fsub_rn(s, __fmul_rn(__ldg(Lf + ea), ic_value(w)));
+    ++ea;
+  }
   while (ea < eb) {
     unsigned long long w[8];
 #pragma unroll
@@ -245,7 +252,7 @@ __device__ __forceinline__ void ic_apply(const DevSys& S, Rows R, unsigned ep, u
         }
         if (stage == 2) {
           const int e_before = ea;
-          if (ic_accumulate(ci, Lf, W, ea, eb, bad ? 0u : tf, s)) {
+          if (ic_accumulate(ci, Lf, W, ea, eb, bad ? 0u : tf, s, !moved)) {
             st_relaxed64(W + i, ic_word(__fdiv_rn(s, __ldg(Lf + eb)), tf));
             ++m;
             stage = 0;
@@ -290,7 +297,7 @@ __device__ __forceinline__ void ic_apply(const DevSys& S, Rows R, unsigned ep, u
         }
         if (stage == 2) {
           const int e_before = ea;
-          if (ic_accumulate(ci, Lf, W, ea, eb, bad ? 0u : tb, s)) {
+          if (ic_accumulate(ci, Lf, W, ea, eb, bad ? 0u : tb, s, !moved)) {
             const float w = __fdiv_rn(s, __ldg(Lf + di));
             st_relaxed64(W + i, ic_word(w, tb));
             consume(i, __ldcg(S.r + i), (double)w);
