@@ -247,7 +247,11 @@ mpcg_status mpcg_matrix_info(mpcg_matrix_t A, mpcg_matrix_stats* info);
  * the fastest (the autotuner). `reps` timed launches per candidate. Matrices with fewer
  * than 2^22 nonzeros, whose products are too short to time apart, keep the row-length rule
  * that mpcg_matrix_create applies (vector loads for a mean row length up to ~32 nonzeros,
- * K lanes with about 24 nonzeros per lane beyond). */
+ * K lanes with about 24 nonzeros per lane beyond). Results are cached in the context by
+ * matrix bucket (half-octave of the mean row length, quarter of its coefficient of
+ * variation, octave of the longest row and of n, column order): a matrix of a bucket tuned
+ * before takes that bucket's schedules without timing when they all apply to it; with
+ * reps < 0 the matrix is timed (|reps| launches per candidate) and replaces the entry. */
 mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, void* stream);
 /* IC(0) factor of A in fp32, computed on the device once per matrix and kept with it
  * (Section 5 preconditions with an fp32 incomplete factorization; for SPD A this is its

@@ -10,7 +10,9 @@
 #include <cstring>
 #include <memory>
 #include <numeric>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -95,6 +97,9 @@ struct mpcg_ctx_s {
   int pocc[kPhaseKernels] = {}, pocc_s[kPhaseKernels] = {};  // the stepped solve's phase kernels
   std::string err;
   Plan plan;   // reused by mpcg_solve / mpcg_solve_batched / training
+  // the autotuner's results by matrix bucket (mean row length, its spread, longest row, n,
+  // column order): schedule and lanes of every format
+  std::map<std::tuple<int, int, int, int, int>, std::pair<std::vector<int>, std::vector<int>>> tune_cache;
   DevBuf spmv_x, spmv_q, spmv_y, spmv_err;
 };
 
@@ -1114,6 +1119,20 @@ mpcg_status mpcg_spmv(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t fmt, const double
   return MPCG_OK;
 }
 
+namespace {
+mpcg_status autotune_timed(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, void* stream);
+
+// Bucket of a matrix for the autotuner's cache: half-octaves of the mean row length, quarters
+// of its coefficient of variation, octaves of the longest row and of n, and the column order.
+std::tuple<int, int, int, int, int> tune_key(const mpcg_matrix_s* A) {
+  const int lm = (int)std::floor(2.0 * std::log2(std::max(A->mean, 1.0)));
+  const int lc = std::min(16, (int)std::floor(4.0 * A->cv));
+  const int lx = (int)std::floor(std::log2(std::max(A->maxr, 1.0)));
+  const int ln = (int)std::floor(std::log2((double)std::max(A->dm.n, 1)));
+  return std::make_tuple(lm, lc, lx, ln, A->dm.cols_sorted);
+}
+}  // namespace
+
 mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, void* stream) {
   if (!ctx || !A) return fail(ctx, MPCG_ERR_INVALID_ARG, "NULL argument");
   cudaSetDevice(ctx->device);
@@ -1125,6 +1144,33 @@ mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, 
     default_schedule(A);
     return MPCG_OK;
   }
+  // a matrix of a bucket tuned before in this context takes that bucket's schedules (when they
+  // all apply to it); reps < 0 times it anyway and replaces the bucket's entry
+  const auto key = tune_key(A);
+  if (reps > 0) {
+    auto it = ctx->tune_cache.find(key);
+    if (it != ctx->tune_cache.end()) {
+      bool ok = true;
+      for (int f = 0; f < NFMT && ok; ++f)
+        ok = mpcg_matrix_set_schedule(A, f, it->second.first[f], it->second.second[f]) == MPCG_OK;
+      if (ok) return MPCG_OK;
+    }
+  }
+  const mpcg_status st = autotune_timed(ctx, A, std::max(1, std::abs(reps)), stream);
+  if (st != MPCG_OK) return st;
+  std::vector<int> sc(NFMT), la(NFMT);
+  for (int f = 0; f < NFMT; ++f) {
+    sc[f] = A->dm.sched[f];
+    la[f] = A->dm.lanes[f];
+  }
+  ctx->tune_cache[key] = std::make_pair(sc, la);
+  return MPCG_OK;
+}
+
+namespace {
+// Times every (schedule, lanes) per format and keeps the fastest configuration.
+mpcg_status autotune_timed(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, void* stream) {
+  const int n = A->dm.n;
   DevBuf x, y;
   CK(ctx, x.ensure(8 * (size_t)n));
   CK(ctx, y.ensure(8 * (size_t)n));
@@ -1202,6 +1248,7 @@ mpcg_status mpcg_matrix_autotune(mpcg_ctx_t ctx, mpcg_matrix_t A, int32_t reps, 
   for (int f = 0; f < NFMT; ++f) mpcg_matrix_set_schedule(A, f, schedP[f], bestP[f]);
   return MPCG_OK;
 }
+}  // namespace
 
 // ---- policies -----------------------------------------------------------------------------
 

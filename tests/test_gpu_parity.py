@@ -347,6 +347,31 @@ def test_staged_x_schedule_in_the_solver_kernels(M, stepped):
         m2.set_schedule(3, 4, 1)
 
 
+def test_autotune_cache_by_bucket(M):
+    """The autotuner times a matrix once per bucket (row-length statistics, n, column order)
+    and context: a second matrix with the same pattern takes the first one's schedules without
+    timing; reps < 0 times it anyway."""
+    import time
+
+    ctx = _ctx(M)
+    m1 = ctx.matrix(_dev(I.fem27_aniso(72, 1e-3)))
+    m2 = ctx.matrix(_dev(I.fem27_aniso(72, 1e-2)))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m1.autotune(3)
+    t1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    m2.autotune(3)
+    t2 = time.perf_counter() - t0
+    i1, i2 = m1.info(), m2.info()
+    assert i1["spmv_sched"] == i2["spmv_sched"] and i1["spmv_lanes"] == i2["spmv_lanes"]
+    assert t2 < 0.1 * t1, (t1, t2)
+    t0 = time.perf_counter()
+    m2.autotune(-3)
+    t3 = time.perf_counter() - t0
+    assert t3 > 5 * t2, (t2, t3)
+
+
 def test_graph_replay_reproduces_results(M):
     sets = I.cfg_train_set(count=4, m_lo=6, m_hi=9)
     ctx = _ctx(M)
